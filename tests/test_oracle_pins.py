@@ -1,0 +1,434 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these tests uses the CUDA library.  Each checks the oracle against
+something other than itself: textbook closed forms, a second independent
+construction of the operator (weak-form assembly), exact invariants of the
+semi-discrete system, analytic heat-equation solutions, and values printed in
+the paper (tests/golden/).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import weakform as W
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _gold(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+# --------------------------------------------------------------------------
+# Nodal basis (Eq. 8): GLL tables
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_gll_closed_forms(p):
+    g = _gold("gll_closed_forms.json")[f"p{p}"]
+    xi, w, _ = O.gll(p)
+    np.testing.assert_allclose(xi, g["nodes"], atol=1e-15)
+    np.testing.assert_allclose(w, g["weights"], rtol=1e-14)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6, 7])
+def test_gll_quadrature_and_derivative_exactness(p):
+    xi, w, D = O.gll(p)
+    for k in range(2 * p):  # GLL integrates degree <= 2p-1 exactly
+        exact = 0.0 if k % 2 else 2.0 / (k + 1)
+        assert abs(np.dot(w, xi ** k) - exact) < 1e-13
+    for k in range(p + 1):  # D differentiates degree <= p exactly
+        d = D @ (xi ** k)
+        ref = k * xi ** (k - 1) if k else np.zeros_like(xi)
+        np.testing.assert_allclose(d, ref, atol=1e-11 * max(1, p ** 2))
+    # summation by parts, W D + (W D)^T = diag(-1, 0, ..., 0, 1)
+    B = np.diag(w) @ D
+    Bsym = B + B.T
+    ref = np.zeros_like(Bsym)
+    ref[0, 0], ref[-1, -1] = -1.0, 1.0
+    np.testing.assert_allclose(Bsym, ref, atol=1e-12 * p ** 2)
+
+
+# --------------------------------------------------------------------------
+# Operator (Eq. 7, fluxes of Sec. 3.2): strong form vs weak-form assembly
+# --------------------------------------------------------------------------
+
+CASES = [  # p, nx, ny, wall_mode, periodic, eta, seed
+    (1, 3, 3, 0, False, 0.0, 0),
+    (2, 4, 3, 0, False, 0.0, 1),
+    (3, 3, 4, 0, True, 0.0, 2),
+    (2, 4, 4, 1, False, 0.0, 3),
+    (2, 4, 4, 0, False, 1.0, 4),
+    (3, 3, 3, 0, False, 0.5, 5),
+    (4, 3, 2, 0, False, 0.0, 6),
+    (5, 2, 3, 1, True, 0.0, 7),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_operator_matches_weak_form_assembly(case):
+    p, nx, ny, mode, per, eta, seed = case
+    rng = np.random.default_rng(seed)
+    act = (rng.random((ny, nx)) > 0.3).astype(np.uint8)
+    act[0, 0] = 1
+    m = O.Mesh(p=p, active=act, h=0.7, x0=-1.0, y0=0.5, k0=1.3, eta=eta,
+               wall_mode=mode, periodic=per)
+    A = O.dense_operator(m)
+    B = W.assemble(m)
+    assert np.abs(A - B).max() <= 1e-13 * np.abs(B).max()
+
+
+def _components(act, periodic):
+    ny, nx = act.shape
+    lab = -np.ones_like(act, dtype=int)
+    c = 0
+    for s in zip(*np.nonzero(act)):
+        if lab[s] >= 0:
+            continue
+        stack = [s]
+        lab[s] = c
+        while stack:
+            y, x = stack.pop()
+            for dy, dx in ((0, 1), (0, -1), (1, 0), (-1, 0)):
+                yy, xx = y + dy, x + dx
+                if periodic:
+                    yy, xx = yy % ny, xx % nx
+                elif not (0 <= yy < ny and 0 <= xx < nx):
+                    continue
+                if act[yy, xx] and lab[yy, xx] < 0:
+                    lab[yy, xx] = c
+                    stack.append((yy, xx))
+        c += 1
+    return c
+
+
+@pytest.mark.parametrize("p,eta", [(1, 0.0), (2, 0.0), (3, 0.0), (2, 1.0), (4, 0.0)])
+def test_symmetric_semidefinite_and_nullspace(p, eta):
+    # periodic 6x6 with a wall ring that cuts off one pocket: two components
+    act = np.ones((6, 6), np.uint8)
+    act[1, 1:4] = 0
+    act[3, 1:4] = 0
+    act[2, 1] = 0
+    act[2, 3] = 0          # pocket (2,2) is isolated
+    act[5, 5] = 0
+    m = O.Mesh(p=p, active=act, h=0.8, k0=1.7, eta=eta, periodic=True)
+    A = O.dense_operator(m)
+    Wd = O.node_weights(m).ravel()
+    keep = np.repeat(act.ravel().astype(bool), (p + 1) ** 2)
+    S = (np.sqrt(Wd)[:, None] * A / np.sqrt(Wd)[None, :])[np.ix_(keep, keep)]
+    scale = np.abs(S).max()
+    assert np.abs(S - S.T).max() <= 1e-13 * scale
+    ev = np.linalg.eigvalsh(0.5 * (S + S.T))
+    assert ev.max() <= 1e-12 * scale
+    assert np.sum(np.abs(ev) < 1e-10 * scale) == _components(act, True) == 2
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_paper_wall_mode_is_stable(p):
+    rng = np.random.default_rng(10 + p)
+    act = (rng.random((5, 5)) > 0.3).astype(np.uint8)
+    m = O.Mesh(p=p, active=act, h=1.0, k0=1.0, wall_mode=1, periodic=True)
+    ev = np.linalg.eigvals(O.dense_operator(m))
+    assert ev.real.max() <= 1e-11 * np.abs(ev).max()
+
+
+def test_power_iteration_matches_dense_spectrum():
+    act = np.ones((5, 4), np.uint8)
+    act[2, 1] = 0
+    m = O.Mesh(p=3, active=act, h=0.5, k0=2.0)
+    A = O.dense_operator(m)
+    Wd = O.node_weights(m).ravel()
+    keep = np.repeat(act.ravel().astype(bool), 16)
+    S = (np.sqrt(Wd)[:, None] * A / np.sqrt(Wd)[None, :])[np.ix_(keep, keep)]
+    rho = np.abs(np.linalg.eigvalsh(0.5 * (S + S.T))).max()
+    est = O.power_rho(m, 400)
+    assert est <= rho * (1 + 1e-12)
+    assert est >= 0.99 * rho
+
+
+def test_rk3_real_limit():
+    z = -O.rk3_real_limit()
+    assert abs(1 + z + z * z / 2 + z ** 3 / 6 + 1) < 1e-13
+    assert abs(z + 2.5127453266) < 1e-8
+
+
+# --------------------------------------------------------------------------
+# Time stepping: SSP-RK3 against the modal solution and exp(tL)
+# --------------------------------------------------------------------------
+
+def test_rk3_equals_modal_formula_and_converges_to_exponential():
+    rng = np.random.default_rng(3)
+    act = np.ones((3, 4), np.uint8)
+    act[1, 2] = 0
+    m = O.Mesh(p=2, active=act, h=1.0, k0=1.0)
+    A = O.dense_operator(m)
+    u0 = rng.random(A.shape[0]) * np.repeat(act.ravel(), 9)
+    lam, V = np.linalg.eig(A)
+    rho = np.abs(lam).max()
+    T = 0.7
+    errs = []
+    for N in (40, 80, 160):
+        dt = T / N
+        R = 1 + dt * lam + (dt * lam) ** 2 / 2 + (dt * lam) ** 3 / 6
+        modal = np.real(V @ (R ** N * np.linalg.solve(V, u0)))
+        u = O.rk3(m, u0, N, dt).ravel()
+        assert np.abs(u - modal).max() <= 1e-12 * np.abs(u0).max()
+        exact = np.real(V @ (np.exp(T * lam) * np.linalg.solve(V, u0)))
+        errs.append(np.abs(u - exact).max())
+        assert dt * rho < 2.5
+    # third order in time
+    assert 7.0 < errs[0] / errs[1] < 9.0
+    assert 7.0 < errs[1] / errs[2] < 9.0
+
+
+# --------------------------------------------------------------------------
+# Sigma scheme (Sec. 4.1) and the paper's free-diffusion case (Sec. 4.2)
+# --------------------------------------------------------------------------
+
+def test_free_diffusion_paper_value_exact():
+    """Sec. 4.2: free diffusion for T = 36 ms, k = 0.45 um^2/ms gives Sigma =
+    2Tk I = 32.4 I.  For p >= 2, x and x^2 lie in the DG space and the
+    discrete Sigma(T) - Sigma(0) equals 2Tk exactly (to round-off) as long as
+    no mass reaches the absorbing edge.  The start density is resolved
+    (sigma0 = 2h) and the edge is >= 8 sigma(T) away: an under-resolved start
+    density excites high-frequency modes that spread faster than the
+    Gaussian and leak through a near edge."""
+    g = _gold("paper_free_diffusion.json")
+    k, T = g["k0_um2_per_ms"], g["T_ms"]
+    # odd p with the central fluxes has a slower-than-Gaussian far tail, so
+    # p = 3 gets a wider window and a looser bound
+    for p, nel, side, s0, tol in ((2, 60, 120.0, 4.0, 1e-11),
+                                  (4, 40, 160.0, 8.0, 1e-11),
+                                  (3, 60, 240.0, 8.0, 1e-9)):
+        h = side / nel
+        m = O.Mesh(p=p, active=np.ones((nel, nel), np.uint8), h=h,
+                   x0=-side / 2, y0=-side / 2, k0=k)
+        r = O.solve(m, np.array([[0.3 * h, -0.2 * h]]), s0, [T])
+        s, mu = r["sigma"][0], r["mu"][0]
+        assert abs(s[0] - g["sigma_analytic_diag"]) < tol * 32.4
+        assert abs(s[2] - g["sigma_analytic_diag"]) < tol * 32.4
+        assert abs(s[1]) < 1e-12 * 32.4
+        # first moments are constant in time (L x = 0), mass is conserved
+        np.testing.assert_allclose(mu, r["mom0"][0, 1:3] / r["mom0"][0, 0],
+                                   atol=1e-11)
+        assert abs(r["mass"][0][0] / r["mom0"][0, 0] - 1) < tol
+
+
+def _images_1d_var(xs, Ls, s2, nimg=8):
+    """Variance about xs of the heat kernel on [0, Ls] with absorbing ends
+    (Eq. 4), by the method of images and high-order quadrature."""
+    x = np.linspace(0, Ls, 40001)
+    f = np.zeros_like(x)
+    for n in range(-nimg, nimg + 1):
+        f += (np.exp(-(x - xs - 2 * n * Ls) ** 2 / (2 * s2))
+              - np.exp(-(x + xs - 2 * n * Ls) ** 2 / (2 * s2)))
+    w = np.full(x.size, x[1] - x[0])
+    w[0] = w[-1] = w[0] / 2
+    Z = np.sum(w * f)
+    m1 = np.sum(w * f * (x - xs)) / Z
+    m2 = np.sum(w * f * (x - xs) ** 2) / Z
+    return m2 - m1 ** 2
+
+
+def test_free_diffusion_paper_domain_absorbing_edge():
+    """The paper's own free-diffusion domain (Sec. 4.2): a 50 um square with
+    the absorbing edge of Eq. 4 only 4.3 sigma from the centre.  The square's
+    heat kernel is a product of 1D image series, which fixes Sigma; the
+    absorption pulls it 0.13% below 2Tk = 32.4."""
+    g = _gold("paper_free_diffusion.json")
+    k, T, side = g["k0_um2_per_ms"], g["T_ms"], g["side_um"]
+    nel, s0 = 50, 2.0
+    m = O.Mesh(p=3, active=np.ones((nel, nel), np.uint8), h=side / nel, k0=k)
+    r = O.solve(m, np.array([[side / 2, side / 2]]), s0, [T])
+    s = r["sigma"][0]
+    exact = (_images_1d_var(side / 2, side, s0 ** 2 + 2 * k * T)
+             - _images_1d_var(side / 2, side, s0 ** 2))
+    assert abs(exact / g["sigma_analytic_diag"] - 1 + 1.3e-3) < 1e-4
+    assert abs(s[0] / exact - 1) < 1e-7
+    assert abs(s[0] - s[2]) < 1e-12 * 32.4
+    assert abs(s[1]) < 1e-12 * 32.4
+
+
+@pytest.mark.parametrize("wall_mode", [0, 1])
+def test_mass_conservation_and_components(wall_mode):
+    """Reflecting walls (Eq. 3) conserve mass, separately in each connected
+    component of the extracellular region."""
+    act = np.ones((10, 10), np.uint8)
+    act[2:8, 2] = act[2:8, 7] = 0
+    act[2, 2:8] = act[7, 2:8] = 0       # closed wall ring around a pocket
+    act[0, 4] = act[5, 9] = 0
+    m = O.Mesh(p=2, active=act, h=0.5, k0=2.0, periodic=True, wall_mode=wall_mode)
+    rho = O.power_rho(m)
+    u0 = O.init_gaussian(m, 1.3, 1.1, 0.4)      # straddles the ring
+    n, dt = O.step_plan(rho, 2.0)
+    u = O.rk3(m, u0, n, dt)
+    inside = np.zeros(act.shape, dtype=bool)
+    inside[3:7, 3:7] = True
+    for region in (inside, ~inside):
+        a = u0.copy()
+        b = u.copy()
+        a[~region] = 0
+        b[~region] = 0
+        M0a = O.moments(m, a, 0, 0)[0]
+        M0b = O.moments(m, b, 0, 0)[0]
+        assert M0a > 1e-3
+        assert abs(M0b / M0a - 1) < 1e-13
+    assert np.abs(u[act == 0]).max() == 0.0
+
+
+def test_symmetry_transforms():
+    """Mirroring geometry and start point in x flips Sigma_xy and keeps the
+    diagonal; transposing swaps Sigma_xx and Sigma_yy."""
+    rng = np.random.default_rng(5)
+    act = (rng.random((20, 20)) > 0.25).astype(np.uint8)
+    h, x0, y0 = 0.5, -3.0, 1.0
+    src = np.array([[x0 + 9.3 * h, y0 + 10.4 * h]])
+    act[10, 9] = 1
+    base = O.Mesh(p=2, active=act, h=h, x0=x0, y0=y0, k0=1.0)
+    rho = O.power_rho(base)
+    plan = [O.step_plan(rho, 1.5)]
+    ns, dts = [plan[0][0]], [plan[0][1]]
+    r0 = O.solve(base, src, 0.3, [1.5], nsteps=ns, dt=dts)
+    mir = O.Mesh(p=2, active=act[:, ::-1], h=h, x0=x0, y0=y0, k0=1.0)
+    xs_m = 2 * x0 + 20 * h - src[0, 0]
+    r1 = O.solve(mir, np.array([[xs_m, src[0, 1]]]), 0.3, [1.5], nsteps=ns, dt=dts)
+    tr = O.Mesh(p=2, active=act.T, h=h, x0=y0, y0=x0, k0=1.0)
+    r2 = O.solve(tr, src[:, ::-1].copy(), 0.3, [1.5], nsteps=ns, dt=dts)
+    s0, s1, s2 = r0["sigma"][0], r1["sigma"][0], r2["sigma"][0]
+    scale = abs(s0[0])
+    assert abs(s1[0] - s0[0]) < 1e-12 * scale and abs(s1[2] - s0[2]) < 1e-12 * scale
+    assert abs(s1[1] + s0[1]) < 1e-12 * scale
+    assert abs(s2[0] - s0[2]) < 1e-12 * scale and abs(s2[2] - s0[0]) < 1e-12 * scale
+    assert abs(s2[1] - s0[1]) < 1e-12 * scale
+    assert s0[0] > 0 and s0[0] * s0[2] - s0[1] ** 2 > 0     # SPD
+
+
+def test_aggregation_is_mixture_covariance():
+    """Sec. 4.1 mixture of normalised densities: brute force on point
+    masses, Sigma = covariance of the equal-weight mixture."""
+    rng = np.random.default_rng(8)
+    m = 5
+    pts = [rng.normal(size=(7, 2)) * rng.uniform(0.5, 2, 2) + rng.normal(size=2) for _ in range(m)]
+    wts = [rng.uniform(0.1, 1.0, 7) for _ in range(m)]
+    starts = rng.normal(size=(m, 2))
+    mom = []
+    for P, w, s in zip(pts, wts, starts):
+        d = P - s
+        mom.append([w.sum(), (w * d[:, 0]).sum(), (w * d[:, 1]).sum(),
+                    (w * d[:, 0] ** 2).sum(), (w * d[:, 0] * d[:, 1]).sum(),
+                    (w * d[:, 1] ** 2).sum()])
+    s3, mu, mass = O.aggregate(np.array(mom))
+    # brute force: displacement samples of the mixture with weights w/(m W)
+    D = np.concatenate([P - s for P, s in zip(pts, starts)])
+    Wt = np.concatenate([w / w.sum() / m for w in wts])
+    mean = (Wt[:, None] * D).sum(0)
+    C = ((D - mean).T * Wt) @ (D - mean)
+    np.testing.assert_allclose(mu, mean, atol=1e-14)
+    np.testing.assert_allclose(s3, [C[0, 0], C[0, 1], C[1, 1]], atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# Convergence to analytic heat solutions
+# --------------------------------------------------------------------------
+
+def _mms_error(p, nel, eta, D=1.0, T=0.1):
+    side = 2 * math.pi
+    h = side / nel
+    m = O.Mesh(p=p, active=np.ones((nel, nel), np.uint8), h=h, k0=D, eta=eta,
+               periodic=True)
+    X, Y = O.node_coords(m)
+    a = 2 * math.pi / side
+    u0 = 1 + np.sin(a * X) * np.sin(a * Y)
+    rho = O.power_rho(m, 100)
+    n, dt = O.step_plan(rho, T, 0.2)
+    u = O.rk3(m, u0, n, dt)
+    ex = 1 + math.exp(-2 * D * a * a * T) * np.sin(a * X) * np.sin(a * Y)
+    return math.sqrt(np.sum(O.node_weights(m) * (u - ex) ** 2))
+
+
+@pytest.mark.parametrize("p,eta,order", [(1, 0.0, 1.8), (2, 0.0, 2.8), (3, 0.0, 2.8),
+                                         (2, 1.0, 2.8), (3, 1.0, 3.8)])
+def test_manufactured_periodic_heat_convergence(p, eta, order):
+    """u = 1 + exp(-2 D a^2 t) sin(ax) sin(ay) on a periodic square: the
+    central fluxes converge at order >= p (p+1 for even p); with the
+    penalty, p+1."""
+    e1, e2 = _mms_error(p, 8, eta), _mms_error(p, 16, eta)
+    assert math.log2(e1 / e2) > order
+
+
+def _channel_exact_sigma_yy(ys, a, sigma0, Dt):
+    """Variance about ys at time t of the Neumann heat problem on [0, a]
+    (Eq. 3 walls at y = 0 and y = a) whose start density is the Gaussian of
+    width sigma0 about ys cut to [0, a], as the discrete start density is.
+    The Neumann kernel is the image series sum_n g(y - y' - 2na) +
+    g(y + y' - 2na), g of variance 2 D t; integrals by 400-point
+    Gauss-Legendre quadrature (smooth integrands on [0, a])."""
+    gx, gw = np.polynomial.legendre.leggauss(400)
+    y = 0.5 * a * (gx + 1)
+    w = 0.5 * a * gw
+    f0 = np.exp(-(y - ys) ** 2 / (2 * sigma0 ** 2))
+    if Dt > 0:
+        d = y[:, None]
+        dp = y[None, :]
+        K = np.zeros((y.size, y.size))
+        for n in range(-4, 5):
+            K += np.exp(-(d - dp - 2 * n * a) ** 2 / (4 * Dt))
+            K += np.exp(-(d + dp - 2 * n * a) ** 2 / (4 * Dt))
+        f = K @ (w * f0)
+    else:
+        f = f0
+    Z = np.sum(w * f)
+    m1 = np.sum(w * f * (y - ys)) / Z
+    m2 = np.sum(w * f * (y - ys) ** 2) / Z
+    return m2 - m1 * m1
+
+
+def test_channel_closed_form():
+    """Walls at y = 0 and y = a (rows of removed elements, Eq. 3): Sigma_xx
+    is the free value 2 D t exactly; Sigma_yy converges to the Neumann image
+    solution."""
+    D, sigma0, T, a, ys = 1.0, 0.25, 0.3, 2.0, 0.62
+    exact_yy = (_channel_exact_sigma_yy(ys, a, sigma0, D * T)
+                - _channel_exact_sigma_yy(ys, a, sigma0, 0.0))
+    errs = []
+    for nel_y in (8, 16):
+        h = a / nel_y
+        nx = int(round(12.0 / h))
+        act = np.ones((nel_y + 2, nx), np.uint8)
+        act[0, :] = act[-1, :] = 0
+        m = O.Mesh(p=3, active=act, h=h, x0=-6.0, y0=-h, k0=D)
+        r = O.solve(m, np.array([[0.3 * h, ys]]), sigma0, [T])
+        s = r["sigma"][0]
+        assert abs(s[0] - 2 * D * T) < 1e-8
+        assert abs(s[1]) < 1e-14
+        errs.append(abs(s[2] - exact_yy))
+    assert errs[1] < errs[0] / 8
+    assert errs[1] < 1e-4 * exact_yy
+
+
+# --------------------------------------------------------------------------
+# Element mask from disks (substrate of Sec. 2.2, pixel mesh of Sec. 3.3)
+# --------------------------------------------------------------------------
+
+def test_mask_matches_brute_force():
+    import dginputs
+    d = dginputs.gamma_disks(3, 10.0, 2.0, 0.4, n=12, min_gap=0.1)
+    nc = 32
+    cell = O.mask_disks(d.L, nc, d.cx, d.cy, d.r)
+    h = d.L / nc
+    ref = np.ones((nc, nc), np.uint8)
+    for j in range(nc):
+        for i in range(nc):
+            x, y = (i + 0.5) * h, (j + 0.5) * h
+            for cx, cy, r in zip(d.cx, d.cy, d.r):
+                dx = (x - cx + d.L / 2) % d.L - d.L / 2
+                dy = (y - cy + d.L / 2) % d.L - d.L / 2
+                if math.hypot(dx, dy) < r:
+                    ref[j, i] = 0
+    assert np.array_equal(cell, ref)
+    assert 0.3 < cell.mean() < 0.9
