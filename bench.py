@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Throughput of the DG diffusion -> Sigma path on the 40 um cell workload.
+
+Workload (one GPU): 40x40 um periodic cell of 256x256 elements, p = 3
+(16 GLL nodes per element), Gamma(2, 0.5 um) disks at a seeded packing in
+[0.5, 0.7], tiled into a 7x7-cell absorbing window (1792^2 elements), 64
+seeded Gaussian start densities (sigma0 = 0.2 um), D = 2 um^2/ms.
+
+One bench step = R SSP-RK3 time steps of all 64 densities followed by the
+FP64 moment reduction and the covariance (every row of the hot path after
+the one-off geometry set-up).  ``value`` is DoF-steps/s (active nodes x
+densities x RK steps per second), timed with CUDA events on the library's
+stream with the state already resident.  ``e2e`` times the user's call
+sequence through the C ABI with host buffers: start points copied in
+(dg_set_sources, which re-initialises the densities), R steps, covariance
+copied out.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       [--precision f32|f64] [--rk R]
+Under torchrun each rank runs its own 64 densities (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import dginputs  # noqa: E402
+
+METRIC = "DoF-steps/s"
+BYTES_PER_DOF_STEP = {"f32": 32, "f64": 64}   # 8 state accesses per RK step
+FLOPS_PER_DOF_STEP = {3: 120}                  # 3 stages x (2n^3 + 12n^2) * 2 / n^2 at n = 4
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace('.', '').isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace('.', '').isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) > 8:
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _traffic_record(kernel_src: str):
+    """DRAM bytes per launch of the stage kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except OSError:
+        return None
+    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    return rec if rec.get("kernel_sha") == h else None
+
+
+def run_reference(args, world, rank):
+    """The oracle (plain FP64 C, OpenMP over elements) on host cores, each
+    step a bounded sample of the workload: one density, one RK step on the
+    full 1792^2-element window."""
+    if rank != 0:
+        return 0
+    import oracle as O
+    O.build()
+    w = dginputs.workload_cell40(args.seed, m=64)
+    cell = O.mask_disks(w.L, w.n_cell, w.disks.cx, w.disks.cy, w.disks.r)
+    act = O.window_mask(cell, w.tiles)
+    mesh = O.Mesh(p=w.p, active=act, h=w.h, x0=w.origin, y0=w.origin, k0=w.D)
+    dof = int(act.sum()) * (w.p + 1) ** 2
+    u = O.init_gaussian(mesh, *w.sources[0], w.sigma0)
+    dt = 1e-4
+    for _ in range(args.warmup):
+        u = O.rk3(mesh, u, 1, dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u = O.rk3(mesh, u, 1, dt)
+    el = time.perf_counter() - t0
+    v = dof * args.steps / el
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "DoF-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "window_elements": int(act.size),
+                       "active_elements": int(act.sum()), "p": w.p},
+            "cpu_baseline": {"value": v, "unit": "DoF-steps/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": "1 density x 1 SSP-RK3 step per bench step on the full window"},
+            "e2e": {"value": v, "unit": "DoF-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_sample(w, seconds_target=20.0):
+    """Oracle DoF-steps/s on a bounded sample: one density of the workload,
+    RK steps on the full window until ~seconds_target of CPU work."""
+    import oracle as O
+    O.build()
+    cell = O.mask_disks(w.L, w.n_cell, w.disks.cx, w.disks.cy, w.disks.r)
+    act = O.window_mask(cell, w.tiles)
+    mesh = O.Mesh(p=w.p, active=act, h=w.h, x0=w.origin, y0=w.origin, k0=w.D)
+    dof = int(act.sum()) * (w.p + 1) ** 2
+    u = O.init_gaussian(mesh, *w.sources[0], w.sigma0)
+    t0 = time.perf_counter()
+    u = O.rk3(mesh, u, 1, 1e-4)
+    one = time.perf_counter() - t0
+    n = max(1, min(20, int(seconds_target / max(one, 1e-3)) - 1))
+    t0 = time.perf_counter()
+    u = O.rk3(mesh, u, n, 1e-4)
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": dof * n / el, "unit": "DoF-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"1 of 64 densities x {n} SSP-RK3 steps on the full {act.shape[0]}^2 window"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--rk", type=int, default=20, help="RK3 steps per bench step")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = _dist()
+
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    import paper_1907_06191_gb300 as dg
+    from paper_1907_06191_gb300 import _build
+    if rank == 0 or world == 1:
+        _build.build()
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+        tdist.barrier()
+        _build.build()
+    torch.cuda.set_device(local)
+    dev = local
+
+    w = dginputs.workload_cell40(args.seed, m=64)
+    # weak scaling: every rank its own 64 start points
+    if world > 1:
+        from dginputs import sample_sources, source_box
+        lo, hi = source_box(w.L, w.tiles, w.sigma0, w.D, max(w.deltas))
+        w.sources = sample_sources(args.seed + 7919 + 1000 * rank, w.disks, 64, lo, hi, margin=w.h)
+    prec = dg.DG_FP32 if args.precision == "f32" else dg.DG_FP64
+    s = dg.DGSolver(p=w.p, precision=prec, D=w.D, sigma0=w.sigma0, device=dev)
+    s.set_geometry_disks(w.disks.cx, w.disks.cy, w.disks.r, w.L, w.n_cell, w.tiles)
+    stream = torch.cuda.Stream(device=dev)
+    s.set_stream(stream.cuda_stream)
+    s.set_sources(w.sources)
+    dt, rho = s.query_dt()
+    inf = s.info()
+    m = inf.m
+    dof = inf.dof_per_source * m
+    R = args.rk
+
+    def bench_step():
+        s.step(R, dt)
+        s.covariance()
+
+    for _ in range(args.warmup):
+        bench_step()
+    torch.cuda.synchronize(dev)
+
+    # device-timed region: state resident (16 GB > L2, no flush needed)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        tdist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(dev) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            bench_step()
+        ev1.record(stream)
+        ev1.synchronize()
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=f"cuda:{dev}")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    total_dof_steps = dof * R * args.steps * world
+    value = total_dof_steps / (ms * 1e-3)
+
+    # stage kernel alone: R RK steps = 3R launches of the fused stage kernel
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(R, dt)
+    e1.record(stream)
+    e1.synchronize()
+    stage_ms = e0.elapsed_time(e1) / (3 * R)
+    bytes_per_launch = BYTES_PER_DOF_STEP[args.precision] * dof / 3.0
+    peaks, src = _peaks()
+    achieved = bytes_per_launch / (stage_ms * 1e-3) / 1e9
+    rec = _traffic_record(os.path.join(ROOT, "paper_1907_06191_gb300", "csrc", "dg_stage.cuh"))
+    traffic = None
+    if rec and rec.get("precision") == args.precision:
+        traffic = rec["dram_bytes_per_launch_per_dof"] * dof
+    if args.precision == "f64":
+        # FP64 is bound by the FP64 pipe (2 FMA/clk/SM): 152 x 2 x 2 x 2.07 GHz
+        peak_f64 = 152 * 2 * 2 * 2.07e9 / 1e12
+        roofline = {"bound": "alu", "achieved": FLOPS_PER_DOF_STEP.get(w.p, 120) * dof / 3.0
+                    / (stage_ms * 1e-3) / 1e12, "peak": peak_f64, "unit": "TFLOP/s",
+                    "traffic": traffic, "peak_source": "derived from unit counts and max clock"}
+        roofline["frac"] = roofline["achieved"] / peak_f64
+    else:
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                    "peak_source": f"{src} hbm_gbs"}
+
+    # e2e through the C ABI with host buffers
+    xy_host = torch.from_numpy(np.ascontiguousarray(w.sources)).pin_memory()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        tdist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.set_sources(xy_host.numpy())
+        s.step(R, dt)
+        sig, mu, mass = s.covariance()
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=f"cuda:{dev}")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": total_dof_steps / e2e_s, "unit": "DoF-steps/s",
+           "h2d_bytes_per_step": int(m * 2 * 8),
+           "d2h_bytes_per_step": int(5 * 8 + m * 8)}
+
+    # agreement with the FP64 GPU path on the same steps
+    check = None
+    if not args.no_check and args.precision == "f32" and rank == 0:
+        s.set_sources(w.sources)
+        s.step(R, dt)
+        sig32 = s.covariance()[0]
+        mom32 = s.moments()
+        with dg.DGSolver(p=w.p, precision=dg.DG_FP64, D=w.D, sigma0=w.sigma0, device=dev) as d64:
+            d64.set_geometry_disks(w.disks.cx, w.disks.cy, w.disks.r, w.L, w.n_cell, w.tiles)
+            d64.set_sources(w.sources)
+            d64.step(R, dt)
+            sig64 = d64.covariance()[0]
+            mom64 = d64.moments()
+        m2_32 = mom32[:, 3:] / mom32[:, :1]
+        m2_64 = mom64[:, 3:] / mom64[:, :1]
+        check = {"steps": R, "sigma_rel_err": float(np.abs(sig32 - sig64).max() / np.abs(sig64).max()),
+                 "second_moment_rel_err": float(np.abs(m2_32 - m2_64).max() / np.abs(m2_64).max())}
+
+    s.close()
+    if rank != 0:
+        return 0
+    nsteps_50 = math.ceil(50.0 / dt)
+    line = {
+        "metric": METRIC, "value": value, "unit": "DoF-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": w.name, "p": w.p, "window_elements": inf.nx * inf.ny,
+                   "active_elements": inf.n_active, "densities_per_gpu": m,
+                   "dof_per_density": inf.dof_per_source, "rk_steps_per_bench_step": R,
+                   "dt_ms": dt, "rho_per_ms": rho, "packing": w.disks.packing,
+                   "disks": w.disks.n, "l2": "state (>=16 GB) larger than L2, no flush"},
+        "sigma_solves_per_s": value / (inf.dof_per_source * nsteps_50),
+        "sigma_solve_note": f"derived: one density to Delta = 50 ms takes {nsteps_50} RK steps",
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": args.steps * (3 * R + 3),
+        "clocks": clk.summary(),
+        "fp64_check": check,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline_sample(w)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,225 @@
+/*
+ * dgsigma.h -- C ABI of the GB300 (sm_103a) DG diffusion / covariance library.
+ *
+ * Method: Cervantes, Moreles, Pena, Ramirez-Manzanares, "A GPU implementation
+ * of the Discontinuous Galerkin method for simulation of diffusion in brain
+ * tissue" (arXiv 1907.06191).  Diffusion u_t = div(k grad u) in the
+ * extracellular space around disk-shaped axons (Sec. 2.1, Eqs. 1-5),
+ * discontinuous Galerkin in space (Sec. 3.1, Eqs. 6-8) with the central u-flux
+ * and the harmonic-mean q-flux (Sec. 3.2), explicit Runge-Kutta in time
+ * (SSP-RK3), then the covariance Sigma of the mixture of normalised densities
+ * (Sec. 4.1).
+ *
+ * Discretisation fixed by this library where the paper is silent: square
+ * elements on a uniform grid, tensor-product Gauss-Lobatto-Legendre (GLL)
+ * nodal basis of order p with the nodes as quadrature points (diagonal mass),
+ * SSP-RK3 (Shu-Osher form), moments by GLL nodal quadrature.
+ *
+ * Conventions for every call:
+ *   - Return value: DG_OK (0) or a positive DG_E* code; dg_last_error() gives
+ *     the message.  No call aborts, throws or exits.
+ *   - Host pointers are read or written only during the call; the library
+ *     copies inputs.  Outputs go to caller-owned host buffers of the stated
+ *     size.  Device memory belongs to the context unless bound with
+ *     dg_bind_state().
+ *   - Units: micrometres (um), milliseconds (ms), um^2/ms.
+ *   - Node values are exchanged in the dense layout [m][ny][nx][n][n]
+ *     (source, element row, element column, node row j along y, node column
+ *     i along x), n = p+1, FP64; elements outside the mesh read as 0.
+ *   - A context is used by one host thread at a time.  All device work goes
+ *     to the context's stream (dg_set_stream); calls that return host data
+ *     synchronise that stream.
+ */
+#ifndef DGSIGMA_H
+#define DGSIGMA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define DG_OK 0
+#define DG_EINVAL 1     /* bad argument (range, size, NULL, point outside mesh) */
+#define DG_ENOMEM 2     /* device or host allocation failed */
+#define DG_ECUDA 3      /* CUDA runtime error (no device, launch failure, ...) */
+#define DG_EUNSTABLE 4  /* the solution grew: time step above the stability bound */
+#define DG_ENONFINITE 5 /* NaN or Inf in the moments */
+#define DG_ETIMEOUT 6   /* a bounded device wait ran out */
+#define DG_ESTATE 7     /* call out of order (e.g. step before sources) */
+
+/* Arithmetic of the state and of the element operator.  Moments and the
+ * covariance are always accumulated in FP64. */
+#define DG_FP64 0
+#define DG_FP32 1
+
+/* Axon (inactive) elements.  DG_WALL_REMOVED: the elements are not in the
+ * mesh; their faces are reflecting walls with u_hat = u^- and q_hat = 0
+ * (Eq. 3).  DG_WALL_PAPER: the paper's Sec. 3.3 treatment, elements kept with
+ * k = 0 and frozen at u = 0, so u_hat = u^-/2 and the harmonic mean of
+ * Sec. 3.2 gives q_hat = 0. */
+#define DG_WALL_REMOVED 0
+#define DG_WALL_PAPER 1
+
+/* Outer edge of the domain: DG_BC_ABSORBING is Eq. 4 (u = 0, u_hat = 0,
+ * normal flux k q^- . n); DG_BC_PERIODIC wraps both axes. */
+#define DG_BC_ABSORBING 0
+#define DG_BC_PERIODIC 1
+
+typedef struct dg_config {
+  int p;             /* polynomial order of the GLL basis, 1..5 (Eq. 8) */
+  int precision;     /* DG_FP64 or DG_FP32 */
+  double D;          /* diffusivity k0 of the extracellular region (Eq. 5), > 0 */
+  double sigma0;     /* width of the Gaussian start density (um), > 0; it
+                        stands in for the Dirac data of Sec. 4.1 */
+  double eta;        /* interior-penalty factor >= 0; 0 = the paper's fluxes */
+  double cfl_safety; /* dt_max = cfl_safety * 2.5127.../rho(L); (0, 1] */
+  int wall_mode;     /* DG_WALL_REMOVED or DG_WALL_PAPER */
+  int boundary;      /* DG_BC_ABSORBING or DG_BC_PERIODIC */
+  int power_iters;   /* power iterations for rho(L); 0 selects 200 */
+  int device;        /* CUDA device ordinal; -1 = the calling thread's current */
+} dg_config;
+
+typedef struct dg_ctx dg_ctx;
+
+typedef struct dg_info {
+  int p, n_nodes;         /* order and nodes per element (p+1)^2 */
+  int nx, ny;             /* elements of the domain grid */
+  long long n_active;     /* elements in the mesh (extracellular) */
+  long long dof_per_source; /* n_active * n_nodes */
+  int m;                  /* number of start points (0 before dg_set_sources) */
+  int precision;
+  double h, x0, y0;       /* element side and lower-left corner */
+  double t;               /* current time (ms) */
+  long long steps;        /* RK steps taken since dg_set_sources */
+  size_t state_bytes;     /* device bytes of the three RK state arrays */
+} dg_info;
+
+/* Fill *cfg with defaults: p=3, FP64, D=2, sigma0=0.2, eta=0, cfl 0.9,
+ * removed walls, absorbing edge, 200 power iterations, device -1. */
+void dg_config_default(dg_config *cfg);
+
+/* Create a context on cfg->device.  *out receives the handle (NULL on
+ * failure).  Errors: DG_EINVAL (cfg out of range), DG_ECUDA (no device),
+ * DG_ENOMEM. */
+int dg_create(const dg_config *cfg, dg_ctx **out);
+
+/* Release the context and all device memory it owns.  NULL is ignored. */
+void dg_destroy(dg_ctx *ctx);
+
+/* Static message of a status code. */
+const char *dg_strerror(int code);
+
+/* Message of the last failing call on ctx ("" if none); valid until the next
+ * call on ctx. */
+const char *dg_last_error(const dg_ctx *ctx);
+
+/* Use the given cudaStream_t (as void*) for all later device work; NULL
+ * returns to the context's own stream.  The caller keeps ownership. */
+int dg_set_stream(dg_ctx *ctx, void *stream);
+
+/* Domain from an explicit element mask (Sec. 3.3 pixel mesh): active is
+ * [ny][nx] bytes, nonzero = extracellular element; element (ex, ey) covers
+ * [x0 + ex h, x0 + (ex+1) h] x [y0 + ey h, y0 + (ey+1) h].  Clears sources.
+ * Errors: DG_EINVAL (nx, ny < 1, h <= 0, no active element), DG_ENOMEM. */
+int dg_set_geometry_mask(dg_ctx *ctx, const uint8_t *active, int nx, int ny,
+                         double h, double x0, double y0);
+
+/* Domain from disks in a periodic square cell (substrate of Sec. 2.2; axons
+ * of Eq. 5).  cx, cy, r: ndisks centres and radii in [0, L)^2.  The cell is
+ * meshed with n_cell x n_cell elements of side h = L/n_cell; an element is
+ * removed when its centre lies strictly inside a disk (squared periodic
+ * minimum-image distance < r^2).  The domain is a tiles x tiles window of
+ * copies of the cell (tiles odd, >= 1) with the central copy at [0, L)^2,
+ * i.e. x0 = y0 = -(tiles/2) L; its outer edge follows cfg->boundary.  The
+ * mask is built on the device.  Clears sources.  Errors: DG_EINVAL. */
+int dg_set_geometry_disks(dg_ctx *ctx, const double *cx, const double *cy,
+                          const double *r, int ndisks, double L, int n_cell,
+                          int tiles);
+
+/* Copy the element mask as built, [ny][nx] bytes (1 = in the mesh). */
+int dg_get_mask(dg_ctx *ctx, uint8_t *active);
+
+/* Sizes and state of the context. */
+int dg_get_info(dg_ctx *ctx, dg_info *info);
+
+/* Start points of the Sigma scheme (Sec. 4.1): xy is [m][2] (um).  Each
+ * density starts as the normalised Gaussian of width sigma0 about its point,
+ * interpolated at the GLL nodes of mesh elements (Dirac data of Sec. 4.1
+ * regularised).  Sets t = 0 and records the start moments for
+ * Sigma(0).  Errors: DG_EINVAL (m < 1, a point outside the domain or in an
+ * element outside the mesh), DG_ENOMEM, DG_ESTATE (no geometry). */
+int dg_set_sources(dg_ctx *ctx, const double *xy, int m);
+
+/* Stability bound of the explicit step: rho = spectral radius of L from
+ * cfg->power_iters FP64 power iterations (seeded, deterministic), and
+ * dt_max = cfl_safety * x3 / rho with x3 = 2.5127... the real-axis limit of
+ * SSP-RK3.  Computed once per geometry.  Either pointer may be NULL. */
+int dg_query_dt(dg_ctx *ctx, double *dt_max, double *rho);
+
+/* Advance every density by nsteps SSP-RK3 steps of size dt (ms):
+ * u1 = u + dt L u, u2 = 3/4 u + 1/4 (u1 + dt L u1),
+ * u <- 1/3 u + 2/3 (u2 + dt L u2) (Sec. 3.1, explicit Runge-Kutta).
+ * No host synchronisation.  Errors: DG_EINVAL (nsteps < 0, dt <= 0),
+ * DG_ESTATE (no sources). */
+int dg_step(dg_ctx *ctx, int nsteps, double dt);
+
+/* Advance from the current t to Delta in N = ceil((Delta - t)/dt_max) equal
+ * steps, then check the moments: DG_ENONFINITE on NaN/Inf, DG_EUNSTABLE when
+ * the L1 norm of any density grew above twice its start value.  Delta >= t. */
+int dg_propagate_to(dg_ctx *ctx, double Delta);
+
+/* Raw FP64 moments at the current t, out[m][6] = {M0, Mx, My, Mxx, Mxy, Myy}
+ * with M_f = sum over nodes of J^2 w_i w_j f(x - xs, y - ys) u, about each
+ * start point (xs, ys) (Sec. 4.1, nodal quadrature). */
+int dg_moments(dg_ctx *ctx, double *out);
+
+/* Covariance by the Sigma scheme of Sec. 4.1: each density normalised by its
+ * mass and centred at its start point, mixed with weights 1/m, moment-matched
+ * Gaussian: mu = mean_s M1/M0, Sigma_mix = mean_s M2/M0 - mu mu^T.  sigma3
+ * receives {Sxx, Sxy, Syy} of Sigma(t) = Sigma_mix(t) - Sigma_mix(0) (the
+ * start width removed), mu2 the mixture mean displacement, mass (m values,
+ * may be NULL) each M0(t).  Computed on the device in FP64. */
+int dg_covariance(dg_ctx *ctx, double *sigma3, double *mu2, double *mass);
+
+/* Replace every density u by L u (the DG operator alone, Eq. 7 with the
+ * fluxes of Sec. 3.2); for operator tests.  Leaves t unchanged. */
+int dg_apply_operator(dg_ctx *ctx);
+
+/* Node values in the dense FP64 layout (see above), host buffer of
+ * m * ny * nx * n * n doubles. */
+int dg_get_nodes(dg_ctx *ctx, double *host);
+int dg_set_nodes(dg_ctx *ctx, const double *host);
+
+/* Node values of selected elements: idx is [k][3] = {source, ex, ey};
+ * out receives [k][n][n] doubles (node row j along y, column i along x); an
+ * element outside the mesh reads as 0.  Errors: DG_EINVAL (index out of
+ * range). */
+int dg_get_elements(dg_ctx *ctx, const int *idx, int k, double *out);
+
+/* Checkpoint: dg_state_size gives the bytes of a snapshot (header, start
+ * points, start moments, t, step count and the densities in the state
+ * precision); dg_get_state writes it to host memory, dg_set_state restores it
+ * into a context with the same geometry, order and precision.  Restored runs
+ * continue bit for bit. */
+int dg_state_size(dg_ctx *ctx, size_t *bytes);
+int dg_get_state(dg_ctx *ctx, void *host, size_t bytes);
+int dg_set_state(dg_ctx *ctx, const void *host, size_t bytes);
+
+/* Bytes of device memory the three RK state arrays need for m start points
+ * (after a geometry is set). */
+int dg_state_bytes(dg_ctx *ctx, int m, size_t *bytes);
+
+/* Use caller-owned device memory (e.g. a torch tensor's data_ptr) of at least
+ * dg_state_bytes(m) bytes, 256-byte aligned, for the state arrays of the
+ * next dg_set_sources with m points.  The caller keeps it alive until the
+ * context is destroyed or rebound; NULL returns to library-owned memory. */
+int dg_bind_state(dg_ctx *ctx, void *device_ptr, size_t bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGSIGMA_H */

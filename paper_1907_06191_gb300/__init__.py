@@ -1,0 +1,275 @@
+"""Python binding of libdgsigma (include/dgsigma.h): GB300-native DG
+diffusion in the extracellular space around axons and the displacement
+covariance Sigma (Cervantes et al., arXiv 1907.06191).
+
+The functions here carry the C names and only marshal arguments (numpy
+arrays, ctypes structs); every step of the method runs in the library's
+CUDA kernels.  There is no fallback: if the library has not been built the
+import raises.  ``DGSolver`` is a small convenience wrapper over the same
+calls.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "DG_OK", "DG_EINVAL", "DG_ENOMEM", "DG_ECUDA", "DG_EUNSTABLE", "DG_ENONFINITE",
+    "DG_ETIMEOUT", "DG_ESTATE", "DG_FP64", "DG_FP32", "DG_WALL_REMOVED",
+    "DG_WALL_PAPER", "DG_BC_ABSORBING", "DG_BC_PERIODIC", "DgError", "dg_config",
+    "dg_info", "lib", "library_path", "DGSolver", "EXPORTS",
+]
+
+DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA = 0, 1, 2, 3
+DG_EUNSTABLE, DG_ENONFINITE, DG_ETIMEOUT, DG_ESTATE = 4, 5, 6, 7
+DG_FP64, DG_FP32 = 0, 1
+DG_WALL_REMOVED, DG_WALL_PAPER = 0, 1
+DG_BC_ABSORBING, DG_BC_PERIODIC = 0, 1
+
+
+class dg_config(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("precision", ctypes.c_int),
+                ("D", ctypes.c_double), ("sigma0", ctypes.c_double),
+                ("eta", ctypes.c_double), ("cfl_safety", ctypes.c_double),
+                ("wall_mode", ctypes.c_int), ("boundary", ctypes.c_int),
+                ("power_iters", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+class dg_info(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("n_nodes", ctypes.c_int),
+                ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("n_active", ctypes.c_longlong), ("dof_per_source", ctypes.c_longlong),
+                ("m", ctypes.c_int), ("precision", ctypes.c_int),
+                ("h", ctypes.c_double), ("x0", ctypes.c_double), ("y0", ctypes.c_double),
+                ("t", ctypes.c_double), ("steps", ctypes.c_longlong),
+                ("state_bytes", ctypes.c_size_t)]
+
+
+_P = ctypes.c_void_p
+_DP = ctypes.POINTER(ctypes.c_double)
+_I, _D, _SZ = ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+
+# name -> (restype, argtypes); the exported C ABI
+EXPORTS = {
+    "dg_config_default": (None, [ctypes.POINTER(dg_config)]),
+    "dg_create": (_I, [ctypes.POINTER(dg_config), ctypes.POINTER(_P)]),
+    "dg_destroy": (None, [_P]),
+    "dg_strerror": (ctypes.c_char_p, [_I]),
+    "dg_last_error": (ctypes.c_char_p, [_P]),
+    "dg_set_stream": (_I, [_P, _P]),
+    "dg_set_geometry_mask": (_I, [_P, _P, _I, _I, _D, _D, _D]),
+    "dg_set_geometry_disks": (_I, [_P, _DP, _DP, _DP, _I, _D, _I, _I]),
+    "dg_get_mask": (_I, [_P, _P]),
+    "dg_get_info": (_I, [_P, ctypes.POINTER(dg_info)]),
+    "dg_set_sources": (_I, [_P, _DP, _I]),
+    "dg_query_dt": (_I, [_P, _DP, _DP]),
+    "dg_step": (_I, [_P, _I, _D]),
+    "dg_propagate_to": (_I, [_P, _D]),
+    "dg_moments": (_I, [_P, _DP]),
+    "dg_covariance": (_I, [_P, _DP, _DP, _DP]),
+    "dg_apply_operator": (_I, [_P]),
+    "dg_get_nodes": (_I, [_P, _DP]),
+    "dg_set_nodes": (_I, [_P, _DP]),
+    "dg_get_elements": (_I, [_P, _P, _I, _DP]),
+    "dg_state_size": (_I, [_P, ctypes.POINTER(_SZ)]),
+    "dg_get_state": (_I, [_P, _P, _SZ]),
+    "dg_set_state": (_I, [_P, _P, _SZ]),
+    "dg_state_bytes": (_I, [_P, _I, ctypes.POINTER(_SZ)]),
+    "dg_bind_state": (_I, [_P, _P, _SZ]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library; raises if it was not built (no fallback)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"libdgsigma is not built ({path} missing); run "
+                "paper_1907_06191_gb300._build.build() or __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class DgError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_DP)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def default_config(**kw) -> dg_config:
+    cfg = dg_config()
+    lib().dg_config_default(ctypes.byref(cfg))
+    for k, v in kw.items():
+        if not hasattr(cfg, k):
+            raise TypeError(f"unknown config field {k}")
+        setattr(cfg, k, v)
+    return cfg
+
+
+class DGSolver:
+    """One library context: geometry, start points, RK3 stepping, moments and
+    Sigma.  Methods map one to one onto the C calls."""
+
+    def __init__(self, **cfg):
+        self._L = lib()
+        self.cfg = default_config(**cfg)
+        h = _P()
+        rc = self._L.dg_create(ctypes.byref(self.cfg), ctypes.byref(h))
+        if rc != DG_OK:
+            raise DgError(rc, f"dg_create: {self._L.dg_strerror(rc).decode()}")
+        self.ctx = h
+        self._bound = None
+
+    def _ck(self, rc: int, what: str):
+        if rc != DG_OK:
+            msg = self._L.dg_last_error(self.ctx).decode()
+            raise DgError(rc, f"{what}: {self._L.dg_strerror(rc).decode()}: {msg}")
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self._L.dg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # geometry
+    def set_geometry_mask(self, active, h: float, x0: float = 0.0, y0: float = 0.0):
+        a = np.ascontiguousarray(active, dtype=np.uint8)
+        ny, nx = a.shape
+        self._ck(self._L.dg_set_geometry_mask(self.ctx, a.ctypes.data, nx, ny, h, x0, y0),
+                 "dg_set_geometry_mask")
+
+    def set_geometry_disks(self, cx, cy, r, L: float, n_cell: int, tiles: int):
+        cx, cy, r = _f64(cx), _f64(cy), _f64(r)
+        self._ck(self._L.dg_set_geometry_disks(self.ctx, _dp(cx), _dp(cy), _dp(r), int(r.size),
+                                               L, n_cell, tiles), "dg_set_geometry_disks")
+
+    def info(self) -> dg_info:
+        inf = dg_info()
+        self._ck(self._L.dg_get_info(self.ctx, ctypes.byref(inf)), "dg_get_info")
+        return inf
+
+    def get_mask(self) -> np.ndarray:
+        inf = self.info()
+        out = np.zeros((inf.ny, inf.nx), dtype=np.uint8)
+        self._ck(self._L.dg_get_mask(self.ctx, out.ctypes.data), "dg_get_mask")
+        return out
+
+    # sources and time stepping
+    def set_sources(self, xy):
+        xy = _f64(xy).reshape(-1, 2)
+        self._ck(self._L.dg_set_sources(self.ctx, _dp(xy), xy.shape[0]), "dg_set_sources")
+
+    def query_dt(self):
+        dt, rho = ctypes.c_double(), ctypes.c_double()
+        self._ck(self._L.dg_query_dt(self.ctx, ctypes.byref(dt), ctypes.byref(rho)), "dg_query_dt")
+        return dt.value, rho.value
+
+    def step(self, nsteps: int, dt: float):
+        self._ck(self._L.dg_step(self.ctx, int(nsteps), float(dt)), "dg_step")
+
+    def propagate_to(self, delta: float):
+        self._ck(self._L.dg_propagate_to(self.ctx, float(delta)), "dg_propagate_to")
+
+    def moments(self) -> np.ndarray:
+        out = np.zeros((self.info().m, 6))
+        self._ck(self._L.dg_moments(self.ctx, _dp(out)), "dg_moments")
+        return out
+
+    def covariance(self):
+        s3, mu, mass = np.zeros(3), np.zeros(2), np.zeros(self.info().m)
+        self._ck(self._L.dg_covariance(self.ctx, _dp(s3), _dp(mu), _dp(mass)), "dg_covariance")
+        return s3, mu, mass
+
+    def apply_operator(self):
+        self._ck(self._L.dg_apply_operator(self.ctx), "dg_apply_operator")
+
+    def get_nodes(self) -> np.ndarray:
+        inf = self.info()
+        n = inf.p + 1
+        out = np.zeros((inf.m, inf.ny, inf.nx, n, n))
+        self._ck(self._L.dg_get_nodes(self.ctx, _dp(out)), "dg_get_nodes")
+        return out
+
+    def set_nodes(self, u):
+        inf = self.info()
+        n = inf.p + 1
+        u = _f64(u).reshape(inf.m, inf.ny, inf.nx, n, n)
+        self._ck(self._L.dg_set_nodes(self.ctx, _dp(u)), "dg_set_nodes")
+
+    def get_elements(self, idx) -> np.ndarray:
+        """Node values [k, n, n] of elements idx = [(source, ex, ey), ...]."""
+        idx = np.ascontiguousarray(idx, dtype=np.int32).reshape(-1, 3)
+        n = self.info().p + 1
+        out = np.zeros((idx.shape[0], n, n))
+        self._ck(self._L.dg_get_elements(self.ctx, idx.ctypes.data, idx.shape[0], _dp(out)),
+                 "dg_get_elements")
+        return out
+
+    # checkpoint
+    def get_state(self) -> bytes:
+        sz = ctypes.c_size_t()
+        self._ck(self._L.dg_state_size(self.ctx, ctypes.byref(sz)), "dg_state_size")
+        buf = ctypes.create_string_buffer(sz.value)
+        self._ck(self._L.dg_get_state(self.ctx, buf, sz.value), "dg_get_state")
+        return buf.raw
+
+    def set_state(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        self._ck(self._L.dg_set_state(self.ctx, buf, len(blob)), "dg_set_state")
+
+    # device memory and streams from torch
+    def state_bytes(self, m: int) -> int:
+        sz = ctypes.c_size_t()
+        self._ck(self._L.dg_state_bytes(self.ctx, int(m), ctypes.byref(sz)), "dg_state_bytes")
+        return sz.value
+
+    def bind_state(self, tensor):
+        """Use a CUDA tensor's memory (uint8, >= state_bytes(m)) for the state."""
+        if tensor is None:
+            self._ck(self._L.dg_bind_state(self.ctx, None, 0), "dg_bind_state")
+            self._bound = None
+            return
+        nbytes = tensor.numel() * tensor.element_size()
+        self._ck(self._L.dg_bind_state(self.ctx, ctypes.c_void_p(tensor.data_ptr()), nbytes),
+                 "dg_bind_state")
+        self._bound = tensor
+
+    def set_stream(self, stream_ptr: int | None):
+        self._ck(self._L.dg_set_stream(self.ctx, ctypes.c_void_p(stream_ptr) if stream_ptr else None),
+                 "dg_set_stream")

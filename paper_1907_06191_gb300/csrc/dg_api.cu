@@ -1,0 +1,725 @@
+// dg_api.cu -- the C ABI of include/dgsigma.h.
+//
+// Host code here validates arguments, owns device memory and sequences the
+// kernels; every arithmetic step of the path runs in the kernels of
+// dg_stage.cuh, dg_geometry.cu and dg_reduce.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dg_internal.h"
+
+using namespace dg;
+
+struct dg_ctx {
+  Ctx c;
+};
+
+namespace {
+
+constexpr int kGraphChunk = 64;             // RK steps per captured graph
+constexpr int kCheckChunk = 4096;           // steps between stability checks
+constexpr uint64_t kStateMagic = 0x31474453474432ull;  // "2DGSDG1"
+
+int fail(dg_ctx *ctx, int code, const std::string &msg) {
+  if (ctx) ctx->c.last_error = msg;
+  return code;
+}
+
+int cuda_fail(dg_ctx *ctx, cudaError_t e, const char *what) {
+  return fail(ctx, DG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(expr, what)                                   \
+  do {                                                   \
+    cudaError_t _e = (expr);                             \
+    if (_e != cudaSuccess) return cuda_fail(ctx, _e, what); \
+  } while (0)
+
+void drop_graph(Ctx &c) {
+  if (c.graph) cudaGraphExecDestroy(c.graph);
+  c.graph = nullptr;
+  c.graph_steps = 0;
+}
+
+void free_state(Ctx &c) {
+  drop_graph(c);
+  if (c.state_owned && c.d_state) cudaFree(c.d_state);
+  c.d_state = nullptr;
+  cudaFree(c.d_src);
+  cudaFree(c.d_mom);
+  cudaFree(c.d_mom0);
+  cudaFree(c.d_part);
+  cudaFree(c.d_out);
+  c.d_src = c.d_mom = c.d_mom0 = c.d_part = c.d_out = nullptr;
+  c.m = 0;
+  c.t = 0;
+  c.steps = 0;
+  c.state_bytes = 0;
+  c.src.clear();
+}
+
+void *state_array(Ctx &c, int k) {
+  return (char *)c.d_state + (size_t)k * c.m * c.field_elems() * c.esize();
+}
+
+size_t state_bytes_for(const Ctx &c, int m) {
+  size_t b = 3 * (size_t)m * c.field_elems() * c.esize();
+  return (b + 255) / 256 * 256;
+}
+
+// One SSP-RK3 step: U1 = U + dt L U; U2 = 3/4 U + 1/4 (U1 + dt L U1);
+// U <- 1/3 U + 2/3 (U2 + dt L U2).  L = (k/J^2) R.
+cudaError_t rk3_step(Ctx &c, double dt, cudaStream_t s) {
+  const double J = 0.5 * c.geo.h;
+  const double kc = c.cfg.D / (J * J);
+  const double pen = c.cfg.eta * (c.cfg.p + 1.0) * (c.cfg.p + 1.0) * 0.5;
+  const int wallA = c.cfg.wall_mode == DG_WALL_PAPER;
+  const long long nA = c.geo.n_active, st = c.geo.n_pad;
+  const double co[3][3] = {{0.0, 1.0, dt * kc},
+                           {0.75, 0.25, 0.25 * dt * kc},
+                           {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * dt * kc}};
+  void *U0 = state_array(c, 0), *U1 = state_array(c, 1), *U2 = state_array(c, 2);
+  void *in[3] = {U0, U1, U2};
+  void *outp[3] = {U1, U2, U0};
+  void *base[3] = {nullptr, U0, U0};
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+    if (c.cfg.precision == DG_FP64) {
+      StageCoef<double> sc{co[k][0], co[k][1], co[k][2], pen, wallA};
+      e = launch_stage_f64(c.cfg.p, (const double *)in[k], (const double *)base[k],
+                           (double *)outp[k], c.geo.d_nb, nA, st, c.m, c.gll, sc, s);
+    } else {
+      StageCoef<float> sc{(float)co[k][0], (float)co[k][1], (float)co[k][2], (float)pen,
+                          wallA};
+      e = launch_stage_f32(c.cfg.p, (const float *)in[k], (const float *)base[k],
+                           (float *)outp[k], c.geo.d_nb, nA, st, c.m, c.gll, sc, s);
+    }
+  }
+  return e;
+}
+
+int run_steps(dg_ctx *ctx, int nsteps, double dt) {
+  Ctx &c = ctx->c;
+  int left = nsteps;
+  if (left >= kGraphChunk) {
+    if (!c.graph || c.graph_dt != dt || c.graph_stream != c.stream) {
+      drop_graph(c);
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+      cudaError_t e = cudaSuccess;
+      for (int k = 0; k < kGraphChunk && e == cudaSuccess; ++k) e = rk3_step(c, dt, c.stream);
+      cudaError_t e2 = cudaStreamEndCapture(c.stream, &g);
+      if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(ctx, e, "stage launch during capture");
+      }
+      CK(e2, "end capture");
+      e = cudaGraphInstantiate(&c.graph, g, 0);
+      cudaGraphDestroy(g);
+      CK(e, "graph instantiate");
+      c.graph_dt = dt;
+      c.graph_steps = kGraphChunk;
+      c.graph_stream = c.stream;
+    }
+    while (left >= kGraphChunk) {
+      CK(cudaGraphLaunch(c.graph, c.stream), "graph launch");
+      left -= kGraphChunk;
+    }
+  }
+  for (int k = 0; k < left; ++k) CK(rk3_step(c, dt, c.stream), "stage launch");
+  c.steps += nsteps;
+  return DG_OK;
+}
+
+int compute_moments(dg_ctx *ctx, double *d_dst) {
+  Ctx &c = ctx->c;
+  CK(launch_moments(c, state_array(c, 0), c.d_part, d_dst, c.stream), "moments");
+  return DG_OK;
+}
+
+int ensure_rho(dg_ctx *ctx) {
+  Ctx &c = ctx->c;
+  if (c.have_rho) return DG_OK;
+  if (!c.have_geo) return fail(ctx, DG_ESTATE, "no geometry");
+  const size_t nv = (size_t)c.geo.n_pad * c.np();
+  double *v = nullptr, *w = nullptr, *res = nullptr, *part = nullptr;
+  auto cleanup = [&]() { cudaFree(v); cudaFree(w); cudaFree(res); cudaFree(part); };
+  cudaError_t e;
+  if ((e = cudaMalloc(&v, nv * 8)) != cudaSuccess || (e = cudaMalloc(&w, nv * 8)) != cudaSuccess ||
+      (e = cudaMalloc(&res, 8 * kMomFields)) != cudaSuccess ||
+      (e = cudaMalloc(&part, 8 * kMomFields * (size_t)kMomBlocks)) != cudaSuccess) {
+    cleanup();
+    return fail(ctx, DG_ENOMEM, std::string("power iteration buffers: ") + cudaGetErrorString(e));
+  }
+  const double J = 0.5 * c.geo.h;
+  const double kc = c.cfg.D / (J * J);
+  const double pen = c.cfg.eta * (c.cfg.p + 1.0) * (c.cfg.p + 1.0) * 0.5;
+  StageCoef<double> sc{0.0, 0.0, kc, pen, c.cfg.wall_mode == DG_WALL_PAPER};
+  const int iters = c.cfg.power_iters > 0 ? c.cfg.power_iters : 200;
+  e = launch_random_field(c, v, 12345ull, c.stream);
+  if (e == cudaSuccess) e = launch_wnorm2(c, v, part, res, c.stream);
+  if (e == cudaSuccess) e = launch_scale_by_rnorm(c, v, res, v, c.stream);
+  for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+    e = launch_stage_f64(c.cfg.p, v, nullptr, w, c.geo.d_nb, c.geo.n_active, c.geo.n_pad, 1,
+                         c.gll, sc, c.stream);
+    if (e == cudaSuccess) e = launch_wnorm2(c, w, part, res, c.stream);
+    if (e == cudaSuccess && it + 1 < iters) e = launch_scale_by_rnorm(c, w, res, v, c.stream);
+  }
+  double r2 = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&r2, res, 8, cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "power iteration");
+  if (!(r2 > 0.0) || !std::isfinite(r2)) return fail(ctx, DG_ENONFINITE, "power iteration gave no finite spectral radius");
+  c.rho = std::sqrt(r2);
+  c.dt_max = c.cfg.cfl_safety * rk3_real_axis_limit() / c.rho;
+  c.have_rho = true;
+  return DG_OK;
+}
+
+int check_config(const dg_config *cfg, std::string &why) {
+  if (cfg->p < 1 || cfg->p > kMaxP) { why = "p must be in 1..5"; return DG_EINVAL; }
+  if (cfg->precision != DG_FP64 && cfg->precision != DG_FP32) { why = "bad precision"; return DG_EINVAL; }
+  if (!(cfg->D > 0.0) || !std::isfinite(cfg->D)) { why = "D must be > 0"; return DG_EINVAL; }
+  if (!(cfg->sigma0 > 0.0)) { why = "sigma0 must be > 0"; return DG_EINVAL; }
+  if (!(cfg->eta >= 0.0)) { why = "eta must be >= 0"; return DG_EINVAL; }
+  if (!(cfg->cfl_safety > 0.0 && cfg->cfl_safety <= 1.0)) { why = "cfl_safety must be in (0, 1]"; return DG_EINVAL; }
+  if (cfg->wall_mode != DG_WALL_REMOVED && cfg->wall_mode != DG_WALL_PAPER) { why = "bad wall_mode"; return DG_EINVAL; }
+  if (cfg->boundary != DG_BC_ABSORBING && cfg->boundary != DG_BC_PERIODIC) { why = "bad boundary"; return DG_EINVAL; }
+  if (cfg->power_iters < 0) { why = "power_iters must be >= 0"; return DG_EINVAL; }
+  return DG_OK;
+}
+
+int finish_geometry(dg_ctx *ctx) {
+  Ctx &c = ctx->c;
+  std::string err;
+  const int code = build_connectivity(c.geo, c.cfg.boundary == DG_BC_PERIODIC, c.stream, err);
+  if (code != DG_OK) {
+    free_geometry(c.geo);
+    return fail(ctx, code, err);
+  }
+  c.geo.h_mask.resize((size_t)c.geo.nx * c.geo.ny);
+  cudaError_t e = cudaMemcpyAsync(c.geo.h_mask.data(), c.geo.d_mask, c.geo.h_mask.size(),
+                                  cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) {
+    free_geometry(c.geo);
+    return cuda_fail(ctx, e, "mask copy");
+  }
+  c.have_geo = true;
+  return DG_OK;
+}
+
+int set_sources_impl(dg_ctx *ctx, const double *xy, int m) {
+  Ctx &c = ctx->c;
+  if (!c.have_geo) return fail(ctx, DG_ESTATE, "dg_set_sources before a geometry");
+  if (!xy || m < 1 || m > 65535) return fail(ctx, DG_EINVAL, "need 1 <= m <= 65535 start points");
+  // validate: inside the domain and in a mesh element
+  const std::vector<uint8_t> &mask = c.geo.h_mask;
+  for (int s = 0; s < m; ++s) {
+    const double x = xy[2 * s], y = xy[2 * s + 1];
+    const double fx = (x - c.geo.x0) / c.geo.h, fy = (y - c.geo.y0) / c.geo.h;
+    if (!(fx >= 0.0 && fy >= 0.0 && fx < c.geo.nx && fy < c.geo.ny))
+      return fail(ctx, DG_EINVAL, "start point " + std::to_string(s) + " outside the domain");
+    const int ex = (int)fx, ey = (int)fy;
+    if (!mask[(size_t)ey * c.geo.nx + ex])
+      return fail(ctx, DG_EINVAL, "start point " + std::to_string(s) + " lies in an axon element");
+  }
+  // Same number of start points on the same geometry: keep the buffers (and
+  // any captured graph, whose pointers stay valid).
+  const bool reuse = c.m == m && c.d_state != nullptr;
+  if (!reuse) {
+    free_state(c);
+    const size_t need = state_bytes_for(c, m);
+    if (c.bound_ptr) {
+      if (c.bound_bytes < need) return fail(ctx, DG_EINVAL, "bound state buffer too small");
+      c.d_state = c.bound_ptr;
+      c.state_owned = false;
+    } else {
+      CK(cudaMalloc(&c.d_state, need), "state allocation");
+      c.state_owned = true;
+    }
+    c.state_bytes = need;
+    c.m = m;
+    CK(cudaMalloc(&c.d_src, sizeof(double) * 2 * m), "source allocation");
+    CK(cudaMalloc(&c.d_mom, sizeof(double) * kMomFields * m), "moment allocation");
+    CK(cudaMalloc(&c.d_mom0, sizeof(double) * kMomFields * m), "moment allocation");
+    CK(cudaMalloc(&c.d_part, sizeof(double) * kMomFields * kMomBlocks * (size_t)m), "partial allocation");
+    CK(cudaMalloc(&c.d_out, sizeof(double) * 8), "output allocation");
+  }
+  c.src.assign(xy, xy + 2 * (size_t)m);
+  CK(cudaMemcpyAsync(c.d_src, c.src.data(), sizeof(double) * 2 * m, cudaMemcpyHostToDevice, c.stream), "source copy");
+  CK(launch_init_sources(c, state_array(c, 0), c.stream), "init sources");
+  int r = compute_moments(ctx, c.d_mom0);
+  if (r != DG_OK) return r;
+  CK(cudaMemcpyAsync(c.d_mom, c.d_mom0, sizeof(double) * kMomFields * m, cudaMemcpyDeviceToDevice, c.stream), "moment copy");
+  c.t = 0.0;
+  c.steps = 0;
+  return DG_OK;
+}
+
+int check_growth(dg_ctx *ctx) {
+  Ctx &c = ctx->c;
+  std::vector<double> mom((size_t)c.m * kMomFields), mom0((size_t)c.m * kMomFields);
+  int r = compute_moments(ctx, c.d_mom);
+  if (r != DG_OK) return r;
+  CK(cudaMemcpyAsync(mom.data(), c.d_mom, mom.size() * 8, cudaMemcpyDeviceToHost, c.stream), "moment copy");
+  CK(cudaMemcpyAsync(mom0.data(), c.d_mom0, mom0.size() * 8, cudaMemcpyDeviceToHost, c.stream), "moment copy");
+  CK(cudaStreamSynchronize(c.stream), "moments");
+  for (int s = 0; s < c.m; ++s) {
+    const double *q = &mom[(size_t)s * kMomFields];
+    for (int f = 0; f < kMomFields; ++f)
+      if (!std::isfinite(q[f]))
+        return fail(ctx, DG_EUNSTABLE, "density " + std::to_string(s) + " became non-finite: time step above the stability bound");
+    if (q[6] > 2.0 * mom0[(size_t)s * kMomFields + 6])
+      return fail(ctx, DG_EUNSTABLE, "density " + std::to_string(s) + " grew: time step above the stability bound");
+  }
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dg_config_default(dg_config *cfg) {
+  if (!cfg) return;
+  cfg->p = 3;
+  cfg->precision = DG_FP64;
+  cfg->D = 2.0;
+  cfg->sigma0 = 0.2;
+  cfg->eta = 0.0;
+  cfg->cfl_safety = 0.9;
+  cfg->wall_mode = DG_WALL_REMOVED;
+  cfg->boundary = DG_BC_ABSORBING;
+  cfg->power_iters = 200;
+  cfg->device = -1;
+}
+
+const char *dg_strerror(int code) {
+  switch (code) {
+    case DG_OK: return "ok";
+    case DG_EINVAL: return "invalid argument";
+    case DG_ENOMEM: return "out of memory";
+    case DG_ECUDA: return "CUDA error";
+    case DG_EUNSTABLE: return "unstable time step";
+    case DG_ENONFINITE: return "non-finite values";
+    case DG_ETIMEOUT: return "device wait timed out";
+    case DG_ESTATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+const char *dg_last_error(const dg_ctx *ctx) { return ctx ? ctx->c.last_error.c_str() : ""; }
+
+int dg_create(const dg_config *cfg, dg_ctx **out) {
+  if (!out) return DG_EINVAL;
+  *out = nullptr;
+  if (!cfg) return DG_EINVAL;
+  std::string why;
+  if (check_config(cfg, why) != DG_OK) return DG_EINVAL;
+  dg_ctx *ctx = new (std::nothrow) dg_ctx();
+  if (!ctx) return DG_ENOMEM;
+  Ctx &c = ctx->c;
+  c.cfg = *cfg;
+  if (c.cfg.power_iters == 0) c.cfg.power_iters = 200;
+  int dev = cfg->device;
+  cudaError_t e;
+  if (dev < 0) {
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) { delete ctx; return DG_ECUDA; }
+  }
+  if ((e = cudaSetDevice(dev)) != cudaSuccess) { delete ctx; return DG_ECUDA; }
+  c.device = dev;
+  if ((e = cudaStreamCreateWithFlags(&c.own_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+    delete ctx;
+    return DG_ECUDA;
+  }
+  c.stream = c.own_stream;
+  if (!gll_tables(c.cfg.p, &c.gll)) {
+    cudaStreamDestroy(c.own_stream);
+    delete ctx;
+    return DG_EINVAL;
+  }
+  *out = ctx;
+  return DG_OK;
+}
+
+void dg_destroy(dg_ctx *ctx) {
+  if (!ctx) return;
+  Ctx &c = ctx->c;
+  cudaSetDevice(c.device);
+  if (c.stream) cudaStreamSynchronize(c.stream);
+  free_state(c);
+  free_geometry(c.geo);
+  if (c.own_stream) cudaStreamDestroy(c.own_stream);
+  delete ctx;
+}
+
+int dg_set_stream(dg_ctx *ctx, void *stream) {
+  if (!ctx) return DG_EINVAL;
+  Ctx &c = ctx->c;
+  c.stream = stream ? (cudaStream_t)stream : c.own_stream;
+  drop_graph(c);
+  return DG_OK;
+}
+
+int dg_set_geometry_mask(dg_ctx *ctx, const uint8_t *active, int nx, int ny, double h,
+                         double x0, double y0) {
+  if (!ctx) return DG_EINVAL;
+  Ctx &c = ctx->c;
+  if (!active || nx < 1 || ny < 1 || !(h > 0.0) || !std::isfinite(x0) || !std::isfinite(y0))
+    return fail(ctx, DG_EINVAL, "bad mask geometry arguments");
+  if ((long long)nx * ny > (1ll << 31) - 1) return fail(ctx, DG_EINVAL, "domain too large");
+  CK(cudaSetDevice(c.device), "set device");
+  free_state(c);
+  free_geometry(c.geo);
+  c.have_geo = false;
+  c.have_rho = false;
+  c.geo.nx = nx; c.geo.ny = ny; c.geo.h = h; c.geo.x0 = x0; c.geo.y0 = y0;
+  CK(cudaMalloc(&c.geo.d_mask, (size_t)nx * ny), "mask allocation");
+  std::vector<uint8_t> m01((size_t)nx * ny);
+  for (size_t k = 0; k < m01.size(); ++k) m01[k] = active[k] ? 1 : 0;
+  CK(cudaMemcpyAsync(c.geo.d_mask, m01.data(), m01.size(), cudaMemcpyHostToDevice, c.stream), "mask copy");
+  CK(cudaStreamSynchronize(c.stream), "mask copy");
+  return finish_geometry(ctx);
+}
+
+int dg_set_geometry_disks(dg_ctx *ctx, const double *cx, const double *cy, const double *r,
+                          int ndisks, double L, int n_cell, int tiles) {
+  if (!ctx) return DG_EINVAL;
+  Ctx &c = ctx->c;
+  if (ndisks < 0 || (ndisks > 0 && (!cx || !cy || !r)) || !(L > 0.0) || n_cell < 1 ||
+      tiles < 1 || tiles % 2 == 0)
+    return fail(ctx, DG_EINVAL, "bad disk geometry arguments (tiles must be odd)");
+  const long long nwin = (long long)n_cell * tiles;
+  if (nwin * nwin > (1ll << 31) - 1) return fail(ctx, DG_EINVAL, "domain too large");
+  for (int d = 0; d < ndisks; ++d)
+    if (!(r[d] >= 0.0) || !std::isfinite(cx[d]) || !std::isfinite(cy[d]))
+      return fail(ctx, DG_EINVAL, "bad disk " + std::to_string(d));
+  CK(cudaSetDevice(c.device), "set device");
+  free_state(c);
+  free_geometry(c.geo);
+  c.have_geo = false;
+  c.have_rho = false;
+  c.geo.nx = c.geo.ny = (int)nwin;
+  c.geo.h = L / n_cell;
+  c.geo.x0 = c.geo.y0 = -(double)(tiles / 2) * L;
+  CK(cudaMalloc(&c.geo.d_mask, (size_t)nwin * nwin), "mask allocation");
+  double *d = nullptr;
+  const int nd = ndisks > 0 ? ndisks : 1;
+  CK(cudaMalloc(&d, sizeof(double) * 3 * nd), "disk allocation");
+  cudaError_t e = cudaSuccess;
+  if (ndisks > 0) {
+    e = cudaMemcpyAsync(d, cx, 8 * ndisks, cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + nd, cy, 8 * ndisks, cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + 2 * nd, r, 8 * ndisks, cudaMemcpyHostToDevice, c.stream);
+  }
+  if (e == cudaSuccess) e = build_mask_disks(d, d + nd, d + 2 * nd, ndisks, L, n_cell, tiles, c.geo.d_mask, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "disk mask");
+  return finish_geometry(ctx);
+}
+
+int dg_get_mask(dg_ctx *ctx, uint8_t *active) {
+  if (!ctx || !active) return DG_EINVAL;
+  Ctx &c = ctx->c;
+  if (!c.have_geo) return fail(ctx, DG_ESTATE, "no geometry");
+  CK(cudaMemcpyAsync(active, c.geo.d_mask, (size_t)c.geo.nx * c.geo.ny, cudaMemcpyDeviceToHost, c.stream), "mask copy");
+  CK(cudaStreamSynchronize(c.stream), "mask copy");
+  return DG_OK;
+}
+
+int dg_get_info(dg_ctx *ctx, dg_info *info) {
+  if (!ctx || !info) return DG_EINVAL;
+  const Ctx &c = ctx->c;
+  std::memset(info, 0, sizeof(*info));
+  info->p = c.cfg.p;
+  info->n_nodes = c.np();
+  info->precision = c.cfg.precision;
+  info->nx = c.geo.nx;
+  info->ny = c.geo.ny;
+  info->n_active = c.geo.n_active;
+  info->dof_per_source = c.geo.n_active * c.np();
+  info->m = c.m;
+  info->h = c.geo.h;
+  info->x0 = c.geo.x0;
+  info->y0 = c.geo.y0;
+  info->t = c.t;
+  info->steps = c.steps;
+  info->state_bytes = c.state_bytes;
+  return DG_OK;
+}
+
+int dg_set_sources(dg_ctx *ctx, const double *xy, int m) {
+  if (!ctx) return DG_EINVAL;
+  CK(cudaSetDevice(ctx->c.device), "set device");
+  try {
+    return set_sources_impl(ctx, xy, m);
+  } catch (const std::bad_alloc &) {
+    return fail(ctx, DG_ENOMEM, "host allocation");
+  }
+}
+
+int dg_query_dt(dg_ctx *ctx, double *dt_max, double *rho) {
+  if (!ctx) return DG_EINVAL;
+  CK(cudaSetDevice(ctx->c.device), "set device");
+  const int r = ensure_rho(ctx);
+  if (r != DG_OK) return r;
+  if (dt_max) *dt_max = ctx->c.dt_max;
+  if (rho) *rho = ctx->c.rho;
+  return DG_OK;
+}
+
+int dg_step(dg_ctx *ctx, int nsteps, double dt) {
+  if (!ctx) return DG_EINVAL;
+  Ctx &c = ctx->c;
+  if (c.m < 1) return fail(ctx, DG_ESTATE, "dg_step before dg_set_sources");
+  if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, DG_EINVAL, "need nsteps >= 0 and dt > 0");
+  CK(cudaSetDevice(c.device), "set device");
+  const int r = run_steps(ctx, nsteps, dt);
+  if (r == DG_OK) c.t += nsteps * dt;
+  return r;
+}
+
+int dg_propagate_to(dg_ctx *ctx, double Delta) {
+  if (!ctx) return DG_EINVAL;
+  Ctx &c = ctx->c;
+  if (c.m < 1) return fail(ctx, DG_ESTATE, "dg_propagate_to before dg_set_sources");
+  if (!std::isfinite(Delta) || Delta < c.t) return fail(ctx, DG_EINVAL, "Delta must be >= the current time");
+  CK(cudaSetDevice(c.device), "set device");
+  int r = ensure_rho(ctx);
+  if (r != DG_OK) return r;
+  if (Delta == c.t) return DG_OK;
+  const double span = Delta - c.t;
+  const double q = span / c.dt_max;
+  long long N = (long long)std::ceil(q - 1e-12);
+  if (N < 1) N = 1;
+  if (N > (1ll << 40)) return fail(ctx, DG_EINVAL, "too many steps");
+  const double dt = span / (double)N;
+  long long done = 0;
+  while (done < N) {
+    const int chunk = (int)std::min<long long>(kCheckChunk, N - done);
+    r = run_steps(ctx, chunk, dt);
+    if (r != DG_OK) return r;
+    done += chunk;
+    r = check_growth(ctx);
+    if (r != DG_OK) return r;
+  }
+  c.t = Delta;
+  return DG_OK;
+}
+
+int dg_moments(dg_ctx *ctx, double *out) {
+  if (!ctx || !out) return DG_EINVAL;
+  Ctx &c = ctx->c;
+  if (c.m < 1) return fail(ctx, DG_ESTATE, "no sources");
+  CK(cudaSetDevice(c.device), "set device");
+  int r = compute_moments(ctx, c.d_mom);
+  if (r != DG_OK) return r;
+  std::vector<double> tmp((size_t)c.m * kMomFields);
+  CK(cudaMemcpyAsync(tmp.data(), c.d_mom, tmp.size() * 8, cudaMemcpyDeviceToHost, c.stream), "moment copy");
+  CK(cudaStreamSynchronize(c.stream), "moments");
+  for (int s = 0; s < c.m; ++s)
+    for (int f = 0; f < 6; ++f) out[s * 6 + f] = tmp[(size_t)s * kMomFields + f];
+  return DG_OK;
+}
+
+int dg_covariance(dg_ctx *ctx, double *sigma3, double *mu2, double *mass) {
+  if (!ctx || !sigma3 || !mu2) return DG_EINVAL;
+  Ctx &c = ctx->c;
+  if (c.m < 1) return fail(ctx, DG_ESTATE, "no sources");
+  CK(cudaSetDevice(c.device), "set device");
+  int r = compute_moments(ctx, c.d_mom);
+  if (r != DG_OK) return r;
+  CK(launch_covariance(c.d_mom, c.d_mom0, c.m, c.d_out, c.stream), "covariance");
+  double out[5];
+  CK(cudaMemcpyAsync(out, c.d_out, sizeof(out), cudaMemcpyDeviceToHost, c.stream), "covariance copy");
+  if (mass)
+    CK(cudaMemcpy2DAsync(mass, sizeof(double), c.d_mom, sizeof(double) * kMomFields, sizeof(double), c.m,
+                         cudaMemcpyDeviceToHost, c.stream), "mass copy");
+  CK(cudaStreamSynchronize(c.stream), "covariance");
+  sigma3[0] = out[0]; sigma3[1] = out[1]; sigma3[2] = out[2];
+  mu2[0] = out[3]; mu2[1] = out[4];
+  return DG_OK;
+}
+
+int dg_apply_operator(dg_ctx *ctx) {
+  if (!ctx) return DG_EINVAL;
+  Ctx &c = ctx->c;
+  if (c.m < 1) return fail(ctx, DG_ESTATE, "no sources");
+  CK(cudaSetDevice(c.device), "set device");
+  const double J = 0.5 * c.geo.h;
+  const double kc = c.cfg.D / (J * J);
+  const double pen = c.cfg.eta * (c.cfg.p + 1.0) * (c.cfg.p + 1.0) * 0.5;
+  const int wallA = c.cfg.wall_mode == DG_WALL_PAPER;
+  void *U0 = state_array(c, 0), *U1 = state_array(c, 1);
+  cudaError_t e;
+  if (c.cfg.precision == DG_FP64) {
+    StageCoef<double> sc{0.0, 0.0, kc, pen, wallA};
+    e = launch_stage_f64(c.cfg.p, (const double *)U0, nullptr, (double *)U1, c.geo.d_nb, c.geo.n_active,
+                         c.geo.n_pad, c.m, c.gll, sc, c.stream);
+  } else {
+    StageCoef<float> sc{0.0f, 0.0f, (float)kc, (float)pen, wallA};
+    e = launch_stage_f32(c.cfg.p, (const float *)U0, nullptr, (float *)U1, c.geo.d_nb, c.geo.n_active,
+                         c.geo.n_pad, c.m, c.gll, sc, c.stream);
+  }
+  CK(e, "operator launch");
+  CK(cudaMemcpyAsync(U0, U1, (size_t)c.m * c.field_elems() * c.esize(), cudaMemcpyDeviceToDevice, c.stream), "copy");
+  CK(cudaStreamSynchronize(c.stream), "operator");
+  return DG_OK;
+}
+
+int dg_get_nodes(dg_ctx *ctx, double *host) {
+  if (!ctx || !host) return DG_EINVAL;
+  Ctx &c = ctx->c;
+  if (c.m < 1) return fail(ctx, DG_ESTATE, "no sources");
+  CK(cudaSetDevice(c.device), "set device");
+  const size_t nd = (size_t)c.m * c.geo.nx * c.geo.ny * c.np();
+  double *d = nullptr;
+  CK(cudaMalloc(&d, nd * 8), "dense buffer");
+  cudaError_t e = cudaMemsetAsync(d, 0, nd * 8, c.stream);
+  if (e == cudaSuccess) e = launch_nodes_to_dense(c, state_array(c, 0), d, c.stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host, d, nd * 8, cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "get nodes");
+  return DG_OK;
+}
+
+int dg_set_nodes(dg_ctx *ctx, const double *host) {
+  if (!ctx || !host) return DG_EINVAL;
+  Ctx &c = ctx->c;
+  if (c.m < 1) return fail(ctx, DG_ESTATE, "no sources");
+  CK(cudaSetDevice(c.device), "set device");
+  const size_t nd = (size_t)c.m * c.geo.nx * c.geo.ny * c.np();
+  double *d = nullptr;
+  CK(cudaMalloc(&d, nd * 8), "dense buffer");
+  cudaError_t e = cudaMemcpyAsync(d, host, nd * 8, cudaMemcpyHostToDevice, c.stream);
+  if (e == cudaSuccess) e = launch_dense_to_nodes(c, d, state_array(c, 0), c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "set nodes");
+  return DG_OK;
+}
+
+int dg_get_elements(dg_ctx *ctx, const int *idx, int k, double *out) {
+  if (!ctx || k < 0 || (k > 0 && (!idx || !out))) return DG_EINVAL;
+  Ctx &c = ctx->c;
+  if (c.m < 1) return fail(ctx, DG_ESTATE, "no sources");
+  CK(cudaSetDevice(c.device), "set device");
+  const int np = c.np();
+  std::vector<int> cidx((size_t)c.geo.nx * c.geo.ny);
+  CK(cudaMemcpyAsync(cidx.data(), c.geo.d_cidx, cidx.size() * sizeof(int), cudaMemcpyDeviceToHost, c.stream),
+     "index copy");
+  CK(cudaStreamSynchronize(c.stream), "index copy");
+  std::vector<char> tmp((size_t)np * c.esize());
+  for (int q = 0; q < k; ++q) {
+    const int s = idx[3 * q], ex = idx[3 * q + 1], ey = idx[3 * q + 2];
+    if (s < 0 || s >= c.m || ex < 0 || ex >= c.geo.nx || ey < 0 || ey >= c.geo.ny)
+      return fail(ctx, DG_EINVAL, "element index out of range");
+    const int a = cidx[(size_t)ey * c.geo.nx + ex];
+    double *o = out + (size_t)q * np;
+    if (a < 0) {
+      for (int t = 0; t < np; ++t) o[t] = 0.0;
+      continue;
+    }
+    const char *src = (const char *)state_array(c, 0) + ((size_t)s * c.field_elems() + (size_t)a * np) * c.esize();
+    CK(cudaMemcpyAsync(tmp.data(), src, tmp.size(), cudaMemcpyDeviceToHost, c.stream), "element copy");
+    CK(cudaStreamSynchronize(c.stream), "element copy");
+    for (int t = 0; t < np; ++t)
+      o[t] = c.cfg.precision == DG_FP64 ? ((const double *)tmp.data())[t] : (double)((const float *)tmp.data())[t];
+  }
+  return DG_OK;
+}
+
+// Snapshot layout: 8 x uint64 header {magic, precision, p, m, n_active,
+// steps, bits of t, payload bytes}, m x 2 start points, m x 7 start moments,
+// then m x n_active x Np values of U (state precision, compact order).
+int dg_state_size(dg_ctx *ctx, size_t *bytes) {
+  if (!ctx || !bytes) return DG_EINVAL;
+  const Ctx &c = ctx->c;
+  if (c.m < 1) return fail(ctx, DG_ESTATE, "no sources");
+  *bytes = 64 + (size_t)c.m * 16 + (size_t)c.m * kMomFields * 8 +
+           (size_t)c.m * c.geo.n_active * c.np() * c.esize();
+  return DG_OK;
+}
+
+int dg_get_state(dg_ctx *ctx, void *host, size_t bytes) {
+  size_t need = 0;
+  int r = dg_state_size(ctx, &need);
+  if (r != DG_OK) return r;
+  if (!host || bytes < need) return fail(ctx, DG_EINVAL, "snapshot buffer too small");
+  Ctx &c = ctx->c;
+  CK(cudaSetDevice(c.device), "set device");
+  uint64_t hdr[8];
+  double tt = c.t;
+  std::memcpy(&hdr[6], &tt, 8);
+  hdr[0] = kStateMagic; hdr[1] = (uint64_t)c.cfg.precision; hdr[2] = (uint64_t)c.cfg.p;
+  hdr[3] = (uint64_t)c.m; hdr[4] = (uint64_t)c.geo.n_active; hdr[5] = (uint64_t)c.steps;
+  hdr[7] = need;
+  char *p = (char *)host;
+  std::memcpy(p, hdr, 64);
+  std::memcpy(p + 64, c.src.data(), (size_t)c.m * 16);
+  char *pm = p + 64 + (size_t)c.m * 16;
+  CK(cudaMemcpyAsync(pm, c.d_mom0, (size_t)c.m * kMomFields * 8, cudaMemcpyDeviceToHost, c.stream), "snapshot");
+  char *pu = pm + (size_t)c.m * kMomFields * 8;
+  const size_t row = (size_t)c.geo.n_active * c.np() * c.esize();
+  for (int s = 0; s < c.m; ++s)
+    CK(cudaMemcpyAsync(pu + s * row, (char *)state_array(c, 0) + (size_t)s * c.field_elems() * c.esize(), row,
+                       cudaMemcpyDeviceToHost, c.stream), "snapshot");
+  CK(cudaStreamSynchronize(c.stream), "snapshot");
+  return DG_OK;
+}
+
+int dg_set_state(dg_ctx *ctx, const void *host, size_t bytes) {
+  if (!ctx || !host || bytes < 64) return DG_EINVAL;
+  Ctx &c = ctx->c;
+  if (!c.have_geo) return fail(ctx, DG_ESTATE, "dg_set_state before a geometry");
+  uint64_t hdr[8];
+  std::memcpy(hdr, host, 64);
+  if (hdr[0] != kStateMagic) return fail(ctx, DG_EINVAL, "not a snapshot");
+  if (hdr[1] != (uint64_t)c.cfg.precision || hdr[2] != (uint64_t)c.cfg.p || hdr[4] != (uint64_t)c.geo.n_active)
+    return fail(ctx, DG_EINVAL, "snapshot does not match the context (precision, order or mesh)");
+  if (hdr[7] > bytes || hdr[3] < 1 || hdr[3] > 65535) return fail(ctx, DG_EINVAL, "truncated snapshot");
+  const int m = (int)hdr[3];
+  const char *p = (const char *)host;
+  std::vector<double> xy(2 * (size_t)m);
+  std::memcpy(xy.data(), p + 64, (size_t)m * 16);
+  int r = dg_set_sources(ctx, xy.data(), m);
+  if (r != DG_OK) return r;
+  const char *pm = p + 64 + (size_t)m * 16;
+  CK(cudaMemcpyAsync(c.d_mom0, pm, (size_t)m * kMomFields * 8, cudaMemcpyHostToDevice, c.stream), "restore");
+  const char *pu = pm + (size_t)m * kMomFields * 8;
+  const size_t row = (size_t)c.geo.n_active * c.np() * c.esize();
+  for (int s = 0; s < m; ++s)
+    CK(cudaMemcpyAsync((char *)state_array(c, 0) + (size_t)s * c.field_elems() * c.esize(), pu + s * row, row,
+                       cudaMemcpyHostToDevice, c.stream), "restore");
+  CK(cudaStreamSynchronize(c.stream), "restore");
+  std::memcpy(&c.t, &hdr[6], 8);
+  c.steps = (long long)hdr[5];
+  return DG_OK;
+}
+
+int dg_state_bytes(dg_ctx *ctx, int m, size_t *bytes) {
+  if (!ctx || !bytes || m < 1) return DG_EINVAL;
+  if (!ctx->c.have_geo) return fail(ctx, DG_ESTATE, "no geometry");
+  *bytes = state_bytes_for(ctx->c, m);
+  return DG_OK;
+}
+
+int dg_bind_state(dg_ctx *ctx, void *device_ptr, size_t bytes) {
+  if (!ctx) return DG_EINVAL;
+  if (device_ptr && ((uintptr_t)device_ptr % 256) != 0) return fail(ctx, DG_EINVAL, "state buffer must be 256-byte aligned");
+  Ctx &c = ctx->c;
+  CK(cudaSetDevice(c.device), "set device");
+  free_state(c);
+  c.bound_ptr = device_ptr;
+  c.bound_bytes = device_ptr ? bytes : 0;
+  return DG_OK;
+}
+
+}  // extern "C"

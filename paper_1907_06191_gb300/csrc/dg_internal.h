@@ -1,0 +1,142 @@
+// dg_internal.h -- internal types of the dgsigma library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/dgsigma.h"
+
+namespace dg {
+
+constexpr int kMaxP = 5;
+constexpr int kMaxN = kMaxP + 1;
+constexpr int kBlock = 256;         // threads per block of the element kernels
+constexpr int kTile = 16;           // element ordering: 16 x 16 tiles, row-major inside
+constexpr int kMomBlocks = 608;     // fixed grid of the moment reduction (4 x 152 SMs)
+constexpr int kMomFields = 7;       // M0, Mx, My, Mxx, Mxy, Myy, |u| mass
+
+// Face codes in the neighbour table (>= 0: neighbour element index).
+constexpr int kWall = -1;
+constexpr int kEdge = -2;
+
+// GLL tables of order p, computed on the host in FP64.
+struct Gll {
+  int p = 0;
+  double xi[kMaxN], w[kMaxN];
+  double D[kMaxN * kMaxN];   // D[a*n + i] = l_i'(xi_a)
+  double D2[kMaxN * kMaxN];  // (D D)[a*n + i]
+};
+bool gll_tables(int p, Gll *g);
+double rk3_real_axis_limit();
+
+// Operator scalars of one stage launch.  out = alpha u0 + beta u + gamma R,
+// where L u = (k / J^2) R.
+template <typename T>
+struct StageCoef {
+  T alpha, beta, gamma;
+  T pen;     // eta (p+1)^2 / 2
+  int wallA; // paper wall mode
+};
+
+// Tables by value in the kernel parameter space (constant bank).
+template <typename T, int P>
+struct StageTab {
+  T D[(P + 1) * (P + 1)];
+  T D2[(P + 1) * (P + 1)];
+  T inv_w;  // 1 / w_0 = 1 / w_p
+};
+
+// Device geometry of one domain.
+struct Geometry {
+  int nx = 0, ny = 0;
+  double h = 0, x0 = 0, y0 = 0;
+  long long n_active = 0;
+  long long n_pad = 0;     // n_active rounded up to 32 (per-source stride in elements)
+  uint8_t *d_mask = nullptr;    // [ny*nx]
+  int *d_cidx = nullptr;        // [ny*nx] compact index or -1
+  int4 *d_nb = nullptr;         // [n_active] E, W, N, S
+  int2 *d_exy = nullptr;        // [n_active] element coordinates
+  std::vector<uint8_t> h_mask;  // host copy of d_mask
+};
+
+struct Ctx {
+  dg_config cfg{};
+  int device = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  std::string last_error;
+  Gll gll;
+  Geometry geo;
+  bool have_geo = false;
+
+  // time-step bound
+  bool have_rho = false;
+  double rho = 0, dt_max = 0;
+
+  // sources and state
+  int m = 0;
+  double t = 0;
+  long long steps = 0;
+  std::vector<double> src;        // [m][2]
+  double *d_src = nullptr;        // [m][2]
+  void *d_state = nullptr;        // 3 arrays of m * n_pad * Np elements
+  size_t state_bytes = 0;
+  bool state_owned = true;
+  void *bound_ptr = nullptr;
+  size_t bound_bytes = 0;
+  double *d_mom = nullptr;        // [m][7] current moments
+  double *d_mom0 = nullptr;       // [m][7] start moments
+  double *d_part = nullptr;       // [m][kMomBlocks][7] partial sums
+  double *d_out = nullptr;        // [8] covariance results
+  size_t part_elems = 0;
+
+  // graph of a chunk of steps
+  cudaGraphExec_t graph = nullptr;
+  double graph_dt = 0;
+  int graph_steps = 0;
+  cudaStream_t graph_stream = nullptr;
+
+  int np() const { return (cfg.p + 1) * (cfg.p + 1); }
+  size_t esize() const { return cfg.precision == DG_FP64 ? 8 : 4; }
+  size_t field_elems() const { return (size_t)geo.n_pad * np(); }  // one source
+};
+
+// ---- launchers (defined in the .cu files) ----
+// One stage over all m densities: out = alpha u0 + beta u + gamma R(u).
+cudaError_t launch_stage_f64(int p, const double *u, const double *u0, double *out,
+                             const int4 *nb, long long nA, long long stride, int m,
+                             const Gll &g, const StageCoef<double> &c, cudaStream_t s);
+cudaError_t launch_stage_f32(int p, const float *u, const float *u0, float *out,
+                             const int4 *nb, long long nA, long long stride, int m,
+                             const Gll &g, const StageCoef<float> &c, cudaStream_t s);
+
+// Geometry construction.
+cudaError_t build_mask_disks(const double *d_cx, const double *d_cy, const double *d_r,
+                             int nd, double L, int n_cell, int tiles, uint8_t *d_mask,
+                             cudaStream_t s);
+// Compaction in tile order and the neighbour table; fills geo (allocates).
+int build_connectivity(Geometry &geo, int periodic, cudaStream_t s, std::string &err);
+void free_geometry(Geometry &geo);
+
+// Densities, moments, covariance.
+cudaError_t launch_init_sources(const Ctx &c, void *u, cudaStream_t s);
+cudaError_t launch_moments(const Ctx &c, const void *u, double *d_part, double *d_mom,
+                           cudaStream_t s);
+cudaError_t launch_covariance(const double *d_mom, const double *d_mom0, int m,
+                              double *d_out, cudaStream_t s);
+cudaError_t launch_nodes_to_dense(const Ctx &c, const void *u, double *d_dense,
+                                  cudaStream_t s);
+cudaError_t launch_dense_to_nodes(const Ctx &c, const double *d_dense, void *u,
+                                  cudaStream_t s);
+// Power iteration helpers (FP64, one density).
+cudaError_t launch_random_field(const Ctx &c, double *v, unsigned long long seed,
+                                cudaStream_t s);
+cudaError_t launch_wnorm2(const Ctx &c, const double *v, double *d_part, double *d_res,
+                          cudaStream_t s);
+cudaError_t launch_scale_by_rnorm(const Ctx &c, const double *in, const double *d_res,
+                                  double *out, cudaStream_t s);
+
+}  // namespace dg

@@ -1,0 +1,361 @@
+// dg_reduce.cu -- start densities, FP64 moment reduction, covariance of the
+// mixture (Sec. 4.1), node layout conversion, power-iteration helpers.
+#include <cmath>
+
+#include "dg_internal.h"
+
+namespace dg {
+
+struct NodeGeo {
+  double xi[kMaxN];
+  double w[kMaxN];
+  double h, x0, y0;
+};
+
+static NodeGeo node_geo(const Ctx &c) {
+  NodeGeo g;
+  for (int i = 0; i <= c.cfg.p; ++i) {
+    g.xi[i] = c.gll.xi[i];
+    g.w[i] = c.gll.w[i];
+  }
+  g.h = c.geo.h;
+  g.x0 = c.geo.x0;
+  g.y0 = c.geo.y0;
+  return g;
+}
+
+// ---- start densities -------------------------------------------------------
+// Normalised Gaussian of width sigma0 about each start point (stand-in for the
+// Dirac data of Sec. 4.1), interpolated at the GLL nodes; FP64 arithmetic,
+// stored in the state precision.  grid (ceil(nA/256), m).
+template <typename T, int P>
+__global__ void k_init(const int2 *__restrict__ exy, long long nA, long long stride,
+                       const double *__restrict__ src, double sigma0, const NodeGeo g,
+                       T *__restrict__ u) {
+  constexpr int n = P + 1, NP = n * n;
+  const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nA) return;
+  const int s = blockIdx.y;
+  const double xs = src[2 * s], ys = src[2 * s + 1];
+  const int2 e = exy[a];
+  const double c = 1.0 / (2.0 * M_PI * sigma0 * sigma0);
+  const double inv2s2 = 1.0 / (2.0 * sigma0 * sigma0);
+  T *out = u + ((size_t)s * stride + a) * NP;
+#pragma unroll
+  for (int j = 0; j < n; ++j)
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+      const double x = g.x0 + (e.x + 0.5) * g.h + 0.5 * g.h * g.xi[i];
+      const double y = g.y0 + (e.y + 0.5) * g.h + 0.5 * g.h * g.xi[j];
+      const double dx = x - xs, dy = y - ys;
+      out[j * n + i] = (T)(c * exp(-(dx * dx + dy * dy) * inv2s2));
+    }
+}
+
+// ---- moments -----------------------------------------------------------------
+// Per density: M0, Mx, My, Mxx, Mxy, Myy about the start point and the L1 mass
+// sum |u| W, with W = J^2 w_i w_j (GLL nodal quadrature, Sec. 4.1).  Pass 1:
+// a fixed grid of kMomBlocks blocks per density, each summing a fixed
+// element stride, block-reduced in a fixed order -> part[s][block][7].
+// Pass 2: one block per density sums the partials in a fixed order.  The
+// result does not depend on scheduling.
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum of kMomFields values; result valid in thread 0.  blockDim = 256.
+__device__ __forceinline__ void block_sum7(double (&v)[kMomFields]) {
+  __shared__ double sh[kMomFields][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int f = 0; f < kMomFields; ++f) {
+    v[f] = warp_sum_d(v[f]);
+    if (lane == 0) sh[f][wid] = v[f];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int f = 0; f < kMomFields; ++f) {
+      double s = 0.0;
+      for (int w = 0; w < 8; ++w) s += sh[f][w];
+      v[f] = s;
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(256)
+    k_moments(const int2 *__restrict__ exy, long long nA, long long stride,
+              const double *__restrict__ src, const NodeGeo g, const T *__restrict__ u,
+              double *__restrict__ part) {
+  constexpr int n = P + 1, NP = n * n;
+  const int s = blockIdx.y;
+  const double xs = src[2 * s], ys = src[2 * s + 1];
+  const double J = 0.5 * g.h;
+  double acc[kMomFields] = {0, 0, 0, 0, 0, 0, 0};
+  const T *U = u + (size_t)s * stride * NP;
+  for (long long a = (long long)blockIdx.x * 256 + threadIdx.x; a < nA;
+       a += (long long)gridDim.x * 256) {
+    const int2 e = exy[a];
+    const T *ue = U + (size_t)a * NP;
+#pragma unroll
+    for (int j = 0; j < n; ++j) {
+      const double y = g.y0 + (e.y + 0.5) * g.h + J * g.xi[j] - ys;
+#pragma unroll
+      for (int i = 0; i < n; ++i) {
+        const double x = g.x0 + (e.x + 0.5) * g.h + J * g.xi[i] - xs;
+        const double wu = J * J * g.w[i] * g.w[j] * (double)ue[j * n + i];
+        acc[0] += wu;
+        acc[1] += wu * x;
+        acc[2] += wu * y;
+        acc[3] += wu * x * x;
+        acc[4] += wu * x * y;
+        acc[5] += wu * y * y;
+        acc[6] += fabs(wu);
+      }
+    }
+  }
+  block_sum7(acc);
+  if (threadIdx.x == 0) {
+    double *o = part + ((size_t)s * gridDim.x + blockIdx.x) * kMomFields;
+#pragma unroll
+    for (int f = 0; f < kMomFields; ++f) o[f] = acc[f];
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    k_moments_final(const double *__restrict__ part, int nblk, double *__restrict__ mom) {
+  const int s = blockIdx.x;
+  double acc[kMomFields] = {0, 0, 0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < nblk; b += 256) {
+    const double *p = part + ((size_t)s * nblk + b) * kMomFields;
+#pragma unroll
+    for (int f = 0; f < kMomFields; ++f) acc[f] += p[f];
+  }
+  block_sum7(acc);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int f = 0; f < kMomFields; ++f) mom[(size_t)s * kMomFields + f] = acc[f];
+  }
+}
+
+// ---- covariance (Sec. 4.1) ---------------------------------------------------
+// Each density normalised by its mass, mixed with weights 1/m; moment-matched
+// Gaussian: mu = mean M1/M0, Sigma_mix = mean M2/M0 - mu mu^T; reported
+// Sigma = Sigma_mix(t) - Sigma_mix(0).  One thread, sources in order.
+// out = {Sxx, Sxy, Syy, mux, muy}.
+__global__ void k_covariance(const double *__restrict__ mom, const double *__restrict__ mom0,
+                             int m, double *__restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double r[2][5];
+  for (int k = 0; k < 2; ++k) {
+    const double *M = k == 0 ? mom : mom0;
+    double mx = 0, my = 0, sxx = 0, sxy = 0, syy = 0;
+    for (int s = 0; s < m; ++s) {
+      const double *q = M + (size_t)s * kMomFields;
+      const double inv = 1.0 / q[0];
+      mx += q[1] * inv;
+      my += q[2] * inv;
+      sxx += q[3] * inv;
+      sxy += q[4] * inv;
+      syy += q[5] * inv;
+    }
+    const double im = 1.0 / (double)m;
+    mx *= im; my *= im; sxx *= im; sxy *= im; syy *= im;
+    r[k][0] = sxx - mx * mx;
+    r[k][1] = sxy - mx * my;
+    r[k][2] = syy - my * my;
+    r[k][3] = mx;
+    r[k][4] = my;
+  }
+  out[0] = r[0][0] - r[1][0];
+  out[1] = r[0][1] - r[1][1];
+  out[2] = r[0][2] - r[1][2];
+  out[3] = r[0][3];
+  out[4] = r[0][4];
+}
+
+// ---- node layout conversion ------------------------------------------------
+template <typename T, int P>
+__global__ void k_to_dense(const int2 *__restrict__ exy, long long nA, long long stride,
+                           int nx, int ny, const T *__restrict__ u, double *__restrict__ d) {
+  constexpr int NP = (P + 1) * (P + 1);
+  const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nA) return;
+  const int s = blockIdx.y;
+  const int2 e = exy[a];
+  const T *src = u + ((size_t)s * stride + a) * NP;
+  double *dst = d + (((size_t)s * ny + e.y) * nx + e.x) * NP;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) dst[k] = (double)src[k];
+}
+
+template <typename T, int P>
+__global__ void k_from_dense(const int2 *__restrict__ exy, long long nA, long long stride,
+                             int nx, int ny, const double *__restrict__ d, T *__restrict__ u) {
+  constexpr int NP = (P + 1) * (P + 1);
+  const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nA) return;
+  const int s = blockIdx.y;
+  const int2 e = exy[a];
+  T *dst = u + ((size_t)s * stride + a) * NP;
+  const double *src = d + (((size_t)s * ny + e.y) * nx + e.x) * NP;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) dst[k] = (T)src[k];
+}
+
+// ---- power iteration helpers (FP64, one density) ----------------------------
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+__global__ void k_random_field(long long nvals, unsigned long long seed, double *__restrict__ v) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nvals) return;
+  v[t] = (double)(splitmix64(seed + (unsigned long long)t) >> 11) * 0x1.0p-53 - 0.5;
+}
+
+template <int P>
+__global__ void __launch_bounds__(256)
+    k_wnorm2(long long nA, const double *__restrict__ v, double J2w0, const NodeGeo g,
+             double *__restrict__ part) {
+  constexpr int n = P + 1, NP = n * n;
+  double acc[kMomFields] = {0, 0, 0, 0, 0, 0, 0};
+  for (long long a = (long long)blockIdx.x * 256 + threadIdx.x; a < nA;
+       a += (long long)gridDim.x * 256) {
+    const double *ve = v + (size_t)a * NP;
+#pragma unroll
+    for (int j = 0; j < n; ++j)
+#pragma unroll
+      for (int i = 0; i < n; ++i) acc[0] += g.w[i] * g.w[j] * ve[j * n + i] * ve[j * n + i];
+  }
+  (void)J2w0;
+  block_sum7(acc);
+  if (threadIdx.x == 0) {
+    double *o = part + (size_t)blockIdx.x * kMomFields;
+#pragma unroll
+    for (int f = 0; f < kMomFields; ++f) o[f] = acc[f];
+  }
+}
+
+__global__ void k_scale_rnorm(long long nvals, const double *__restrict__ in,
+                              const double *__restrict__ res, double *__restrict__ out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nvals) return;
+  out[t] = in[t] / sqrt(res[0]);
+}
+
+// ---- launchers ----------------------------------------------------------------
+#define DG_P_SWITCH(p, CALL)          \
+  switch (p) {                        \
+    case 1: { constexpr int PP = 1; CALL; } break; \
+    case 2: { constexpr int PP = 2; CALL; } break; \
+    case 3: { constexpr int PP = 3; CALL; } break; \
+    case 4: { constexpr int PP = 4; CALL; } break; \
+    case 5: { constexpr int PP = 5; CALL; } break; \
+    default: return cudaErrorInvalidValue;         \
+  }
+
+cudaError_t launch_init_sources(const Ctx &c, void *u, cudaStream_t s) {
+  const long long nA = c.geo.n_active;
+  const dim3 grid((unsigned)((nA + 255) / 256), (unsigned)c.m);
+  const NodeGeo g = node_geo(c);
+  if (c.cfg.precision == DG_FP64) {
+    DG_P_SWITCH(c.cfg.p, (k_init<double, PP><<<grid, 256, 0, s>>>(
+                             c.geo.d_exy, nA, c.geo.n_pad, c.d_src, c.cfg.sigma0, g,
+                             (double *)u)));
+  } else {
+    DG_P_SWITCH(c.cfg.p, (k_init<float, PP><<<grid, 256, 0, s>>>(
+                             c.geo.d_exy, nA, c.geo.n_pad, c.d_src, c.cfg.sigma0, g,
+                             (float *)u)));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const Ctx &c, const void *u, double *d_part, double *d_mom,
+                           cudaStream_t s) {
+  const long long nA = c.geo.n_active;
+  const dim3 grid(kMomBlocks, (unsigned)c.m);
+  const NodeGeo g = node_geo(c);
+  if (c.cfg.precision == DG_FP64) {
+    DG_P_SWITCH(c.cfg.p, (k_moments<double, PP><<<grid, 256, 0, s>>>(
+                             c.geo.d_exy, nA, c.geo.n_pad, c.d_src, g, (const double *)u,
+                             d_part)));
+  } else {
+    DG_P_SWITCH(c.cfg.p, (k_moments<float, PP><<<grid, 256, 0, s>>>(
+                             c.geo.d_exy, nA, c.geo.n_pad, c.d_src, g, (const float *)u,
+                             d_part)));
+  }
+  k_moments_final<<<c.m, 256, 0, s>>>(d_part, kMomBlocks, d_mom);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_covariance(const double *d_mom, const double *d_mom0, int m,
+                              double *d_out, cudaStream_t s) {
+  k_covariance<<<1, 32, 0, s>>>(d_mom, d_mom0, m, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nodes_to_dense(const Ctx &c, const void *u, double *d_dense,
+                                  cudaStream_t s) {
+  const long long nA = c.geo.n_active;
+  const dim3 grid((unsigned)((nA + 255) / 256), (unsigned)c.m);
+  if (c.cfg.precision == DG_FP64) {
+    DG_P_SWITCH(c.cfg.p, (k_to_dense<double, PP><<<grid, 256, 0, s>>>(
+                             c.geo.d_exy, nA, c.geo.n_pad, c.geo.nx, c.geo.ny,
+                             (const double *)u, d_dense)));
+  } else {
+    DG_P_SWITCH(c.cfg.p, (k_to_dense<float, PP><<<grid, 256, 0, s>>>(
+                             c.geo.d_exy, nA, c.geo.n_pad, c.geo.nx, c.geo.ny,
+                             (const float *)u, d_dense)));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dense_to_nodes(const Ctx &c, const double *d_dense, void *u,
+                                  cudaStream_t s) {
+  const long long nA = c.geo.n_active;
+  const dim3 grid((unsigned)((nA + 255) / 256), (unsigned)c.m);
+  if (c.cfg.precision == DG_FP64) {
+    DG_P_SWITCH(c.cfg.p, (k_from_dense<double, PP><<<grid, 256, 0, s>>>(
+                             c.geo.d_exy, nA, c.geo.n_pad, c.geo.nx, c.geo.ny, d_dense,
+                             (double *)u)));
+  } else {
+    DG_P_SWITCH(c.cfg.p, (k_from_dense<float, PP><<<grid, 256, 0, s>>>(
+                             c.geo.d_exy, nA, c.geo.n_pad, c.geo.nx, c.geo.ny, d_dense,
+                             (float *)u)));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_random_field(const Ctx &c, double *v, unsigned long long seed,
+                                cudaStream_t s) {
+  const long long nv = c.geo.n_active * c.np();
+  k_random_field<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(nv, seed, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wnorm2(const Ctx &c, const double *v, double *d_part, double *d_res,
+                          cudaStream_t s) {
+  const NodeGeo g = node_geo(c);
+  DG_P_SWITCH(c.cfg.p, (k_wnorm2<PP><<<kMomBlocks, 256, 0, s>>>(c.geo.n_active, v, 0.0, g,
+                                                                 d_part)));
+  k_moments_final<<<1, 256, 0, s>>>(d_part, kMomBlocks, d_res);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_by_rnorm(const Ctx &c, const double *in, const double *d_res,
+                                  double *out, cudaStream_t s) {
+  const long long nv = c.geo.n_active * c.np();
+  k_scale_rnorm<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(nv, in, d_res, out);
+  return cudaGetLastError();
+}
+
+}  // namespace dg

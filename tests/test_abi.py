@@ -1,0 +1,61 @@
+"""The C ABI library builds, loads and exports every symbol that
+include/dgsigma.h declares; host-only calls behave.  No device compute."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _header_functions():
+    src = open(os.path.join(ROOT, "include", "dgsigma.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dg_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1907_06191_gb300 import _build
+    _build.build()
+    import paper_1907_06191_gb300 as dg
+    return dg.lib()
+
+
+def test_every_declared_symbol_is_exported(L):
+    import paper_1907_06191_gb300 as dg
+    names = _header_functions()
+    assert len(names) >= 25
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(dg.EXPORTS) == names
+
+
+def test_host_only_calls(L):
+    import paper_1907_06191_gb300 as dg
+    assert L.dg_strerror(dg.DG_OK) == b"ok"
+    assert L.dg_strerror(dg.DG_EUNSTABLE) == b"unstable time step"
+    assert L.dg_strerror(99) == b"unknown status"
+    cfg = dg.default_config()
+    assert (cfg.p, cfg.precision, cfg.D, cfg.sigma0, cfg.cfl_safety) == (3, dg.DG_FP64, 2.0, 0.2, 0.9)
+    assert L.dg_last_error(None) == b""
+    L.dg_destroy(None)
+    h = ctypes.c_void_p()
+    bad = dg.default_config(p=9)
+    assert L.dg_create(ctypes.byref(bad), ctypes.byref(h)) == dg.DG_EINVAL
+    bad = dg.default_config(cfl_safety=1.5)
+    assert L.dg_create(ctypes.byref(bad), ctypes.byref(h)) == dg.DG_EINVAL
+    assert L.dg_create(None, ctypes.byref(h)) == dg.DG_EINVAL
+    assert L.dg_step(None, 1, 1.0) == dg.DG_EINVAL
+
+
+def test_no_device_is_an_error_not_a_crash(L):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    import paper_1907_06191_gb300 as dg
+    h = ctypes.c_void_p()
+    cfg = dg.default_config()
+    assert L.dg_create(ctypes.byref(cfg), ctypes.byref(h)) == dg.DG_ECUDA
+    assert not h.value

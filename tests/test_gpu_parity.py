@@ -1,0 +1,365 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Every expected value comes from ``oracle/``; inputs come from ``dginputs``
+or are seeded here.  Tolerances: FP64 path relative 1e-10 on nodes and
+Sigma (1e-12 on a single operator application), FP32 path 1e-5 on Sigma
+and node values relative to the field maximum.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import dginputs
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1907_06191_gb300 as dg  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1907_06191_gb300 import _build
+    _build.build()
+    O.build()
+
+
+PREC = {"f64": dg.DG_FP64, "f32": dg.DG_FP32}
+
+
+def _solver(p, prec, **kw):
+    return dg.DGSolver(p=p, precision=PREC[prec], device=0, **kw)
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _random_mesh(seed, nx, ny, frac=0.25):
+    rng = np.random.default_rng(seed)
+    act = (rng.random((ny, nx)) > frac).astype(np.uint8)
+    return act, rng
+
+
+def _sources_in(act, rng, m, h, x0, y0, margin=0):
+    ny, nx = act.shape
+    out = []
+    while len(out) < m:
+        ex = int(rng.integers(margin, nx - margin))
+        ey = int(rng.integers(margin, ny - margin))
+        if act[ey, ex]:
+            out.append((x0 + (ex + rng.uniform(0.1, 0.9)) * h,
+                        y0 + (ey + rng.uniform(0.1, 0.9)) * h))
+    return np.array(out)
+
+
+# --------------------------------------------------------------------------
+# a1: element mask from disks -- bit exact
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("which", ["small", "cell40"])
+def test_mask_bit_exact(which):
+    w = dginputs.workload_small(0) if which == "small" else dginputs.workload_cell40(0, m=1)
+    tiles = w.tiles if which == "small" else 1
+    with _solver(w.p, "f32", D=w.D, sigma0=w.sigma0) as s:
+        s.set_geometry_disks(w.disks.cx, w.disks.cy, w.disks.r, w.L, w.n_cell, tiles)
+        got = s.get_mask()
+        inf = s.info()
+    ref = O.window_mask(O.mask_disks(w.L, w.n_cell, w.disks.cx, w.disks.cy, w.disks.r), tiles)
+    assert got.shape == ref.shape
+    assert np.array_equal(got, ref)
+    assert inf.n_active == int(ref.sum())
+    assert abs(inf.x0 + (tiles // 2) * w.L) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# a3 + a4: the operator L alone, against the oracle's two-pass strong form
+# --------------------------------------------------------------------------
+
+OP_CASES = [  # p, nx, ny, wall_mode, periodic, eta
+    (1, 37, 21, 0, False, 0.0), (2, 37, 21, 0, False, 0.0), (3, 37, 21, 0, False, 0.0),
+    (4, 19, 23, 0, False, 0.0), (5, 17, 18, 0, False, 0.0), (3, 37, 21, 1, False, 0.0),
+    (2, 33, 17, 0, True, 0.0), (3, 20, 35, 0, False, 1.0), (4, 21, 17, 1, True, 0.5),
+    (2, 1, 1, 0, True, 0.0), (3, 1, 40, 0, False, 0.0),
+]
+
+
+@pytest.mark.parametrize("case", OP_CASES)
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_operator_parity(case, prec):
+    p, nx, ny, mode, per, eta = case
+    act, rng = _random_mesh(100 + p + nx, nx, ny)
+    act[0, 0] = 1
+    h, x0, y0, k0 = 0.3, -2.0, 1.0, 1.7
+    mesh = O.Mesh(p=p, active=act, h=h, x0=x0, y0=y0, k0=k0, eta=eta, wall_mode=mode,
+                  periodic=per)
+    m = 2
+    u = rng.standard_normal((m,) + mesh.field_shape) * act[None, :, :, None, None]
+    with _solver(p, prec, D=k0, eta=eta, wall_mode=mode,
+                 boundary=dg.DG_BC_PERIODIC if per else dg.DG_BC_ABSORBING) as s:
+        s.set_geometry_mask(act, h, x0, y0)
+        s.set_sources(_sources_in(act, rng, m, h, x0, y0))
+        s.set_nodes(u)
+        s.apply_operator()
+        got = s.get_nodes()
+    for k in range(m):
+        ref = O.apply_L(mesh, u[k])
+        tol = 1e-12 if prec == "f64" else 2e-5
+        assert _rel(got[k], ref) < tol
+
+
+# --------------------------------------------------------------------------
+# a2 + a5: start densities and SSP-RK3 steps, node by node
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_rk3_steps_parity(p, prec):
+    act, rng = _random_mesh(7 + p, 40, 37, 0.3)
+    h, x0, y0, D, s0 = 0.2, 0.5, -3.0, 2.0, 0.25
+    mesh = O.Mesh(p=p, active=act, h=h, x0=x0, y0=y0, k0=D)
+    src = _sources_in(act, rng, 3, h, x0, y0, margin=8)
+    rho = O.power_rho(mesh)
+    nsteps, dt = 70, 0.85 * O.rk3_real_limit() / rho
+    with _solver(p, prec, D=D, sigma0=s0) as s:
+        s.set_geometry_mask(act, h, x0, y0)
+        s.set_sources(src)
+        u0 = s.get_nodes()
+        s.step(nsteps, dt)   # 64-step graph chunk + 6 direct steps
+        got = s.get_nodes()
+        s3, mu, mass = s.covariance()
+    tol = 1e-10 if prec == "f64" else 1e-5
+    fields0 = [O.init_gaussian(mesh, x, y, s0) for x, y in src]
+    fields = [O.rk3(mesh, f, nsteps, dt) for f in fields0]
+    for k in range(3):
+        assert _rel(u0[k], fields0[k]) < (1e-14 if prec == "f64" else 1e-7)
+        assert _rel(got[k], fields[k]) < tol
+    mom0 = np.array([O.moments(mesh, f, x, y) for f, (x, y) in zip(fields0, src)])
+    mom = np.array([O.moments(mesh, f, x, y) for f, (x, y) in zip(fields, src)])
+    s_ref, mu_ref, m_ref = O.aggregate(mom, mom0)
+    assert _rel(s3, s_ref) < tol
+    assert _rel(mass, m_ref) < tol
+
+
+# --------------------------------------------------------------------------
+# Full Sigma solve of the small cell workload (10 um cell, p=2, Delta=5 ms)
+# --------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def small_ref():
+    w = dginputs.workload_small(0)
+    cell = O.mask_disks(w.L, w.n_cell, w.disks.cx, w.disks.cy, w.disks.r)
+    act = O.window_mask(cell, w.tiles)
+    mesh = O.Mesh(p=w.p, active=act, h=w.h, x0=w.origin, y0=w.origin, k0=w.D)
+    rho = O.power_rho(mesh)
+    plan = O.step_plan(rho, w.deltas[0])
+    r = O.solve(mesh, w.sources, w.sigma0, w.deltas, nsteps=[plan[0]], dt=[plan[1]])
+    return w, mesh, rho, plan, r
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_small_cell_sigma_parity(small_ref, prec):
+    w, mesh, rho, (nsteps, dt), r = small_ref
+    with _solver(w.p, prec, D=w.D, sigma0=w.sigma0) as s:
+        s.set_geometry_disks(w.disks.cx, w.disks.cy, w.disks.r, w.L, w.n_cell, w.tiles)
+        s.set_sources(w.sources)
+        s.step(nsteps, dt)
+        s3, mu, mass = s.covariance()
+        mom = s.moments()
+        dt_gpu, rho_gpu = s.query_dt()
+    tol = 1e-10 if prec == "f64" else 1e-5
+    assert _rel(s3, r["sigma"][0]) < tol
+    assert _rel(mass, r["mass"][0]) < tol
+    assert _rel(mom, r["moments"][0]) < (1e-10 if prec == "f64" else 1e-4)
+    # the power iteration runs in FP64 on both paths, from different start vectors
+    assert abs(rho_gpu / rho - 1) < 5e-3
+    assert s3[0] > 0 and s3[0] * s3[2] > s3[1] ** 2
+
+
+def test_propagate_and_checkpoint_bitwise(small_ref):
+    w = small_ref[0]
+    kw = dict(D=w.D, sigma0=w.sigma0)
+    with _solver(w.p, "f64", **kw) as a:
+        a.set_geometry_disks(w.disks.cx, w.disks.cy, w.disks.r, w.L, w.n_cell, w.tiles)
+        a.set_sources(w.sources)
+        dt, _ = a.query_dt()
+        a.step(100, dt)
+        blob = a.get_state()
+        a.step(100, dt)
+        ref_nodes = a.get_nodes()
+        ref_sig = a.covariance()[0]
+    with _solver(w.p, "f64", **kw) as b:
+        b.set_geometry_disks(w.disks.cx, w.disks.cy, w.disks.r, w.L, w.n_cell, w.tiles)
+        b.set_state(blob)
+        assert b.info().steps == 100
+        b.step(100, dt)
+        assert np.array_equal(b.get_nodes(), ref_nodes)
+        assert np.array_equal(b.covariance()[0], ref_sig)
+
+
+# --------------------------------------------------------------------------
+# Paper pins through the GPU path
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec,p", [("f64", 2), ("f64", 4), ("f32", 2)])
+def test_free_diffusion_exact_gpu(prec, p):
+    """Sec. 4.2: Sigma = 2 T k I = 32.4 I for k = 0.45 um^2/ms, T = 36 ms."""
+    nel, side, s0 = (60, 120.0, 4.0) if p == 2 else (40, 160.0, 8.0)
+    act = np.ones((nel, nel), np.uint8)
+    with _solver(p, prec, D=0.45, sigma0=s0) as s:
+        s.set_geometry_mask(act, side / nel, -side / 2, -side / 2)
+        s.set_sources(np.array([[0.3 * side / nel, -0.2 * side / nel]]))
+        s.propagate_to(36.0)
+        s3, mu, mass = s.covariance()
+    tol = 1e-10 if prec == "f64" else 1e-5
+    assert abs(s3[0] / 32.4 - 1) < tol and abs(s3[2] / 32.4 - 1) < tol
+    assert abs(s3[1]) < tol * 32.4
+
+
+def test_paper_wall_mode_parity():
+    act, rng = _random_mesh(77, 30, 26, 0.3)
+    h, D = 0.25, 1.0
+    mesh = O.Mesh(p=3, active=act, h=h, k0=D, wall_mode=1)
+    src = _sources_in(act, rng, 2, h, 0.0, 0.0, margin=6)
+    rho = O.power_rho(mesh)
+    n, dt = 40, 0.5 * O.rk3_real_limit() / rho
+    with _solver(3, "f64", D=D, sigma0=0.3, wall_mode=dg.DG_WALL_PAPER) as s:
+        s.set_geometry_mask(act, h)
+        s.set_sources(src)
+        s.step(n, dt)
+        got = s.get_nodes()
+    for k, (x, y) in enumerate(src):
+        ref = O.rk3(mesh, O.init_gaussian(mesh, x, y, 0.3), n, dt)
+        assert _rel(got[k], ref) < 1e-10
+
+
+# --------------------------------------------------------------------------
+# Full-size cell40 workload (1792^2 window, 64 densities): sampled outputs
+# --------------------------------------------------------------------------
+
+def test_cell40_fullsize_sampled_parity():
+    """The 40 um cell workload at full size (7x7-cell window of 1792^2
+    elements, p=3, 64 densities) in the benchmark's launch configuration:
+    two FP64 steps, then sampled elements against the oracle run on a patch
+    around each (one stage reaches one element further, so a patch of
+    radius 3 x steps reproduces the centre element exactly)."""
+    w = dginputs.workload_cell40(0, m=64)
+    nsteps = 2
+    R = 3 * nsteps + 1
+    cell = O.mask_disks(w.L, w.n_cell, w.disks.cx, w.disks.cy, w.disks.r)
+    win = O.window_mask(cell, w.tiles)
+    patch = O.Mesh(p=w.p, active=win[:96, :96].copy(), h=w.h, k0=w.D)
+    rho_patch = O.power_rho(patch, 300)
+    dt = 0.8 * O.rk3_real_limit() / rho_patch
+    rng = np.random.default_rng(5)
+    picks = []
+    while len(picks) < 16:
+        k = int(rng.integers(0, w.sources.shape[0]))
+        xs, ys = w.sources[k]
+        ex = int((xs - w.origin) / w.h) + int(rng.integers(-3, 4))
+        ey = int((ys - w.origin) / w.h) + int(rng.integers(-3, 4))
+        if win[ey, ex]:
+            picks.append((k, ex, ey))
+    with _solver(w.p, "f64", D=w.D, sigma0=w.sigma0) as s:
+        s.set_geometry_disks(w.disks.cx, w.disks.cy, w.disks.r, w.L, w.n_cell, w.tiles)
+        assert np.array_equal(s.get_mask(), win)
+        s.set_sources(w.sources)
+        _, rho_gpu = s.query_dt()
+        s.step(nsteps, dt)
+        got = s.get_elements(picks)
+        mom = s.moments()
+    for q, (k, ex, ey) in enumerate(picks):
+        xs, ys = w.sources[k]
+        sub = win[ey - R:ey + R + 1, ex - R:ex + R + 1].copy()
+        pm = O.Mesh(p=w.p, active=sub, h=w.h, x0=w.origin + (ex - R) * w.h,
+                    y0=w.origin + (ey - R) * w.h, k0=w.D)
+        ref = O.rk3(pm, O.init_gaussian(pm, xs, ys, w.sigma0), nsteps, dt)[R, R]
+        assert np.abs(got[q] - ref).max() <= 1e-10 * np.abs(ref).max()
+    assert np.all(mom[:, 0] > 0.5)
+    # the whole window's bound is at least the patch's
+    assert rho_gpu > 0.98 * rho_patch
+
+
+# --------------------------------------------------------------------------
+# Edge cases and error handling
+# --------------------------------------------------------------------------
+
+def test_many_sources_and_isolated_element():
+    act = np.zeros((9, 9), np.uint8)
+    act[4, 4] = 1                       # a single element walled on all sides
+    act[0:3, 0:9] = 1
+    mesh = O.Mesh(p=2, active=act, h=0.5, k0=1.0)
+    rng = np.random.default_rng(3)
+    src = _sources_in(act, rng, 300, 0.5, 0.0, 0.0)
+    src[0] = (4.5 * 0.5, 4.5 * 0.5)
+    rho = O.power_rho(mesh)
+    dt = 0.8 * O.rk3_real_limit() / rho
+    with _solver(2, "f64", D=1.0, sigma0=0.3) as s:
+        s.set_geometry_mask(act, 0.5)
+        s.set_sources(src)
+        s.step(5, dt)
+        got = s.get_nodes()
+        mass = s.covariance()[2]
+    for k in (0, 1, 150, 299):
+        ref = O.rk3(mesh, O.init_gaussian(mesh, *src[k], 0.3), 5, dt)
+        assert _rel(got[k], ref) < 1e-10
+    m_iso = O.moments(mesh, O.init_gaussian(mesh, *src[0], 0.3), 0, 0)[0]
+    assert abs(mass[0] / m_iso - 1) < 1e-13
+
+
+def test_unstable_step_is_reported():
+    """One power iteration underestimates rho, so dt exceeds the RK3 bound;
+    the host-side growth check reports it (no device fault involved)."""
+    act = np.ones((24, 24), np.uint8)
+    with _solver(3, "f64", D=2.0, sigma0=0.3, power_iters=1, cfl_safety=1.0) as s:
+        s.set_geometry_mask(act, 0.2)
+        s.set_sources(np.array([[2.41, 2.43]]))
+        with pytest.raises(dg.DgError) as ei:
+            s.propagate_to(5.0)
+        assert ei.value.code == dg.DG_EUNSTABLE
+
+
+def test_argument_errors():
+    act = np.ones((8, 8), np.uint8)
+    act[3, 3] = 0
+    with _solver(2, "f64") as s:
+        with pytest.raises(dg.DgError) as ei:
+            s.step(1, 1e-3)
+        assert ei.value.code == dg.DG_ESTATE
+        s.set_geometry_mask(act, 1.0)
+        with pytest.raises(dg.DgError) as ei:
+            s.set_sources(np.array([[3.5, 3.5]]))       # inside the removed element
+        assert ei.value.code == dg.DG_EINVAL
+        with pytest.raises(dg.DgError) as ei:
+            s.set_sources(np.array([[-0.5, 3.5]]))      # outside the domain
+        assert ei.value.code == dg.DG_EINVAL
+        with pytest.raises(dg.DgError) as ei:
+            s.set_geometry_mask(np.zeros((4, 4), np.uint8), 1.0)
+        assert ei.value.code == dg.DG_EINVAL
+
+
+def test_torch_stream_and_bound_state():
+    act, rng = _random_mesh(11, 30, 30, 0.2)
+    src = _sources_in(act, rng, 4, 0.3, 0.0, 0.0, margin=5)
+    with _solver(3, "f32", D=1.0, sigma0=0.3) as a:
+        a.set_geometry_mask(act, 0.3)
+        a.set_sources(src)
+        dt, _ = a.query_dt()
+        a.step(10, dt)
+        ref = a.get_nodes()
+    with _solver(3, "f32", D=1.0, sigma0=0.3) as b:
+        b.set_geometry_mask(act, 0.3)
+        buf = torch.empty(b.state_bytes(4), dtype=torch.uint8, device="cuda:0")
+        st = torch.cuda.Stream(device=0)
+        b.bind_state(buf)
+        b.set_stream(st.cuda_stream)
+        b.set_sources(src)
+        b.step(10, dt)
+        got = b.get_nodes()
+        b.set_stream(None)
+    assert np.array_equal(got, ref)
