@@ -194,6 +194,8 @@ def main():
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--rk", type=int, default=20, help="RK3 steps per bench step")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--densities", type=int, default=64,
+                    help="start points per GPU (64 = the workload; fewer for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
     args = ap.parse_args()
@@ -216,11 +218,13 @@ def main():
     dev = local
 
     w = dginputs.workload_cell40(args.seed, m=64)
+    w.sources = w.sources[:args.densities]
     # weak scaling: every rank its own 64 start points
     if world > 1:
         from dginputs import sample_sources, source_box
         lo, hi = source_box(w.L, w.tiles, w.sigma0, w.D, max(w.deltas))
-        w.sources = sample_sources(args.seed + 7919 + 1000 * rank, w.disks, 64, lo, hi, margin=w.h)
+        w.sources = sample_sources(args.seed + 7919 + 1000 * rank, w.disks, args.densities, lo, hi,
+                                   margin=w.h)
     prec = dg.DG_FP32 if args.precision == "f32" else dg.DG_FP64
     s = dg.DGSolver(p=w.p, precision=prec, D=w.D, sigma0=w.sigma0, device=dev)
     s.set_geometry_disks(w.disks.cx, w.disks.cy, w.disks.r, w.L, w.n_cell, w.tiles)

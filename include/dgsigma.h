@@ -184,6 +184,14 @@ int dg_moments(dg_ctx *ctx, double *out);
  * may be NULL) each M0(t).  Computed on the device in FP64. */
 int dg_covariance(dg_ctx *ctx, double *sigma3, double *mu2, double *mass);
 
+/* Mixture covariance (Sec. 4.1) of raw moments supplied by the caller, e.g.
+ * moments of densities propagated on several GPUs and gathered: mom and mom0
+ * are host arrays [m][6] = {M0, Mx, My, Mxx, Mxy, Myy} at t and at t = 0.
+ * Same formula as dg_covariance, computed on ctx's device in FP64; needs no
+ * geometry.  Errors: DG_EINVAL (m < 1, NULL pointers). */
+int dg_mixture_covariance(dg_ctx *ctx, const double *mom, const double *mom0, int m,
+                          double *sigma3, double *mu2);
+
 /* Replace every density u by L u (the DG operator alone, Eq. 7 with the
  * fluxes of Sec. 3.2); for operator tests.  Leaves t unchanged. */
 int dg_apply_operator(dg_ctx *ctx);

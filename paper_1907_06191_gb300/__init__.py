@@ -71,6 +71,7 @@ EXPORTS = {
     "dg_propagate_to": (_I, [_P, _D]),
     "dg_moments": (_I, [_P, _DP]),
     "dg_covariance": (_I, [_P, _DP, _DP, _DP]),
+    "dg_mixture_covariance": (_I, [_P, _DP, _DP, _I, _DP, _DP]),
     "dg_apply_operator": (_I, [_P]),
     "dg_get_nodes": (_I, [_P, _DP]),
     "dg_set_nodes": (_I, [_P, _DP]),
@@ -215,6 +216,14 @@ class DGSolver:
         s3, mu, mass = np.zeros(3), np.zeros(2), np.zeros(self.info().m)
         self._ck(self._L.dg_covariance(self.ctx, _dp(s3), _dp(mu), _dp(mass)), "dg_covariance")
         return s3, mu, mass
+
+    def mixture_covariance(self, mom, mom0):
+        """Sigma and mu of externally supplied raw moments [m, 6] (t and 0)."""
+        mom, mom0 = _f64(mom).reshape(-1, 6), _f64(mom0).reshape(-1, 6)
+        s3, mu = np.zeros(3), np.zeros(2)
+        self._ck(self._L.dg_mixture_covariance(self.ctx, _dp(mom), _dp(mom0), mom.shape[0],
+                                               _dp(s3), _dp(mu)), "dg_mixture_covariance")
+        return s3, mu
 
     def apply_operator(self):
         self._ck(self._L.dg_apply_operator(self.ctx), "dg_apply_operator")

@@ -547,6 +547,32 @@ int dg_covariance(dg_ctx *ctx, double *sigma3, double *mu2, double *mass) {
   return DG_OK;
 }
 
+int dg_mixture_covariance(dg_ctx *ctx, const double *mom, const double *mom0, int m,
+                          double *sigma3, double *mu2) {
+  if (!ctx || !mom || !mom0 || !sigma3 || !mu2 || m < 1) return DG_EINVAL;
+  Ctx &c = ctx->c;
+  CK(cudaSetDevice(c.device), "set device");
+  std::vector<double> h(2 * (size_t)m * kMomFields, 0.0);
+  for (int s = 0; s < m; ++s)
+    for (int f = 0; f < 6; ++f) {
+      h[(size_t)s * kMomFields + f] = mom[s * 6 + f];
+      h[((size_t)m + s) * kMomFields + f] = mom0[s * 6 + f];
+    }
+  double *d = nullptr;
+  CK(cudaMalloc(&d, sizeof(double) * (h.size() + 8)), "moment buffer");
+  double out[5];
+  cudaError_t e = cudaMemcpyAsync(d, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, c.stream);
+  double *dout = d + h.size();
+  if (e == cudaSuccess) e = launch_covariance(d, d + (size_t)m * kMomFields, m, dout, c.stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, sizeof(out), cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "mixture covariance");
+  sigma3[0] = out[0]; sigma3[1] = out[1]; sigma3[2] = out[2];
+  mu2[0] = out[3]; mu2[1] = out[4];
+  return DG_OK;
+}
+
 int dg_apply_operator(dg_ctx *ctx) {
   if (!ctx) return DG_EINVAL;
   Ctx &c = ctx->c;

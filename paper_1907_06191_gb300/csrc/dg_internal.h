@@ -32,11 +32,11 @@ struct Gll {
 bool gll_tables(int p, Gll *g);
 double rk3_real_axis_limit();
 
-// Operator scalars of one stage launch.  out = alpha u0 + beta u + gamma R,
-// where L u = (k / J^2) R.
+// Operator scalars of one stage launch: out = u0 + beta (u - u0) + gamma R
+// (or beta u + gamma R without u0), where L u = (k / J^2) R.
 template <typename T>
 struct StageCoef {
-  T alpha, beta, gamma;
+  T alpha, beta, gamma;  // alpha = 1 - beta, kept for reference only
   T pen;     // eta (p+1)^2 / 2
   int wallA; // paper wall mode
 };

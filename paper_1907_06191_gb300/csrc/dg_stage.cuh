@@ -3,8 +3,11 @@
 // One thread owns one mesh element of one density: the element's (p+1)^2
 // nodal values sit in registers, the four face neighbours are read whole
 // (through L1/L2; they are other threads' elements) and the stage result
-//   out = alpha u0 + beta u + gamma R(u),   L u = (k / J^2) R(u),
-// is written once.  q = grad u is never stored: substituting the gradient
+//   out = u0 + beta (u - u0) + gamma R(u),   L u = (k / J^2) R(u),
+// is written once (u0 absent: out = beta u + gamma R).  This increment form
+// of the Shu-Osher combination (1 - beta) u0 + beta (u + dt L u) keeps the
+// weight of u0 exactly 1 - beta in any precision, so FP32 rounding of 1/3
+// and 2/3 does not bias the mass.  q = grad u is never stored: substituting the gradient
 // equation into the divergence equation gives, at node (a, b),
 //   R_ab = sum_i (D D)_ai u_ib + sum_j (D D)_bj u_aj                  (volume)
 //        + sum over faces f: s_f D_{a,i_f} g_f,b / w                  (lifting)
@@ -80,167 +83,286 @@ __device__ __forceinline__ void store_elem(T *p, const T (&u)[NP]) {
   }
 }
 
-// x-faces: S = +1 east (own column i = P, neighbour column 0),
-//          S = -1 west (own column 0, neighbour column P).
-template <typename T, int P, int S>
-__device__ __forceinline__ void face_x(const T (&u)[(P + 1) * (P + 1)],
-                                       T (&R)[(P + 1) * (P + 1)], int nbk,
-                                       const T *__restrict__ U, const StageTab<T, P> &tb,
-                                       const StageCoef<T> &c) {
-  constexpr int n = P + 1, NP = n * n;
-  constexpr int i_f = S > 0 ? P : 0, i_n = S > 0 ? 0 : P;
-  const T sg = (T)S;
-  T g[n];
-  if (nbk >= 0) {
-    T v[NP];
-    load_elem<T, NP>(U + (size_t)nbk * NP, v);
+// ---------------------------------------------------------------------------
+// Shared-memory staging.  A block owns kBlock consecutive mesh elements (one
+// per thread).  Their values are copied into shared memory with 16-byte
+// asynchronous copies (coalesced; no registers held while in flight), and the
+// result leaves through shared memory with coalesced 16-byte stores.  When an
+// element is a whole number S of 16-byte slots, slot k of element e lives at
+// slot e*S + (k ^ swz(e)) (S a power of two), which makes the slot reads of 8
+// consecutive threads hit 8 different bank groups; other element sizes are
+// stored linearly and read word by word (odd word strides are conflict free).
+template <typename T, int NP>
+struct Stage {
+  static constexpr int B = NP * (int)sizeof(T);
+  static constexpr bool SLOT = (B % 16) == 0;
+  static constexpr int S = SLOT ? B / 16 : 0;
+  static constexpr bool POW2 = SLOT && ((S & (S - 1)) == 0);
+  static constexpr int WPS = 16 / (int)sizeof(T);
+  static constexpr int CHUNK_BYTES = ((kBlock * B + 15) / 16) * 16;
+
+  __device__ static __forceinline__ int swz(int e) {
+    if constexpr (!POW2 || S == 1) return 0;
+    else if constexpr (S == 2) return (e >> 2) & 1;
+    else if constexpr (S == 4) return (e >> 1) & 3;
+    else return e & 7;
+  }
+  __device__ static __forceinline__ int slot(int e, int k) {
+    if constexpr (POW2) return e * S + (k ^ swz(e));
+    else return e * S + k;
+  }
+  // index (in T units) of value w of element e
+  __device__ static __forceinline__ int word(int e, int w) {
+    if constexpr (SLOT) return slot(e, w / WPS) * WPS + (w % WPS);
+    else return e * NP + w;
+  }
+  __device__ static __forceinline__ void read(const T *sm, int e, T (&u)[NP]) {
+    if constexpr (SLOT) {
 #pragma unroll
-    for (int b = 0; b < n; ++b) {
-      T dm = 0, dp = 0;
+      for (int k = 0; k < S; ++k) {
+        const float4 v = *reinterpret_cast<const float4 *>(sm + slot(e, k) * WPS);
+        const T *pv = reinterpret_cast<const T *>(&v);
 #pragma unroll
-      for (int m = 0; m < n; ++m) {
-        dm += tb.D[i_f * n + m] * u[b * n + m];
-        dp += tb.D[i_n * n + m] * v[b * n + m];
+        for (int q = 0; q < WPS; ++q) u[k * WPS + q] = pv[q];
       }
-      const T um = u[b * n + i_f], up = v[b * n + i_n];
-      g[b] = (T)0.5 * (up - um);
-      R[b * n + i_f] += tb.inv_w * ((T)0.5 * sg * (dp - dm) - c.pen * (um - up));
-    }
-  } else if (nbk == kWall && !c.wallA) {
+    } else {
 #pragma unroll
-    for (int b = 0; b < n; ++b) {
-      T dm = 0;
-#pragma unroll
-      for (int m = 0; m < n; ++m) dm += tb.D[i_f * n + m] * u[b * n + m];
-      R[b * n + i_f] -= tb.inv_w * sg * dm;
-    }
-    return;  // g = 0: no lifting
-  } else if (nbk == kWall) {
-#pragma unroll
-    for (int b = 0; b < n; ++b) {
-      T dm = 0;
-#pragma unroll
-      for (int m = 0; m < n; ++m) dm += tb.D[i_f * n + m] * u[b * n + m];
-      g[b] = (T)-0.5 * u[b * n + i_f];
-      R[b * n + i_f] -= tb.inv_w * (sg * dm + tb.inv_w * g[b]);
-    }
-  } else {
-#pragma unroll
-    for (int b = 0; b < n; ++b) {
-      const T um = u[b * n + i_f];
-      g[b] = -um;
-      R[b * n + i_f] -= tb.inv_w * c.pen * um;
+      for (int w = 0; w < NP; ++w) u[w] = sm[e * NP + w];
     }
   }
+  __device__ static __forceinline__ void write(T *sm, int e, const T (&u)[NP]) {
+    if constexpr (SLOT) {
 #pragma unroll
-  for (int b = 0; b < n; ++b) {
-    const T gs = sg * tb.inv_w * g[b];
+      for (int k = 0; k < S; ++k) {
+        float4 v;
+        T *pv = reinterpret_cast<T *>(&v);
 #pragma unroll
-    for (int a = 0; a < n; ++a) R[b * n + a] += tb.D[a * n + i_f] * gs;
+        for (int q = 0; q < WPS; ++q) pv[q] = u[k * WPS + q];
+        *reinterpret_cast<float4 *>(sm + slot(e, k) * WPS) = v;
+      }
+    } else {
+#pragma unroll
+      for (int w = 0; w < NP; ++w) sm[e * NP + w] = u[w];
+    }
   }
+  // number of 16-byte pieces covering cnt elements
+  __device__ static __forceinline__ int pieces(int cnt) {
+    if constexpr (SLOT) return cnt * S;
+    else return (cnt * B + 15) / 16;
+  }
+  __device__ static __forceinline__ int piece_dst(int j) {  // in 16-byte units
+    if constexpr (SLOT) return slot(j / S, j % S);
+    else return j;
+  }
+};
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// y-faces: S = +1 north (own row j = P, neighbour row 0),
-//          S = -1 south (own row 0, neighbour row P).
-template <typename T, int P, int S>
-__device__ __forceinline__ void face_y(const T (&u)[(P + 1) * (P + 1)],
-                                       T (&R)[(P + 1) * (P + 1)], int nbk,
-                                       const T *__restrict__ U, const StageTab<T, P> &tb,
-                                       const StageCoef<T> &c) {
-  constexpr int n = P + 1, NP = n * n;
-  constexpr int j_f = S > 0 ? P : 0, j_n = S > 0 ? 0 : P;
-  const T sg = (T)S;
-  T g[n];
-  if (nbk >= 0) {
-    T v[NP];
-    load_elem<T, NP>(U + (size_t)nbk * NP, v);
-#pragma unroll
-    for (int a = 0; a < n; ++a) {
-      T dm = 0, dp = 0;
-#pragma unroll
-      for (int m = 0; m < n; ++m) {
-        dm += tb.D[j_f * n + m] * u[m * n + a];
-        dp += tb.D[j_n * n + m] * v[m * n + a];
-      }
-      const T um = u[j_f * n + a], up = v[j_n * n + a];
-      g[a] = (T)0.5 * (up - um);
-      R[j_f * n + a] += tb.inv_w * ((T)0.5 * sg * (dp - dm) - c.pen * (um - up));
-    }
-  } else if (nbk == kWall && !c.wallA) {
-#pragma unroll
-    for (int a = 0; a < n; ++a) {
-      T dm = 0;
-#pragma unroll
-      for (int m = 0; m < n; ++m) dm += tb.D[j_f * n + m] * u[m * n + a];
-      R[j_f * n + a] -= tb.inv_w * sg * dm;
-    }
-    return;
-  } else if (nbk == kWall) {
-#pragma unroll
-    for (int a = 0; a < n; ++a) {
-      T dm = 0;
-#pragma unroll
-      for (int m = 0; m < n; ++m) dm += tb.D[j_f * n + m] * u[m * n + a];
-      g[a] = (T)-0.5 * u[j_f * n + a];
-      R[j_f * n + a] -= tb.inv_w * (sg * dm + tb.inv_w * g[a]);
-    }
-  } else {
-#pragma unroll
-    for (int a = 0; a < n; ++a) {
-      const T um = u[j_f * n + a];
-      g[a] = -um;
-      R[j_f * n + a] -= tb.inv_w * c.pen * um;
-    }
+// Face f of an element: 0 east (x = +1), 1 west, 2 north (y = +1), 3 south.
+// Node t runs along the face.  own(f, t): node index on face f; the matching
+// node of the neighbour across f is own(opposite(f), t).
+template <int P>
+struct Faces {
+  static constexpr int n = P + 1;
+  __host__ __device__ static constexpr int own(int f, int t) {
+    return f == 0 ? t * n + P : f == 1 ? t * n : f == 2 ? P * n + t : t;
   }
+  __host__ __device__ static constexpr int opp(int f) { return f ^ 1; }
+  __host__ __device__ static constexpr int sgn(int f) { return (f & 1) ? -1 : 1; }
+  __host__ __device__ static constexpr int row(int f) { return (f & 1) ? 0 : P; }  // D row of the face
+};
+
+// Outward normal derivative (reference units) at the nodes of face f.
+template <typename T, int P>
+__device__ __forceinline__ void outward_derivative(const T (&u)[(P + 1) * (P + 1)], int f,
+                                                   const StageTab<T, P> &tb, T (&d)[P + 1]) {
+  constexpr int n = P + 1;
+  const int r = Faces<P>::row(f);
+  const T sg = (T)Faces<P>::sgn(f);
 #pragma unroll
-  for (int a = 0; a < n; ++a) {
-    const T gs = sg * tb.inv_w * g[a];
+  for (int t = 0; t < n; ++t) {
+    T s = 0;
 #pragma unroll
-    for (int b = 0; b < n; ++b) R[b * n + a] += tb.D[b * n + j_f] * gs;
+    for (int m = 0; m < n; ++m)
+      s += tb.D[r * n + m] * (f < 2 ? u[t * n + m] : u[m * n + t]);
+    d[t] = sg * s;
   }
 }
 
 // grid: (ceil(nA / kBlock), m); density s = blockIdx.y starts at s * stride
 // elements.  nb entries are < nA (checked when the table is built).  out may
-// alias u0 (the last stage updates u^n in place: each thread reads its own
-// element of u0 before writing the same element); it never aliases uin.
+// alias u0 (the last stage updates u^n in place: a block reads its whole u0
+// chunk into shared memory before it writes the same chunk); it never aliases
+// uin.  Shared memory: chunk of u, chunk of u0 (then of the result), and the
+// outward face derivatives [4][kBlock][n].
 template <typename T, int P, bool HAS_U0>
 __global__ void __launch_bounds__(kBlock)
     k_stage(const T *__restrict__ uin, const T *u0, T *out,
             const int4 *__restrict__ nb, long long nA, long long stride,
             const StageTab<T, P> tb, const StageCoef<T> c) {
   constexpr int n = P + 1, NP = n * n;
-  const long long a = (long long)blockIdx.x * kBlock + threadIdx.x;
-  if (a >= nA) return;
+  using St = Stage<T, NP>;
+  using Fc = Faces<P>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *su = reinterpret_cast<T *>(smem_raw);
+  T *so = reinterpret_cast<T *>(smem_raw + St::CHUNK_BYTES);
+  T *sd = reinterpret_cast<T *>(smem_raw + 2 * St::CHUNK_BYTES);
+
+  const long long a0 = (long long)blockIdx.x * kBlock;
+  const int cnt = (int)min((long long)kBlock, nA - a0);
+  const int el = threadIdx.x;
+  const bool live = el < cnt;
   const size_t sbase = (size_t)blockIdx.y * (size_t)stride * NP;
   const T *U = uin + sbase;
-  T u[NP], R[NP];
-  load_elem<T, NP>(U + (size_t)a * NP, u);
-  const int4 f = __ldg(nb + a);
-#pragma unroll
-  for (int j = 0; j < n; ++j)
-#pragma unroll
-    for (int i = 0; i < n; ++i) {
-      T s = 0;
-#pragma unroll
-      for (int m = 0; m < n; ++m)
-        s += tb.D2[i * n + m] * u[j * n + m] + tb.D2[j * n + m] * u[m * n + i];
-      R[j * n + i] = s;
+
+  {  // async copies of the u chunk (group 0) and the u0 chunk (group 1)
+    const char *gu = reinterpret_cast<const char *>(U + (size_t)a0 * NP);
+    const int np16 = St::pieces(cnt);
+    for (int j = el; j < np16; j += kBlock)
+      cp_async16(smem_raw + 16 * St::piece_dst(j), gu + 16 * (size_t)j);
+    cp_async_commit();
+    if constexpr (HAS_U0) {
+      const char *g0 = reinterpret_cast<const char *>(u0 + sbase + (size_t)a0 * NP);
+      for (int j = el; j < np16; j += kBlock)
+        cp_async16(reinterpret_cast<unsigned char *>(so) + 16 * St::piece_dst(j), g0 + 16 * (size_t)j);
+      cp_async_commit();
     }
-  face_x<T, P, +1>(u, R, f.x, U, tb, c);
-  face_x<T, P, -1>(u, R, f.y, U, tb, c);
-  face_y<T, P, +1>(u, R, f.z, U, tb, c);
-  face_y<T, P, -1>(u, R, f.w, U, tb, c);
-  T o[NP];
-  if constexpr (HAS_U0) {
-    load_elem<T, NP, false>(u0 + sbase + (size_t)a * NP, o);
-#pragma unroll
-    for (int k = 0; k < NP; ++k) o[k] = c.alpha * o[k] + c.beta * u[k] + c.gamma * R[k];
-  } else {
-#pragma unroll
-    for (int k = 0; k < NP; ++k) o[k] = c.beta * u[k] + c.gamma * R[k];
   }
-  store_elem<T, NP>(out + sbase + (size_t)a * NP, o);
+  const int4 f4 = live ? __ldg(nb + a0 + el) : make_int4(kEdge, kEdge, kEdge, kEdge);
+  if constexpr (HAS_U0) cp_async_wait<1>();
+  else cp_async_wait<0>();
+  __syncthreads();
+
+  T u[NP], R[NP];
+  if (live) {
+    St::read(su, el, u);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      T d[n];
+      outward_derivative<T, P>(u, f, tb, d);
+#pragma unroll
+      for (int t = 0; t < n; ++t) sd[(f * kBlock + el) * n + t] = d[t];
+    }
+    // volume: (D D) along x and along y
+#pragma unroll
+    for (int j = 0; j < n; ++j)
+#pragma unroll
+      for (int i = 0; i < n; ++i) {
+        T s = 0;
+#pragma unroll
+        for (int m = 0; m < n; ++m)
+          s += tb.D2[i * n + m] * u[j * n + m] + tb.D2[j * n + m] * u[m * n + i];
+        R[j * n + i] = s;
+      }
+  }
+  __syncthreads();
+
+  if (live) {
+    const int nbk[4] = {f4.x, f4.y, f4.z, f4.w};
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const int k = nbk[f];
+      const int fo = Fc::opp(f);
+      T g[n], odf[n];
+#pragma unroll
+      for (int t = 0; t < n; ++t) odf[t] = sd[(f * kBlock + el) * n + t];
+      bool lift = true;
+      if (k >= 0) {
+        T up[n], odn[n];
+        const long long loc = (long long)k - a0;
+        if (loc >= 0 && loc < cnt) {
+#pragma unroll
+          for (int t = 0; t < n; ++t) {
+            up[t] = su[St::word((int)loc, Fc::own(fo, t))];
+            odn[t] = sd[(fo * kBlock + (int)loc) * n + t];
+          }
+        } else {
+          T v[NP];
+          load_elem<T, NP>(U + (size_t)k * NP, v);
+          outward_derivative<T, P>(v, fo, tb, odn);
+#pragma unroll
+          for (int t = 0; t < n; ++t) up[t] = v[Fc::own(fo, t)];
+        }
+#pragma unroll
+        for (int t = 0; t < n; ++t) {
+          const T um = u[Fc::own(f, t)];
+          g[t] = (T)0.5 * (up[t] - um);
+          R[Fc::own(f, t)] -= tb.inv_w * ((T)0.5 * (odf[t] + odn[t]) + c.pen * (um - up[t]));
+        }
+      } else if (k == kWall && !c.wallA) {
+#pragma unroll
+        for (int t = 0; t < n; ++t) R[Fc::own(f, t)] -= tb.inv_w * odf[t];
+        lift = false;
+      } else if (k == kWall) {
+#pragma unroll
+        for (int t = 0; t < n; ++t) {
+          g[t] = (T)-0.5 * u[Fc::own(f, t)];
+          R[Fc::own(f, t)] -= tb.inv_w * (odf[t] + tb.inv_w * g[t]);
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < n; ++t) {
+          const T um = u[Fc::own(f, t)];
+          g[t] = -um;
+          R[Fc::own(f, t)] -= tb.inv_w * c.pen * um;
+        }
+      }
+      if (lift) {
+        // lifting of the u-flux jump: column (x-faces) or row (y-faces) of D
+        const int r = Fc::row(f);
+        const T sg = (T)Fc::sgn(f);
+#pragma unroll
+        for (int t = 0; t < n; ++t) {
+          const T gs = sg * tb.inv_w * g[t];
+#pragma unroll
+          for (int q = 0; q < n; ++q) {
+            if (f < 2) R[t * n + q] += tb.D[q * n + r] * gs;
+            else R[q * n + t] += tb.D[q * n + r] * gs;
+          }
+        }
+      }
+    }
+  }
+
+  if constexpr (HAS_U0) {
+    cp_async_wait<0>();
+    __syncthreads();
+  }
+  if (live) {
+    T o[NP];
+    if constexpr (HAS_U0) {
+      St::read(so, el, o);
+#pragma unroll
+      for (int k = 0; k < NP; ++k) o[k] = o[k] + c.beta * (u[k] - o[k]) + c.gamma * R[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < NP; ++k) o[k] = c.beta * u[k] + c.gamma * R[k];
+    }
+    St::write(so, el, o);
+  }
+  __syncthreads();
+  {  // coalesced 16-byte stores of the result chunk
+    char *go = reinterpret_cast<char *>(out + sbase + (size_t)a0 * NP);
+    const int np16 = St::pieces(cnt);
+    for (int j = el; j < np16; j += kBlock)
+      *reinterpret_cast<float4 *>(go + 16 * (size_t)j) =
+          *reinterpret_cast<const float4 *>(reinterpret_cast<unsigned char *>(so) + 16 * St::piece_dst(j));
+  }
+}
+
+template <typename T, int P>
+constexpr int stage_smem_bytes() {
+  return 2 * Stage<T, (P + 1) * (P + 1)>::CHUNK_BYTES + 4 * kBlock * (P + 1) * (int)sizeof(T);
 }
 
 template <typename T, int P>
@@ -262,10 +384,21 @@ cudaError_t launch_stage_p(const T *u, const T *u0, T *out, const int4 *nb, long
   if (nA <= 0 || m <= 0) return cudaSuccess;
   const dim3 grid((unsigned)((nA + kBlock - 1) / kBlock), (unsigned)m);
   const StageTab<T, P> tb = make_tab<T, P>(g);
+  constexpr int smem = stage_smem_bytes<T, P>();
+  static bool attr_set = false;  // per instantiation, first launch
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_stage<T, P, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_stage<T, P, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
   if (u0)
-    k_stage<T, P, true><<<grid, kBlock, 0, s>>>(u, u0, out, nb, nA, stride, tb, c);
+    k_stage<T, P, true><<<grid, kBlock, smem, s>>>(u, u0, out, nb, nA, stride, tb, c);
   else
-    k_stage<T, P, false><<<grid, kBlock, 0, s>>>(u, u0, out, nb, nA, stride, tb, c);
+    k_stage<T, P, false><<<grid, kBlock, smem, s>>>(u, u0, out, nb, nA, stride, tb, c);
   return cudaGetLastError();
 }
 
