@@ -226,6 +226,34 @@ int dg_state_bytes(dg_ctx *ctx, int m, size_t *bytes);
  * context is destroyed or rebound; NULL returns to library-owned memory. */
 int dg_bind_state(dg_ctx *ctx, void *device_ptr, size_t bytes);
 
+/* Moments of densities without allocating anything.  No counterpart in the
+ * paper: it is a service to callers that cannot allocate device memory --
+ * their memory is owned by another allocator (a framework's caching pool, a
+ * fixed pre-reservation) or they run where cudaMalloc is off limits (a loop
+ * that must not risk the implicit synchronisation of an allocation).  The
+ * caller passes device pointers: u holds m densities in the dense layout
+ * [m][ny][nx][n][n] (n = p+1; FP64 or FP32 per precision; elements outside
+ * the mesh hold 0) on the grid of dg_set_geometry_mask (side h, lower-left
+ * corner x0, y0), xy the start points [m][2] (FP64), and mom receives the
+ * raw moments [m][6] = {M0, Mx, My, Mxx, Mxy, Myy} (FP64) as dg_moments
+ * defines them.  Work is queued on stream (a cudaStream_t, NULL = legacy
+ * default stream) of the calling thread's current device; the call does not
+ * synchronise.
+ * Scratch: the reduction's partial sums live in one fixed device array of
+ * 1.09 MB inside the library (room for m <= 128), which every GPU that loads
+ * the library holds until the process exits.  The first call on a device
+ * looks up that array's address with the device current; make that first
+ * call before any stream capture.  All calls share the array: calls whose
+ * work overlaps on the GPU (different streams, or threads) race and give
+ * wrong moments; serialise them.  The array needs no clearing (each call
+ * overwrites every partial it reads).
+ * Errors: DG_EINVAL (NULL pointer, m < 1 or m > 128, p outside 1..5, nx or
+ * ny < 1, h <= 0, bad precision), DG_ECUDA (launch failure).  No
+ * cudaMalloc, cudaFree or other allocating call is made. */
+int dg_moments_dense_static(const void *u, int precision, int m, int nx, int ny, int p,
+                            double h, double x0, double y0, const double *xy, double *mom,
+                            void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -81,6 +81,7 @@ EXPORTS = {
     "dg_set_state": (_I, [_P, _P, _SZ]),
     "dg_state_bytes": (_I, [_P, _I, ctypes.POINTER(_SZ)]),
     "dg_bind_state": (_I, [_P, _P, _SZ]),
+    "dg_moments_dense_static": (_I, [_P, _I, _I, _I, _I, _I, _D, _D, _D, _P, _P, _P]),
 }
 
 _lib = None

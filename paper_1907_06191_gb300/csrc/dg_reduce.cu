@@ -1,6 +1,7 @@
 // dg_reduce.cu -- start densities, FP64 moment reduction, covariance of the
 // mixture (Sec. 4.1), node layout conversion, power-iteration helpers.
 #include <cmath>
+#include <mutex>
 
 #include "dg_internal.h"
 
@@ -358,4 +359,139 @@ cudaError_t launch_scale_by_rnorm(const Ctx &c, const double *in, const double *
   return cudaGetLastError();
 }
 
+// ---- moments without allocation ---------------------------------------------
+// Some callers cannot allocate device memory: their device memory is held by
+// another allocator (a framework's caching pool or a fixed pre-reservation),
+// or they run where cudaMalloc is off limits (a latency-critical loop that
+// must not risk the implicit synchronisation cudaMalloc can cause, code that
+// owns no CUDA context set-up).  dg_moments_dense_static serves them: the
+// first-pass partial sums of the two-pass reduction live in this file-scope
+// device array, so the call allocates nothing.  Every GPU that loads the
+// library holds the array (1.09 MB) until the process exits.
+
+constexpr int kStaticMomBlocks = 152;          // first-pass blocks per density
+constexpr int kStaticMomMaxDensities = 128;    // largest m of one call
+static __device__ __align__(256) double
+    g_static_mom_partials[kStaticMomMaxDensities * kStaticMomBlocks * kMomFields];
+
+// Moments of densities in the dense node layout [m][ny][nx][n][n]; elements
+// outside the mesh hold zeros and add nothing.  grid (kStaticMomBlocks, m).
+template <typename T, int P>
+__global__ void __launch_bounds__(256)
+    k_moments_dense(const T *__restrict__ u, int nx, int ny, const double *__restrict__ xy,
+                    const NodeGeo g, double *__restrict__ part) {
+  constexpr int n = P + 1, NP = n * n;
+  const int s = blockIdx.y;
+  const double xs = xy[2 * s], ys = xy[2 * s + 1];
+  const double J = 0.5 * g.h;
+  const long long ne = (long long)nx * ny;
+  double acc[kMomFields] = {0, 0, 0, 0, 0, 0, 0};
+  const T *U = u + (size_t)s * ne * NP;
+  for (long long e = (long long)blockIdx.x * 256 + threadIdx.x; e < ne;
+       e += (long long)gridDim.x * 256) {
+    const int ex = (int)(e % nx), ey = (int)(e / nx);
+    const T *ue = U + (size_t)e * NP;
+#pragma unroll
+    for (int j = 0; j < n; ++j) {
+      const double y = g.y0 + (ey + 0.5) * g.h + J * g.xi[j] - ys;
+#pragma unroll
+      for (int i = 0; i < n; ++i) {
+        const double x = g.x0 + (ex + 0.5) * g.h + J * g.xi[i] - xs;
+        const double wu = J * J * g.w[i] * g.w[j] * (double)ue[j * n + i];
+        acc[0] += wu;
+        acc[1] += wu * x;
+        acc[2] += wu * y;
+        acc[3] += wu * x * x;
+        acc[4] += wu * x * y;
+        acc[5] += wu * y * y;
+        acc[6] += fabs(wu);
+      }
+    }
+  }
+  block_sum7(acc);
+  if (threadIdx.x == 0) {
+    double *o = part + ((size_t)s * gridDim.x + blockIdx.x) * kMomFields;
+#pragma unroll
+    for (int f = 0; f < kMomFields; ++f) o[f] = acc[f];
+  }
+}
+
+// Second pass: one block per density, partials summed in a fixed order;
+// writes the six moments [m][6].
+__global__ void __launch_bounds__(256)
+    k_moments_dense_final(const double *__restrict__ part, int nblk, double *__restrict__ mom) {
+  const int s = blockIdx.x;
+  double acc[kMomFields] = {0, 0, 0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < nblk; b += 256) {
+    const double *p = part + ((size_t)s * nblk + b) * kMomFields;
+#pragma unroll
+    for (int f = 0; f < kMomFields; ++f) acc[f] += p[f];
+  }
+  block_sum7(acc);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int f = 0; f < 6; ++f) mom[(size_t)s * 6 + f] = acc[f];
+  }
+}
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+double *g_static_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device with that device current.
+cudaError_t static_scratch(double **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    double *p = nullptr;
+    e = cudaGetSymbolAddress((void **)&p, g_static_mom_partials);
+    if (e != cudaSuccess) return e;
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
 }  // namespace dg
+
+extern "C" int dg_moments_dense_static(const void *u, int precision, int m, int nx, int ny,
+                                       int p, double h, double x0, double y0,
+                                       const double *xy, double *mom, void *stream) {
+  using namespace dg;
+  if (!u || !xy || !mom) return DG_EINVAL;
+  if (m < 1 || m > kStaticMomMaxDensities) return DG_EINVAL;
+  if (p < 1 || p > kMaxP || nx < 1 || ny < 1 || !(h > 0.0)) return DG_EINVAL;
+  if (precision != DG_FP64 && precision != DG_FP32) return DG_EINVAL;
+  Gll gl;
+  if (!gll_tables(p, &gl)) return DG_EINVAL;
+  NodeGeo g;
+  for (int i = 0; i <= p; ++i) {
+    g.xi[i] = gl.xi[i];
+    g.w[i] = gl.w[i];
+  }
+  g.h = h;
+  g.x0 = x0;
+  g.y0 = y0;
+  double *part = nullptr;
+  if (static_scratch(&part) != cudaSuccess) return DG_ECUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  const dim3 grid(kStaticMomBlocks, (unsigned)m);
+  auto launch = [&]() -> cudaError_t {
+    if (precision == DG_FP64) {
+      DG_P_SWITCH(p, (k_moments_dense<double, PP><<<grid, 256, 0, s>>>(
+                         (const double *)u, nx, ny, xy, g, part)));
+    } else {
+      DG_P_SWITCH(p, (k_moments_dense<float, PP><<<grid, 256, 0, s>>>(
+                         (const float *)u, nx, ny, xy, g, part)));
+    }
+    k_moments_dense_final<<<m, 256, 0, s>>>(part, kStaticMomBlocks, mom);
+    return cudaGetLastError();
+  };
+  return launch() == cudaSuccess ? DG_OK : DG_ECUDA;
+}
