@@ -4,6 +4,7 @@
 #include <mutex>
 
 #include "dg_internal.h"
+#include "dg_stage.cuh"
 
 namespace dg {
 
@@ -42,15 +43,37 @@ __global__ void k_init(const int2 *__restrict__ exy, long long nA, long long str
   const double c = 1.0 / (2.0 * M_PI * sigma0 * sigma0);
   const double inv2s2 = 1.0 / (2.0 * sigma0 * sigma0);
   T *out = u + ((size_t)s * stride + a) * NP;
+  // exp(-(dx^2 + dy^2)/(2 s^2)) = exp(-dx^2/(2 s^2)) exp(-dy^2/(2 s^2)): 2n
+  // exponentials per element instead of n^2; elements whose largest
+  // exponent already underflows the state precision are written as zeros.
+  double ax[n], ay[n], amax_x = -1e300, amax_y = -1e300;
 #pragma unroll
-  for (int j = 0; j < n; ++j)
+  for (int i = 0; i < n; ++i) {
+    const double dx = g.x0 + (e.x + 0.5) * g.h + 0.5 * g.h * g.xi[i] - xs;
+    const double dy = g.y0 + (e.y + 0.5) * g.h + 0.5 * g.h * g.xi[i] - ys;
+    ax[i] = -(dx * dx) * inv2s2;
+    ay[i] = -(dy * dy) * inv2s2;
+    amax_x = fmax(amax_x, ax[i]);
+    amax_y = fmax(amax_y, ay[i]);
+  }
+  const double floor_exp = sizeof(T) == 4 ? -110.0 : -760.0;
+  T v[NP];
+  if (amax_x + amax_y < floor_exp) {
+#pragma unroll
+    for (int k = 0; k < NP; ++k) v[k] = (T)0;
+  } else {
+    double gx[n], gy[n];
 #pragma unroll
     for (int i = 0; i < n; ++i) {
-      const double x = g.x0 + (e.x + 0.5) * g.h + 0.5 * g.h * g.xi[i];
-      const double y = g.y0 + (e.y + 0.5) * g.h + 0.5 * g.h * g.xi[j];
-      const double dx = x - xs, dy = y - ys;
-      out[j * n + i] = (T)(c * exp(-(dx * dx + dy * dy) * inv2s2));
+      gx[i] = exp(ax[i]);
+      gy[i] = exp(ay[i]);
     }
+#pragma unroll
+    for (int j = 0; j < n; ++j)
+#pragma unroll
+      for (int i = 0; i < n; ++i) v[j * n + i] = (T)(c * (gx[i] * gy[j]));
+  }
+  store_elem<T, NP>(out, v);
 }
 
 // ---- moments -----------------------------------------------------------------
@@ -88,6 +111,53 @@ __device__ __forceinline__ void block_sum7(double (&v)[kMomFields]) {
   __syncthreads();
 }
 
+// Element-local moments in reference coordinates, with the GLL weights:
+// m_ab = sum_ij w_i w_j xi_i^a xi_j^b u_ij (a + b <= 2) and sum w_i w_j |u_ij|,
+// accumulated in the state precision T (tensor product: rows first).
+template <typename T, int P>
+__device__ __forceinline__ void local_moments(const T *__restrict__ ue, const T (&w)[P + 1],
+                                              const T (&wx)[P + 1], const T (&wxx)[P + 1],
+                                              T (&lm)[7]) {
+  constexpr int n = P + 1;
+  for (int k = 0; k < 7; ++k) lm[k] = (T)0;
+#pragma unroll
+  for (int j = 0; j < n; ++j) {
+    T r0 = 0, r1 = 0, r2 = 0, ra = 0;
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+      const T v = ue[j * n + i];
+      r0 += w[i] * v;
+      r1 += wx[i] * v;
+      r2 += wxx[i] * v;
+      ra += w[i] * fabs(v);
+    }
+    lm[0] += w[j] * r0;    // m00
+    lm[1] += w[j] * r1;    // m10
+    lm[2] += wx[j] * r0;   // m01
+    lm[3] += w[j] * r2;    // m20
+    lm[4] += wx[j] * r1;   // m11
+    lm[5] += wxx[j] * r0;  // m02
+    lm[6] += w[j] * ra;    // |u| mass
+  }
+}
+
+// Adds the element's contribution to the FP64 moments about the start point:
+// node displacement (X + J xi_i, Y + J xi_j) with (X, Y) = element centre - xs.
+__device__ __forceinline__ void add_element_moments(double X, double Y, double J,
+                                                    const double (&lm)[7],
+                                                    double (&acc)[kMomFields]) {
+  const double J2 = J * J;
+  const double m00 = lm[0], m10 = J * lm[1], m01 = J * lm[2];
+  const double m20 = J2 * lm[3], m11 = J2 * lm[4], m02 = J2 * lm[5];
+  acc[0] += J2 * m00;
+  acc[1] += J2 * (X * m00 + m10);
+  acc[2] += J2 * (Y * m00 + m01);
+  acc[3] += J2 * (X * X * m00 + 2.0 * X * m10 + m20);
+  acc[4] += J2 * (X * Y * m00 + X * m01 + Y * m10 + m11);
+  acc[5] += J2 * (Y * Y * m00 + 2.0 * Y * m01 + m02);
+  acc[6] += J2 * lm[6];
+}
+
 template <typename T, int P>
 __global__ void __launch_bounds__(256)
     k_moments(const int2 *__restrict__ exy, long long nA, long long stride,
@@ -97,28 +167,26 @@ __global__ void __launch_bounds__(256)
   const int s = blockIdx.y;
   const double xs = src[2 * s], ys = src[2 * s + 1];
   const double J = 0.5 * g.h;
+  T w[n], wx[n], wxx[n];
+#pragma unroll
+  for (int i = 0; i < n; ++i) {
+    w[i] = (T)g.w[i];
+    wx[i] = (T)(g.w[i] * g.xi[i]);
+    wxx[i] = (T)(g.w[i] * g.xi[i] * g.xi[i]);
+  }
   double acc[kMomFields] = {0, 0, 0, 0, 0, 0, 0};
   const T *U = u + (size_t)s * stride * NP;
   for (long long a = (long long)blockIdx.x * 256 + threadIdx.x; a < nA;
        a += (long long)gridDim.x * 256) {
     const int2 e = exy[a];
-    const T *ue = U + (size_t)a * NP;
+    T lmT[7];
+    local_moments<T, P>(U + (size_t)a * NP, w, wx, wxx, lmT);
+    double lm[7];
 #pragma unroll
-    for (int j = 0; j < n; ++j) {
-      const double y = g.y0 + (e.y + 0.5) * g.h + J * g.xi[j] - ys;
-#pragma unroll
-      for (int i = 0; i < n; ++i) {
-        const double x = g.x0 + (e.x + 0.5) * g.h + J * g.xi[i] - xs;
-        const double wu = J * J * g.w[i] * g.w[j] * (double)ue[j * n + i];
-        acc[0] += wu;
-        acc[1] += wu * x;
-        acc[2] += wu * y;
-        acc[3] += wu * x * x;
-        acc[4] += wu * x * y;
-        acc[5] += wu * y * y;
-        acc[6] += fabs(wu);
-      }
-    }
+    for (int k = 0; k < 7; ++k) lm[k] = (double)lmT[k];
+    const double X = g.x0 + (e.x + 0.5) * g.h - xs;
+    const double Y = g.y0 + (e.y + 0.5) * g.h - ys;
+    add_element_moments(X, Y, J, lm, acc);
   }
   block_sum7(acc);
   if (threadIdx.x == 0) {
@@ -246,11 +314,16 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// res[1] = 1 / sqrt(res[0]), once
+__global__ void k_inv_norm(double *__restrict__ res) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) res[1] = 1.0 / sqrt(res[0]);
+}
+
 __global__ void k_scale_rnorm(long long nvals, const double *__restrict__ in,
                               const double *__restrict__ res, double *__restrict__ out) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nvals) return;
-  out[t] = in[t] / sqrt(res[0]);
+  out[t] = in[t] * res[1];
 }
 
 // ---- launchers ----------------------------------------------------------------
@@ -355,6 +428,7 @@ cudaError_t launch_wnorm2(const Ctx &c, const double *v, double *d_part, double 
 cudaError_t launch_scale_by_rnorm(const Ctx &c, const double *in, const double *d_res,
                                   double *out, cudaStream_t s) {
   const long long nv = c.geo.n_active * c.np();
+  k_inv_norm<<<1, 32, 0, s>>>(const_cast<double *>(d_res));
   k_scale_rnorm<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(nv, in, d_res, out);
   return cudaGetLastError();
 }

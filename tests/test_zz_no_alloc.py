@@ -60,8 +60,10 @@ def test_static_moments_match_context_moments():
         assert rc == dg.DG_OK, f"call {call}: status {rc}"
         stream.synchronize()
         got = out.cpu().numpy()
-        # same FP64 sums in another order: the FP64 tolerance of the suite
-        assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max(), (call, got, ref)
+        # the suite's tolerances: FP64 1e-10; FP32 densities 1e-5 (dg_moments
+        # forms their element-local sums in FP32)
+        tol = 1e-10 if prec_name == "f64" else 1e-5
+        assert np.abs(got - ref).max() <= tol * np.abs(ref).max(), (call, got, ref)
 
     # a size beyond the fixed scratch is refused before any device work
     big = torch.zeros((129, 1, 1, 4, 4), dtype=torch.float64, device="cuda:0")
