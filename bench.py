@@ -344,6 +344,7 @@ def main():
                    "active_elements": inf.n_active, "densities_per_gpu": m,
                    "dof_per_density": inf.dof_per_source, "rk_steps_per_bench_step": R,
                    "dt_ms": dt, "rho_per_ms": rho, "packing": w.disks.packing,
+                   "halo_max_per_block": inf.halo_max,
                    "disks": w.disks.n, "l2": "state (>=16 GB) larger than L2, no flush"},
         "sigma_solves_per_s": value / (inf.dof_per_source * nsteps_50),
         "sigma_solve_note": f"derived: one density to Delta = 50 ms takes {nsteps_50} RK steps",

@@ -95,6 +95,8 @@ typedef struct dg_info {
   double t;               /* current time (ms) */
   long long steps;        /* RK steps taken since dg_set_sources */
   size_t state_bytes;     /* device bytes of the three RK state arrays */
+  int halo_max;           /* largest number of out-of-block face neighbours of
+                             a block of 256 consecutive elements */
 } dg_info;
 
 /* Fill *cfg with defaults: p=3, FP64, D=2, sigma0=0.2, eta=0, cfl 0.9,

@@ -46,7 +46,7 @@ class dg_info(ctypes.Structure):
                 ("m", ctypes.c_int), ("precision", ctypes.c_int),
                 ("h", ctypes.c_double), ("x0", ctypes.c_double), ("y0", ctypes.c_double),
                 ("t", ctypes.c_double), ("steps", ctypes.c_longlong),
-                ("state_bytes", ctypes.c_size_t)]
+                ("state_bytes", ctypes.c_size_t), ("halo_max", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

@@ -91,12 +91,12 @@ cudaError_t rk3_step(Ctx &c, double dt, cudaStream_t s) {
     if (c.cfg.precision == DG_FP64) {
       StageCoef<double> sc{co[k][0], co[k][1], co[k][2], pen, wallA};
       e = launch_stage_f64(c.cfg.p, (const double *)in[k], (const double *)base[k],
-                           (double *)outp[k], c.geo.d_nb, nA, st, c.m, c.gll, sc, s);
+                           (double *)outp[k], c.geo, st, c.m, c.gll, sc, s);
     } else {
       StageCoef<float> sc{(float)co[k][0], (float)co[k][1], (float)co[k][2], (float)pen,
                           wallA};
       e = launch_stage_f32(c.cfg.p, (const float *)in[k], (const float *)base[k],
-                           (float *)outp[k], c.geo.d_nb, nA, st, c.m, c.gll, sc, s);
+                           (float *)outp[k], c.geo, st, c.m, c.gll, sc, s);
     }
   }
   return e;
@@ -164,8 +164,7 @@ int ensure_rho(dg_ctx *ctx) {
   if (e == cudaSuccess) e = launch_wnorm2(c, v, part, res, c.stream);
   if (e == cudaSuccess) e = launch_scale_by_rnorm(c, v, res, v, c.stream);
   for (int it = 0; it < iters && e == cudaSuccess; ++it) {
-    e = launch_stage_f64(c.cfg.p, v, nullptr, w, c.geo.d_nb, c.geo.n_active, c.geo.n_pad, 1,
-                         c.gll, sc, c.stream);
+    e = launch_stage_f64(c.cfg.p, v, nullptr, w, c.geo, c.geo.n_pad, 1, c.gll, sc, c.stream);
     if (e == cudaSuccess) e = launch_wnorm2(c, w, part, res, c.stream);
     if (e == cudaSuccess && it + 1 < iters) e = launch_scale_by_rnorm(c, w, res, v, c.stream);
   }
@@ -451,6 +450,7 @@ int dg_get_info(dg_ctx *ctx, dg_info *info) {
   info->t = c.t;
   info->steps = c.steps;
   info->state_bytes = c.state_bytes;
+  info->halo_max = c.geo.halo_max;
   return DG_OK;
 }
 
@@ -586,12 +586,12 @@ int dg_apply_operator(dg_ctx *ctx) {
   cudaError_t e;
   if (c.cfg.precision == DG_FP64) {
     StageCoef<double> sc{0.0, 0.0, kc, pen, wallA};
-    e = launch_stage_f64(c.cfg.p, (const double *)U0, nullptr, (double *)U1, c.geo.d_nb, c.geo.n_active,
-                         c.geo.n_pad, c.m, c.gll, sc, c.stream);
+    e = launch_stage_f64(c.cfg.p, (const double *)U0, nullptr, (double *)U1, c.geo, c.geo.n_pad, c.m,
+                         c.gll, sc, c.stream);
   } else {
     StageCoef<float> sc{0.0f, 0.0f, (float)kc, (float)pen, wallA};
-    e = launch_stage_f32(c.cfg.p, (const float *)U0, nullptr, (float *)U1, c.geo.d_nb, c.geo.n_active,
-                         c.geo.n_pad, c.m, c.gll, sc, c.stream);
+    e = launch_stage_f32(c.cfg.p, (const float *)U0, nullptr, (float *)U1, c.geo, c.geo.n_pad, c.m,
+                         c.gll, sc, c.stream);
   }
   CK(e, "operator launch");
   CK(cudaMemcpyAsync(U0, U1, (size_t)c.m * c.field_elems() * c.esize(), cudaMemcpyDeviceToDevice, c.stream), "copy");

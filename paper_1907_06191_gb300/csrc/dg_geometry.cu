@@ -171,16 +171,86 @@ __global__ void k_neighbours(const int2 *__restrict__ exy, const int *__restrict
   nb[a] = make_int4(res[0], res[1], res[2], res[3]);
 }
 
+// ---- halo lists ----------------------------------------------------------
+// One block per chunk of kBlock consecutive elements.  For each face f (in
+// order), the elements whose neighbour across f lies outside the chunk get
+// consecutive halo slots (block-wide prefix of a ballot), so the table does
+// not depend on scheduling.  A halo entry is {neighbour, neighbour's face
+// toward the chunk element} = {k, f ^ 1}.
+__global__ void k_halo(const int4 *__restrict__ nb, int nA, int4 *__restrict__ loc,
+                       int2 *__restrict__ halo, int *__restrict__ halo_cnt) {
+  __shared__ int wsum[kBlock / 32];
+  __shared__ int base_s;
+  const int c = blockIdx.x;
+  const int a0 = c * kBlock;
+  const int el = threadIdx.x;
+  const int a = a0 + el;
+  const bool live = a < nA;
+  const int4 q = live ? nb[a] : make_int4(kEdge, kEdge, kEdge, kEdge);
+  int qn[4] = {q.x, q.y, q.z, q.w};
+  int out[4];
+  const int lane = el & 31, wid = el >> 5;
+  if (el == 0) base_s = 0;
+  __syncthreads();
+  for (int f = 0; f < 4; ++f) {
+    const int k = qn[f];
+    const bool inside = k >= a0 && k < a0 + kBlock && k < nA;
+    const bool need = live && k >= 0 && !inside;
+    const unsigned bal = __ballot_sync(0xffffffffu, need);
+    if (lane == 0) wsum[wid] = __popc(bal);
+    __syncthreads();
+    int pre = 0, tot = 0;
+    for (int w = 0; w < kBlock / 32; ++w) {
+      if (w < wid) pre += wsum[w];
+      tot += wsum[w];
+    }
+    pre += __popc(bal & ((1u << lane) - 1u));
+    const int base = base_s;
+    if (k < 0) out[f] = k;
+    else if (inside) out[f] = k - a0;
+    else {
+      const int slot = base + pre;  // < kHaloCap by construction
+      out[f] = kBlock + slot;
+      halo[(size_t)c * kHaloCap + slot] = make_int2(k, f ^ 1);
+    }
+    __syncthreads();
+    if (el == 0) base_s = base + tot;
+    __syncthreads();
+  }
+  if (live) loc[a] = make_int4(out[0], out[1], out[2], out[3]);
+  if (el == 0) halo_cnt[c] = base_s;
+}
+
+__global__ void k_max_int(const int *__restrict__ v, int n, int *__restrict__ out) {
+  __shared__ int sm[256];
+  int m = 0;
+  for (int i = threadIdx.x; i < n; i += 256) m = max(m, v[i]);
+  sm[threadIdx.x] = m;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sm[threadIdx.x] = max(sm[threadIdx.x], sm[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sm[0];
+}
+
 void free_geometry(Geometry &geo) {
   cudaFree(geo.d_mask);
   cudaFree(geo.d_cidx);
   cudaFree(geo.d_nb);
   cudaFree(geo.d_exy);
+  cudaFree(geo.d_loc);
+  cudaFree(geo.d_halo);
+  cudaFree(geo.d_halo_cnt);
   geo.d_mask = nullptr;
   geo.d_cidx = nullptr;
   geo.d_nb = nullptr;
   geo.d_exy = nullptr;
+  geo.d_loc = nullptr;
+  geo.d_halo = nullptr;
+  geo.d_halo_cnt = nullptr;
   geo.n_active = 0;
+  geo.halo_max = 0;
 }
 
 // geo.d_mask, nx, ny must be set.  Returns a DG_* code.
@@ -236,6 +306,33 @@ int build_connectivity(Geometry &geo, int periodic, cudaStream_t s, std::string 
   if (bad) {
     err = "neighbour table out of range";
     code = DG_ECUDA;
+    goto done;
+  }
+  {
+    const int nch = (int)((total + kBlock - 1) / kBlock);
+    int hmax = 0;
+    if ((e = cudaMalloc(&geo.d_loc, sizeof(int4) * (size_t)total)) != cudaSuccess ||
+        (e = cudaMalloc(&geo.d_halo, sizeof(int2) * (size_t)nch * kHaloCap)) != cudaSuccess ||
+        (e = cudaMalloc(&geo.d_halo_cnt, sizeof(int) * ((size_t)nch + 1))) != cudaSuccess) {
+      err = std::string("halo table allocation: ") + cudaGetErrorString(e);
+      code = DG_ENOMEM;
+      goto done;
+    }
+    k_halo<<<nch, kBlock, 0, s>>>(geo.d_nb, total, geo.d_loc, geo.d_halo, geo.d_halo_cnt);
+    k_max_int<<<1, 256, 0, s>>>(geo.d_halo_cnt, nch, geo.d_halo_cnt + nch);
+    if ((e = cudaMemcpyAsync(&hmax, geo.d_halo_cnt + nch, sizeof(int), cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+      err = std::string("halo table: ") + cudaGetErrorString(e);
+      code = DG_ECUDA;
+      goto done;
+    }
+    if (hmax < 0 || hmax > kHaloCap) {
+      err = "halo table out of range";
+      code = DG_ECUDA;
+      goto done;
+    }
+    geo.halo_max = hmax;
   }
 done:
   cudaFree(d_count);

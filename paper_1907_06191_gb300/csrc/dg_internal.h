@@ -17,6 +17,7 @@ constexpr int kBlock = 256;         // threads per block of the element kernels
 constexpr int kTile = 16;           // element ordering: 16 x 16 tiles, row-major inside
 constexpr int kMomBlocks = 608;     // fixed grid of the moment reduction (4 x 152 SMs)
 constexpr int kMomFields = 7;       // M0, Mx, My, Mxx, Mxy, Myy, |u| mass
+constexpr int kHaloCap = 4 * 256;   // halo entries a chunk can have (4 faces x kBlock)
 
 // Face codes in the neighbour table (>= 0: neighbour element index).
 constexpr int kWall = -1;
@@ -60,6 +61,14 @@ struct Geometry {
   int4 *d_nb = nullptr;         // [n_active] E, W, N, S
   int2 *d_exy = nullptr;        // [n_active] element coordinates
   std::vector<uint8_t> h_mask;  // host copy of d_mask
+  // Per block of kBlock consecutive elements ("chunk"): face neighbours
+  // outside the chunk are halo entries {element, its face toward the chunk}.
+  // d_loc gives, per element and face, the chunk-local index (0..kBlock-1),
+  // kBlock + halo slot, kWall or kEdge.
+  int4 *d_loc = nullptr;        // [n_active]
+  int2 *d_halo = nullptr;       // [n_chunks][kHaloCap]
+  int *d_halo_cnt = nullptr;    // [n_chunks]
+  int halo_max = 0;             // largest halo of any chunk
 };
 
 struct Ctx {
@@ -107,10 +116,10 @@ struct Ctx {
 // ---- launchers (defined in the .cu files) ----
 // One stage over all m densities: out = alpha u0 + beta u + gamma R(u).
 cudaError_t launch_stage_f64(int p, const double *u, const double *u0, double *out,
-                             const int4 *nb, long long nA, long long stride, int m,
+                             const Geometry &geo, long long stride, int m,
                              const Gll &g, const StageCoef<double> &c, cudaStream_t s);
 cudaError_t launch_stage_f32(int p, const float *u, const float *u0, float *out,
-                             const int4 *nb, long long nA, long long stride, int m,
+                             const Geometry &geo, long long stride, int m,
                              const Gll &g, const StageCoef<float> &c, cudaStream_t s);
 
 // Geometry construction.

@@ -24,6 +24,8 @@
 // faces the lifting parts of q^- and q^+ cancel in q_hat - k q^-.
 #pragma once
 
+#include <algorithm>
+
 #include "dg_internal.h"
 
 namespace dg {
@@ -199,26 +201,106 @@ __device__ __forceinline__ void outward_derivative(const T (&u)[(P + 1) * (P + 1
   }
 }
 
+// Face records in shared memory: for record r, the trace tr[t] and the
+// outward normal derivative d[t] (t = 0..n-1) of one element face.  Record
+// f*kBlock + e is face f of chunk element e; record 4*kBlock + h is halo entry
+// h; the last record is all zeros (read for walls and edges).  When n values
+// fill one 16-byte slot, record r is slot r of each array; otherwise the
+// arrays are transposed ([t][r]).  Either way threads reading consecutive
+// records hit distinct banks.
+template <typename T, int P>
+struct Records {
+  static constexpr int n = P + 1;
+  static constexpr bool VEC = n * (int)sizeof(T) == 16;
+  T *tr, *d;
+  int nrec;
+  __device__ __forceinline__ void put(int r, const T (&a)[n], const T (&b)[n]) const {
+    if constexpr (VEC) {
+      float4 va, vb;
+      T *pa = reinterpret_cast<T *>(&va), *pb = reinterpret_cast<T *>(&vb);
+#pragma unroll
+      for (int t = 0; t < n; ++t) { pa[t] = a[t]; pb[t] = b[t]; }
+      reinterpret_cast<float4 *>(tr)[r] = va;
+      reinterpret_cast<float4 *>(d)[r] = vb;
+    } else {
+#pragma unroll
+      for (int t = 0; t < n; ++t) {
+        tr[t * nrec + r] = a[t];
+        d[t * nrec + r] = b[t];
+      }
+    }
+  }
+  __device__ __forceinline__ void get_tr(int r, T (&a)[n]) const {
+    if constexpr (VEC) {
+      const float4 v = reinterpret_cast<const float4 *>(tr)[r];
+      const T *pv = reinterpret_cast<const T *>(&v);
+#pragma unroll
+      for (int t = 0; t < n; ++t) a[t] = pv[t];
+    } else {
+#pragma unroll
+      for (int t = 0; t < n; ++t) a[t] = tr[t * nrec + r];
+    }
+  }
+  __device__ __forceinline__ void get_d(int r, T (&a)[n]) const {
+    if constexpr (VEC) {
+      const float4 v = reinterpret_cast<const float4 *>(d)[r];
+      const T *pv = reinterpret_cast<const T *>(&v);
+#pragma unroll
+      for (int t = 0; t < n; ++t) a[t] = pv[t];
+    } else {
+#pragma unroll
+      for (int t = 0; t < n; ++t) a[t] = d[t * nrec + r];
+    }
+  }
+  __host__ __device__ static constexpr int bytes(int nrec_) {
+    return 2 * ((nrec_ * n * (int)sizeof(T) + 15) / 16) * 16;
+  }
+};
+
+template <typename T, int P>
+__device__ __forceinline__ void face_record(const T (&u)[(P + 1) * (P + 1)], int f,
+                                            const StageTab<T, P> &tb, T (&tr)[P + 1],
+                                            T (&d)[P + 1]) {
+  outward_derivative<T, P>(u, f, tb, d);
+#pragma unroll
+  for (int t = 0; t < P + 1; ++t) tr[t] = u[Faces<P>::own(f, t)];
+}
+
 // grid: (ceil(nA / kBlock), m); density s = blockIdx.y starts at s * stride
-// elements.  nb entries are < nA (checked when the table is built).  out may
-// alias u0 (the last stage updates u^n in place: a block reads its whole u0
-// chunk into shared memory before it writes the same chunk); it never aliases
-// uin.  Shared memory: chunk of u, chunk of u0 (then of the result), and the
-// outward face derivatives [4][kBlock][n].
+// elements.  loc/halo tables come from the geometry (entries checked when
+// built).  out may alias u0 (the last stage updates u^n in place: a block
+// reads its whole u0 chunk into shared memory before it writes the same
+// chunk); it never aliases uin.  Shared memory: chunk of u, chunk of u0 (then
+// of the result), face records.
+template <typename T, int P>
+constexpr int stage_min_blocks() {
+  // blocks of 256 threads per SM the register budget is sized for:
+  // 4 -> 64 registers, 2 -> 128, 1 -> 255
+  if constexpr (sizeof(T) == 4) return P <= 3 ? 4 : 2;
+  else return P <= 3 ? 2 : 1;
+}
+
 template <typename T, int P, bool HAS_U0>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
     k_stage(const T *__restrict__ uin, const T *u0, T *out,
-            const int4 *__restrict__ nb, long long nA, long long stride,
+            const int4 *__restrict__ loc, const int2 *__restrict__ halo,
+            const int *__restrict__ halo_cnt, long long nA, long long stride, int nrec,
             const StageTab<T, P> tb, const StageCoef<T> c) {
   constexpr int n = P + 1, NP = n * n;
   using St = Stage<T, NP>;
   using Fc = Faces<P>;
+  // shared memory: [u chunk, later the face records][u0 chunk, later the result]
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int front = max(St::CHUNK_BYTES, Records<T, P>::bytes(nrec));
   T *su = reinterpret_cast<T *>(smem_raw);
-  T *so = reinterpret_cast<T *>(smem_raw + St::CHUNK_BYTES);
-  T *sd = reinterpret_cast<T *>(smem_raw + 2 * St::CHUNK_BYTES);
+  T *so = reinterpret_cast<T *>(smem_raw + front);
+  T *rec_base = reinterpret_cast<T *>(smem_raw);
+  Records<T, P> rec{rec_base,
+                    rec_base + ((nrec * n * (int)sizeof(T) + 15) / 16) * 16 / (int)sizeof(T), nrec};
+  const int zero_rec = nrec - 1;
 
-  const long long a0 = (long long)blockIdx.x * kBlock;
+  const int chunk = blockIdx.x;
+  const long long a0 = (long long)chunk * kBlock;
   const int cnt = (int)min((long long)kBlock, nA - a0);
   const int el = threadIdx.x;
   const bool live = el < cnt;
@@ -238,22 +320,36 @@ __global__ void __launch_bounds__(kBlock)
       cp_async_commit();
     }
   }
-  const int4 f4 = live ? __ldg(nb + a0 + el) : make_int4(kEdge, kEdge, kEdge, kEdge);
+  const int4 l4 = live ? __ldg(loc + a0 + el) : make_int4(kEdge, kEdge, kEdge, kEdge);
+  const int hcnt = __ldg(halo_cnt + chunk);
+  // first halo entry of this thread: element values into registers while the
+  // chunk copies are in flight
+  int2 hk = make_int2(-1, 0);
+  T hv[NP];
+  if (el < hcnt) {
+    hk = __ldg(halo + (size_t)chunk * kHaloCap + el);
+    load_elem<T, NP>(U + (size_t)hk.x * NP, hv);
+  }
   if constexpr (HAS_U0) cp_async_wait<1>();
   else cp_async_wait<0>();
   __syncthreads();
 
   T u[NP], R[NP];
+  if (live) St::read(su, el, u);
+  __syncthreads();  // the u chunk is in registers; its space now takes the face records
+  if (el == 0) {
+    T z[n];
+#pragma unroll
+    for (int t = 0; t < n; ++t) z[t] = (T)0;
+    rec.put(zero_rec, z, z);
+  }
   if (live) {
-    St::read(su, el, u);
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-      T d[n];
-      outward_derivative<T, P>(u, f, tb, d);
-#pragma unroll
-      for (int t = 0; t < n; ++t) sd[(f * kBlock + el) * n + t] = d[t];
+      T tr[n], d[n];
+      face_record<T, P>(u, f, tb, tr, d);
+      rec.put(f * kBlock + el, tr, d);
     }
-    // volume: (D D) along x and along y
 #pragma unroll
     for (int j = 0; j < n; ++j)
 #pragma unroll
@@ -265,70 +361,69 @@ __global__ void __launch_bounds__(kBlock)
         R[j * n + i] = s;
       }
   }
+  if (el < hcnt) {
+    T tr[n], d[n];
+    switch (hk.y) {  // the face of the halo element that touches the chunk
+      case 0: face_record<T, P>(hv, 0, tb, tr, d); break;
+      case 1: face_record<T, P>(hv, 1, tb, tr, d); break;
+      case 2: face_record<T, P>(hv, 2, tb, tr, d); break;
+      default: face_record<T, P>(hv, 3, tb, tr, d); break;
+    }
+    rec.put(4 * kBlock + el, tr, d);
+  }
+  for (int h = el + kBlock; h < hcnt; h += kBlock) {  // chunks with > kBlock halo entries
+    const int2 q = __ldg(halo + (size_t)chunk * kHaloCap + h);
+    T v[NP], tr[n], d[n];
+    load_elem<T, NP>(U + (size_t)q.x * NP, v);
+    switch (q.y) {
+      case 0: face_record<T, P>(v, 0, tb, tr, d); break;
+      case 1: face_record<T, P>(v, 1, tb, tr, d); break;
+      case 2: face_record<T, P>(v, 2, tb, tr, d); break;
+      default: face_record<T, P>(v, 3, tb, tr, d); break;
+    }
+    rec.put(4 * kBlock + h, tr, d);
+  }
   __syncthreads();
 
   if (live) {
-    const int nbk[4] = {f4.x, f4.y, f4.z, f4.w};
+    const int lq[4] = {l4.x, l4.y, l4.z, l4.w};
+    const T half = (T)0.5;
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-      const int k = nbk[f];
+      const int L = lq[f];
       const int fo = Fc::opp(f);
-      T g[n], odf[n];
+      // neighbour record: chunk element, halo entry, or the zero record
+      const int rn = L >= kBlock ? 4 * kBlock + (L - kBlock) : (L >= 0 ? fo * kBlock + L : zero_rec);
+      // face-kind coefficients: g = cg_up u+ + cg_um u-,
+      // F = -(c_od d- + c_odn d+ + c_um u- + c_up u+) / w   (see file header)
+      const bool in = L >= 0, wl = L == kWall, wa = wl && c.wallA, ed = L == kEdge;
+      const T cg_up = in ? half : (T)0;
+      const T cg_um = in ? -half : (wa ? -half : (ed ? (T)-1 : (T)0));
+      const T c_od = in ? half : (ed ? (T)0 : (T)1);
+      const T c_odn = in ? half : (T)0;
+      const T c_um = in ? c.pen : (wa ? -half * tb.inv_w : (ed ? c.pen : (T)0));
+      const T c_up = in ? -c.pen : (T)0;
+      T up[n], odn[n], od[n];
+      rec.get_tr(rn, up);
+      rec.get_d(rn, odn);
+      rec.get_d(f * kBlock + el, od);
+      T g[n];
 #pragma unroll
-      for (int t = 0; t < n; ++t) odf[t] = sd[(f * kBlock + el) * n + t];
-      bool lift = true;
-      if (k >= 0) {
-        T up[n], odn[n];
-        const long long loc = (long long)k - a0;
-        if (loc >= 0 && loc < cnt) {
-#pragma unroll
-          for (int t = 0; t < n; ++t) {
-            up[t] = su[St::word((int)loc, Fc::own(fo, t))];
-            odn[t] = sd[(fo * kBlock + (int)loc) * n + t];
-          }
-        } else {
-          T v[NP];
-          load_elem<T, NP>(U + (size_t)k * NP, v);
-          outward_derivative<T, P>(v, fo, tb, odn);
-#pragma unroll
-          for (int t = 0; t < n; ++t) up[t] = v[Fc::own(fo, t)];
-        }
-#pragma unroll
-        for (int t = 0; t < n; ++t) {
-          const T um = u[Fc::own(f, t)];
-          g[t] = (T)0.5 * (up[t] - um);
-          R[Fc::own(f, t)] -= tb.inv_w * ((T)0.5 * (odf[t] + odn[t]) + c.pen * (um - up[t]));
-        }
-      } else if (k == kWall && !c.wallA) {
-#pragma unroll
-        for (int t = 0; t < n; ++t) R[Fc::own(f, t)] -= tb.inv_w * odf[t];
-        lift = false;
-      } else if (k == kWall) {
-#pragma unroll
-        for (int t = 0; t < n; ++t) {
-          g[t] = (T)-0.5 * u[Fc::own(f, t)];
-          R[Fc::own(f, t)] -= tb.inv_w * (odf[t] + tb.inv_w * g[t]);
-        }
-      } else {
-#pragma unroll
-        for (int t = 0; t < n; ++t) {
-          const T um = u[Fc::own(f, t)];
-          g[t] = -um;
-          R[Fc::own(f, t)] -= tb.inv_w * c.pen * um;
-        }
+      for (int t = 0; t < n; ++t) {
+        const T um = u[Fc::own(f, t)];
+        g[t] = cg_up * up[t] + cg_um * um;
+        R[Fc::own(f, t)] -= tb.inv_w * (c_od * od[t] + c_odn * odn[t] + c_um * um + c_up * up[t]);
       }
-      if (lift) {
-        // lifting of the u-flux jump: column (x-faces) or row (y-faces) of D
-        const int r = Fc::row(f);
-        const T sg = (T)Fc::sgn(f);
+      // lifting of the u-flux jump: column (x-faces) or row (y-faces) of D
+      const int r = Fc::row(f);
+      const T sg = (T)Fc::sgn(f);
 #pragma unroll
-        for (int t = 0; t < n; ++t) {
-          const T gs = sg * tb.inv_w * g[t];
+      for (int t = 0; t < n; ++t) {
+        const T gs = sg * tb.inv_w * g[t];
 #pragma unroll
-          for (int q = 0; q < n; ++q) {
-            if (f < 2) R[t * n + q] += tb.D[q * n + r] * gs;
-            else R[q * n + t] += tb.D[q * n + r] * gs;
-          }
+        for (int q = 0; q < n; ++q) {
+          if (f < 2) R[t * n + q] += tb.D[q * n + r] * gs;
+          else R[q * n + t] += tb.D[q * n + r] * gs;
         }
       }
     }
@@ -361,8 +456,10 @@ __global__ void __launch_bounds__(kBlock)
 }
 
 template <typename T, int P>
-constexpr int stage_smem_bytes() {
-  return 2 * Stage<T, (P + 1) * (P + 1)>::CHUNK_BYTES + 4 * kBlock * (P + 1) * (int)sizeof(T);
+int stage_smem_bytes(int halo_max) {
+  const int nrec = 4 * kBlock + halo_max + 1;
+  const int chunk = Stage<T, (P + 1) * (P + 1)>::CHUNK_BYTES;
+  return std::max(chunk, Records<T, P>::bytes(nrec)) + chunk;
 }
 
 template <typename T, int P>
@@ -378,40 +475,44 @@ StageTab<T, P> make_tab(const Gll &g) {
 }
 
 template <typename T, int P>
-cudaError_t launch_stage_p(const T *u, const T *u0, T *out, const int4 *nb, long long nA,
+cudaError_t launch_stage_p(const T *u, const T *u0, T *out, const Geometry &geo,
                            long long stride, int m, const Gll &g, const StageCoef<T> &c,
                            cudaStream_t s) {
+  const long long nA = geo.n_active;
   if (nA <= 0 || m <= 0) return cudaSuccess;
   const dim3 grid((unsigned)((nA + kBlock - 1) / kBlock), (unsigned)m);
   const StageTab<T, P> tb = make_tab<T, P>(g);
-  constexpr int smem = stage_smem_bytes<T, P>();
-  static bool attr_set = false;  // per instantiation, first launch
-  if (!attr_set) {
+  const int nrec = 4 * kBlock + geo.halo_max + 1;
+  const int smem = stage_smem_bytes<T, P>(geo.halo_max);
+  static int attr_bytes = 0;  // per instantiation: largest size configured so far
+  if (smem > attr_bytes) {
     cudaError_t e = cudaFuncSetAttribute(k_stage<T, P, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_stage<T, P, false>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_bytes = smem;
   }
   if (u0)
-    k_stage<T, P, true><<<grid, kBlock, smem, s>>>(u, u0, out, nb, nA, stride, tb, c);
+    k_stage<T, P, true><<<grid, kBlock, smem, s>>>(u, u0, out, geo.d_loc, geo.d_halo,
+                                                   geo.d_halo_cnt, nA, stride, nrec, tb, c);
   else
-    k_stage<T, P, false><<<grid, kBlock, smem, s>>>(u, u0, out, nb, nA, stride, tb, c);
+    k_stage<T, P, false><<<grid, kBlock, smem, s>>>(u, u0, out, geo.d_loc, geo.d_halo,
+                                                    geo.d_halo_cnt, nA, stride, nrec, tb, c);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_stage_any(int p, const T *u, const T *u0, T *out, const int4 *nb,
-                             long long nA, long long stride, int m, const Gll &g,
-                             const StageCoef<T> &c, cudaStream_t s) {
+cudaError_t launch_stage_any(int p, const T *u, const T *u0, T *out, const Geometry &geo,
+                             long long stride, int m, const Gll &g, const StageCoef<T> &c,
+                             cudaStream_t s) {
   switch (p) {
-    case 1: return launch_stage_p<T, 1>(u, u0, out, nb, nA, stride, m, g, c, s);
-    case 2: return launch_stage_p<T, 2>(u, u0, out, nb, nA, stride, m, g, c, s);
-    case 3: return launch_stage_p<T, 3>(u, u0, out, nb, nA, stride, m, g, c, s);
-    case 4: return launch_stage_p<T, 4>(u, u0, out, nb, nA, stride, m, g, c, s);
-    case 5: return launch_stage_p<T, 5>(u, u0, out, nb, nA, stride, m, g, c, s);
+    case 1: return launch_stage_p<T, 1>(u, u0, out, geo, stride, m, g, c, s);
+    case 2: return launch_stage_p<T, 2>(u, u0, out, geo, stride, m, g, c, s);
+    case 3: return launch_stage_p<T, 3>(u, u0, out, geo, stride, m, g, c, s);
+    case 4: return launch_stage_p<T, 4>(u, u0, out, geo, stride, m, g, c, s);
+    case 5: return launch_stage_p<T, 5>(u, u0, out, geo, stride, m, g, c, s);
     default: return cudaErrorInvalidValue;
   }
 }
