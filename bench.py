@@ -185,6 +185,105 @@ def cpu_baseline_sample(w, seconds_target=20.0):
             "sample": f"1 of 64 densities x {n} SSP-RK3 steps on the full {act.shape[0]}^2 window"}
 
 
+def run_batch(args):
+    """Uneven-geometry batch: seeded geometries with 64..256 elements per cell
+    side (h = 0.156 um), p in {2, 3, 4}, packing 0.40-0.75, Gamma shape
+    1.5-3.0, 16 densities each, windows sized for Delta = 20 ms.  Geometries
+    of equal p share one context (one launch per RK stage for all of them);
+    geometries are added in seed order while the FP32 state stays under
+    --batch-gb.  The same geometries are then run one context at a time."""
+    import torch
+    import paper_1907_06191_gb300 as dg
+    from paper_1907_06191_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+    budget = args.batch_gb * 2 ** 30
+    members, used, seed = [], 0.0, 0
+    while seed < args.batch_geometries:
+        w = dginputs.workload_batch_member(seed)
+        npe = (w.p + 1) ** 2
+        est = w.n_window ** 2 * (1 - w.disks.packing) * npe * 16 * 4 * 3
+        if used + est > budget:
+            break
+        members.append(w)
+        used += est
+        seed += 1
+    groups = {}
+    for w in members:
+        groups.setdefault(w.p, []).append(w)
+    stream = torch.cuda.Stream(device=0)
+    ctxs = []
+    for p, ws in sorted(groups.items()):
+        s = dg.DGSolver(p=p, precision=dg.DG_FP32, D=2.0, sigma0=0.2, device=0)
+        s.set_stream(stream.cuda_stream)
+        s.set_geometry_batch([(w.disks.cx, w.disks.cy, w.disks.r) for w in ws],
+                             [w.L for w in ws], [w.n_cell for w in ws], [w.tiles for w in ws])
+        s.set_sources(np.stack([w.sources for w in ws]))
+        dt, _ = s.query_dt()
+        ctxs.append((s, dt, s.info()))
+    dof = sum(inf.dof_per_source * inf.m for _, _, inf in ctxs)
+    R = args.rk
+
+    def step_all():
+        for s, dt, _ in ctxs:
+            s.step(R, dt)
+        for s, _, _ in ctxs:
+            s.covariance_batch()
+
+    for _ in range(args.warmup):
+        step_all()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step_all()
+        e1.record(stream)
+        e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    batched = dof * R * args.steps / (ms * 1e-3)
+    for s, _, _ in ctxs:
+        s.close()
+    # the same geometries one context each
+    singles = []
+    for w in members:
+        s = dg.DGSolver(p=w.p, precision=dg.DG_FP32, D=2.0, sigma0=0.2, device=0)
+        s.set_stream(stream.cuda_stream)
+        s.set_geometry_disks(w.disks.cx, w.disks.cy, w.disks.r, w.L, w.n_cell, w.tiles)
+        s.set_sources(w.sources)
+        singles.append((s, dict((p, dt) for (c, dt, inf), p in zip(ctxs, sorted(groups)))[w.p]))
+    for s, dt in singles:
+        s.step(R, dt)
+        s.covariance()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        for s, dt in singles:
+            s.step(R, dt)
+        for s, dt in singles:
+            s.covariance()
+    e1.record(stream)
+    e1.synchronize()
+    ms1 = e0.elapsed_time(e1)
+    for s, _ in singles:
+        s.close()
+    line = {"metric": METRIC, "value": batched, "unit": "DoF-steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "batch_uneven_p234", "geometries": len(members),
+                       "geometries_requested": args.batch_geometries,
+                       "per_p": {str(p): len(ws) for p, ws in groups.items()},
+                       "densities_per_geometry": 16, "rk_steps_per_bench_step": R,
+                       "state_gb": used / 2 ** 30,
+                       "l2": "state larger than L2, no flush"},
+            "unbatched_value": dof * R * args.steps / (ms1 * 1e-3),
+            "gpu_launches": args.steps * len(ctxs) * (3 * R + 3),
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -198,8 +297,13 @@ def main():
                     help="start points per GPU (64 = the workload; fewer for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--workload", default="cell40", choices=["cell40", "batch"])
+    ap.add_argument("--batch-geometries", type=int, default=512)
+    ap.add_argument("--batch-gb", type=float, default=60.0)
     args = ap.parse_args()
     world, rank, local = _dist()
+    if args.workload == "batch" and args.impl == "ours":
+        return run_batch(args) if rank == 0 else 0
 
     if args.impl == "reference":
         return run_reference(args, world, rank)

@@ -97,6 +97,9 @@ typedef struct dg_info {
   size_t state_bytes;     /* device bytes of the three RK state arrays */
   int halo_max;           /* largest number of out-of-block face neighbours of
                              a block of 256 consecutive elements */
+  int n_geometries;       /* G: geometries held by the context */
+  long long n_elements_padded; /* element slots of all geometries, each padded to
+                             a multiple of 256 (the state stride per density) */
 } dg_info;
 
 /* Fill *cfg with defaults: p=3, FP64, D=2, sigma0=0.2, eta=0, cfl 0.9,
@@ -141,13 +144,30 @@ int dg_set_geometry_disks(dg_ctx *ctx, const double *cx, const double *cy,
                           const double *r, int ndisks, double L, int n_cell,
                           int tiles);
 
-/* Copy the element mask as built, [ny][nx] bytes (1 = in the mesh). */
+/* Batch of G geometries advanced together (one launch per RK stage covers
+ * all of them).  Geometry g is given like dg_set_geometry_disks: ndisks[g]
+ * disks whose centres and radii are consecutive in cx, cy, r (geometry after
+ * geometry), a periodic cell of side L[g] meshed with n_cell[g] elements per
+ * side, tiled into a tiles[g] x tiles[g] window centred on the cell (window
+ * origin -(tiles[g]/2) L[g]).  Geometries may differ in size and element
+ * side; the context's p, precision, D and wall treatment apply to all.
+ * Start points then come as [G][m][2] (dg_set_sources), moments as
+ * [G][m][6] (dg_moments), and Sigma per geometry (dg_covariance_batch); the
+ * time step bound covers every geometry.  Clears sources.  Errors:
+ * DG_EINVAL (bad counts or cells), DG_ENOMEM. */
+int dg_set_geometry_batch(dg_ctx *ctx, int G, const int *ndisks, const double *cx,
+                          const double *cy, const double *r, const double *L,
+                          const int *n_cell, const int *tiles);
+
+/* Copy the element mask as built, [ny][nx] bytes (1 = in the mesh); the
+ * first geometry of a batch. */
 int dg_get_mask(dg_ctx *ctx, uint8_t *active);
 
 /* Sizes and state of the context. */
 int dg_get_info(dg_ctx *ctx, dg_info *info);
 
-/* Start points of the Sigma scheme (Sec. 4.1): xy is [m][2] (um).  Each
+/* Start points of the Sigma scheme (Sec. 4.1): xy is [m][2] (um); for a
+ * batch of G geometries [G][m][2], m points in each geometry.  Each
  * density starts as the normalised Gaussian of width sigma0 about its point,
  * interpolated at the GLL nodes of mesh elements (Dirac data of Sec. 4.1
  * regularised).  Sets t = 0 and records the start moments for
@@ -173,7 +193,8 @@ int dg_step(dg_ctx *ctx, int nsteps, double dt);
  * the L1 norm of any density grew above twice its start value.  Delta >= t. */
 int dg_propagate_to(dg_ctx *ctx, double Delta);
 
-/* Raw FP64 moments at the current t, out[m][6] = {M0, Mx, My, Mxx, Mxy, Myy}
+/* Raw FP64 moments at the current t, out[m][6] ([G][m][6] for a batch)
+ * = {M0, Mx, My, Mxx, Mxy, Myy}
  * with M_f = sum over nodes of J^2 w_i w_j f(x - xs, y - ys) u, about each
  * start point (xs, ys) (Sec. 4.1, nodal quadrature). */
 int dg_moments(dg_ctx *ctx, double *out);
@@ -185,6 +206,10 @@ int dg_moments(dg_ctx *ctx, double *out);
  * start width removed), mu2 the mixture mean displacement, mass (m values,
  * may be NULL) each M0(t).  Computed on the device in FP64. */
 int dg_covariance(dg_ctx *ctx, double *sigma3, double *mu2, double *mass);
+
+/* dg_covariance of every geometry of a batch: sigma3 [G][3], mu2 [G][2],
+ * mass [G][m] (or NULL); the mixture of geometry g is its own m densities. */
+int dg_covariance_batch(dg_ctx *ctx, double *sigma3, double *mu2, double *mass);
 
 /* Mixture covariance (Sec. 4.1) of raw moments supplied by the caller, e.g.
  * moments of densities propagated on several GPUs and gathered: mom and mom0
@@ -199,7 +224,7 @@ int dg_mixture_covariance(dg_ctx *ctx, const double *mom, const double *mom0, in
 int dg_apply_operator(dg_ctx *ctx);
 
 /* Node values in the dense FP64 layout (see above), host buffer of
- * m * ny * nx * n * n doubles. */
+ * m * ny * nx * n * n doubles; single-geometry contexts only. */
 int dg_get_nodes(dg_ctx *ctx, double *host);
 int dg_set_nodes(dg_ctx *ctx, const double *host);
 
@@ -208,6 +233,9 @@ int dg_set_nodes(dg_ctx *ctx, const double *host);
  * element outside the mesh reads as 0.  Errors: DG_EINVAL (index out of
  * range). */
 int dg_get_elements(dg_ctx *ctx, const int *idx, int k, double *out);
+
+/* dg_get_elements for a batch: idx is [k][4] = {geometry, source, ex, ey}. */
+int dg_get_elements_batch(dg_ctx *ctx, const int *idx, int k, double *out);
 
 /* Checkpoint: dg_state_size gives the bytes of a snapshot (header, start
  * points, start moments, t, step count and the densities in the state

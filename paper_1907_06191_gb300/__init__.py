@@ -46,7 +46,8 @@ class dg_info(ctypes.Structure):
                 ("m", ctypes.c_int), ("precision", ctypes.c_int),
                 ("h", ctypes.c_double), ("x0", ctypes.c_double), ("y0", ctypes.c_double),
                 ("t", ctypes.c_double), ("steps", ctypes.c_longlong),
-                ("state_bytes", ctypes.c_size_t), ("halo_max", ctypes.c_int)]
+                ("state_bytes", ctypes.c_size_t), ("halo_max", ctypes.c_int),
+                ("n_geometries", ctypes.c_int), ("n_elements_padded", ctypes.c_longlong)]
 
 
 _P = ctypes.c_void_p
@@ -63,6 +64,7 @@ EXPORTS = {
     "dg_set_stream": (_I, [_P, _P]),
     "dg_set_geometry_mask": (_I, [_P, _P, _I, _I, _D, _D, _D]),
     "dg_set_geometry_disks": (_I, [_P, _DP, _DP, _DP, _I, _D, _I, _I]),
+    "dg_set_geometry_batch": (_I, [_P, _I, _P, _DP, _DP, _DP, _DP, _P, _P]),
     "dg_get_mask": (_I, [_P, _P]),
     "dg_get_info": (_I, [_P, ctypes.POINTER(dg_info)]),
     "dg_set_sources": (_I, [_P, _DP, _I]),
@@ -71,11 +73,13 @@ EXPORTS = {
     "dg_propagate_to": (_I, [_P, _D]),
     "dg_moments": (_I, [_P, _DP]),
     "dg_covariance": (_I, [_P, _DP, _DP, _DP]),
+    "dg_covariance_batch": (_I, [_P, _DP, _DP, _DP]),
     "dg_mixture_covariance": (_I, [_P, _DP, _DP, _I, _DP, _DP]),
     "dg_apply_operator": (_I, [_P]),
     "dg_get_nodes": (_I, [_P, _DP]),
     "dg_set_nodes": (_I, [_P, _DP]),
     "dg_get_elements": (_I, [_P, _P, _I, _DP]),
+    "dg_get_elements_batch": (_I, [_P, _P, _I, _DP]),
     "dg_state_size": (_I, [_P, ctypes.POINTER(_SZ)]),
     "dg_get_state": (_I, [_P, _P, _SZ]),
     "dg_set_state": (_I, [_P, _P, _SZ]),
@@ -181,6 +185,36 @@ class DGSolver:
         self._ck(self._L.dg_set_geometry_disks(self.ctx, _dp(cx), _dp(cy), _dp(r), int(r.size),
                                                L, n_cell, tiles), "dg_set_geometry_disks")
 
+    def set_geometry_batch(self, disks_list, L, n_cell, tiles):
+        """disks_list: G tuples (cx, cy, r); L, n_cell, tiles: G values each."""
+        G = len(disks_list)
+        nd = np.array([len(np.atleast_1d(d[2])) for d in disks_list], dtype=np.int32)
+        cat = [np.concatenate([_f64(np.atleast_1d(d[k])) for d in disks_list]) if nd.sum() else
+               np.zeros(1) for k in range(3)]
+        Lh = _f64(L)
+        nc = np.ascontiguousarray(n_cell, dtype=np.int32)
+        tl = np.ascontiguousarray(tiles, dtype=np.int32)
+        self._ck(self._L.dg_set_geometry_batch(self.ctx, G, nd.ctypes.data, _dp(cat[0]), _dp(cat[1]),
+                                               _dp(cat[2]), _dp(Lh), nc.ctypes.data, tl.ctypes.data),
+                 "dg_set_geometry_batch")
+
+    def covariance_batch(self):
+        inf = self.info()
+        G = inf.n_geometries
+        s3, mu, mass = np.zeros((G, 3)), np.zeros((G, 2)), np.zeros((G, inf.m))
+        self._ck(self._L.dg_covariance_batch(self.ctx, _dp(s3), _dp(mu), _dp(mass)),
+                 "dg_covariance_batch")
+        return s3, mu, mass
+
+    def get_elements_batch(self, idx) -> np.ndarray:
+        """Node values [k, n, n] of elements idx = [(geometry, source, ex, ey), ...]."""
+        idx = np.ascontiguousarray(idx, dtype=np.int32).reshape(-1, 4)
+        n = self.info().p + 1
+        out = np.zeros((idx.shape[0], n, n))
+        self._ck(self._L.dg_get_elements_batch(self.ctx, idx.ctypes.data, idx.shape[0], _dp(out)),
+                 "dg_get_elements_batch")
+        return out
+
     def info(self) -> dg_info:
         inf = dg_info()
         self._ck(self._L.dg_get_info(self.ctx, ctypes.byref(inf)), "dg_get_info")
@@ -194,8 +228,12 @@ class DGSolver:
 
     # sources and time stepping
     def set_sources(self, xy):
+        """Start points [m, 2], or [G, m, 2] for a batch of G geometries."""
+        G = self.info().n_geometries
         xy = _f64(xy).reshape(-1, 2)
-        self._ck(self._L.dg_set_sources(self.ctx, _dp(xy), xy.shape[0]), "dg_set_sources")
+        if xy.shape[0] % G:
+            raise ValueError(f"{xy.shape[0]} start points do not split over {G} geometries")
+        self._ck(self._L.dg_set_sources(self.ctx, _dp(xy), xy.shape[0] // G), "dg_set_sources")
 
     def query_dt(self):
         dt, rho = ctypes.c_double(), ctypes.c_double()
@@ -209,7 +247,8 @@ class DGSolver:
         self._ck(self._L.dg_propagate_to(self.ctx, float(delta)), "dg_propagate_to")
 
     def moments(self) -> np.ndarray:
-        out = np.zeros((self.info().m, 6))
+        inf = self.info()
+        out = np.zeros((inf.n_geometries * inf.m, 6))
         self._ck(self._L.dg_moments(self.ctx, _dp(out)), "dg_moments")
         return out
 

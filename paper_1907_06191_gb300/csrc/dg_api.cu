@@ -50,6 +50,8 @@ void free_state(Ctx &c) {
   if (c.state_owned && c.d_state) cudaFree(c.d_state);
   c.d_state = nullptr;
   cudaFree(c.d_src);
+  cudaFree(c.d_srel);
+  c.d_srel = nullptr;
   cudaFree(c.d_mom);
   cudaFree(c.d_mom0);
   cudaFree(c.d_part);
@@ -74,11 +76,10 @@ size_t state_bytes_for(const Ctx &c, int m) {
 // One SSP-RK3 step: U1 = U + dt L U; U2 = 3/4 U + 1/4 (U1 + dt L U1);
 // U <- 1/3 U + 2/3 (U2 + dt L U2).  L = (k/J^2) R.
 cudaError_t rk3_step(Ctx &c, double dt, cudaStream_t s) {
-  const double J = 0.5 * c.geo.h;
-  const double kc = c.cfg.D / (J * J);
+  const double kc = c.cfg.D;  // the kernel applies 1/J^2 of each element's geometry
   const double pen = c.cfg.eta * (c.cfg.p + 1.0) * (c.cfg.p + 1.0) * 0.5;
   const int wallA = c.cfg.wall_mode == DG_WALL_PAPER;
-  const long long nA = c.geo.n_active, st = c.geo.n_pad;
+  const long long st = c.geo.n_pad;
   const double co[3][3] = {{0.0, 1.0, dt * kc},
                            {0.75, 0.25, 0.25 * dt * kc},
                            {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * dt * kc}};
@@ -155,8 +156,7 @@ int ensure_rho(dg_ctx *ctx) {
     cleanup();
     return fail(ctx, DG_ENOMEM, std::string("power iteration buffers: ") + cudaGetErrorString(e));
   }
-  const double J = 0.5 * c.geo.h;
-  const double kc = c.cfg.D / (J * J);
+  const double kc = c.cfg.D;
   const double pen = c.cfg.eta * (c.cfg.p + 1.0) * (c.cfg.p + 1.0) * 0.5;
   StageCoef<double> sc{0.0, 0.0, kc, pen, c.cfg.wall_mode == DG_WALL_PAPER};
   const int iters = c.cfg.power_iters > 0 ? c.cfg.power_iters : 200;
@@ -193,44 +193,74 @@ int check_config(const dg_config *cfg, std::string &why) {
   return DG_OK;
 }
 
-int finish_geometry(dg_ctx *ctx) {
+int set_parts(dg_ctx *ctx, const std::vector<PartSpec> &parts) {
   Ctx &c = ctx->c;
+  free_state(c);
+  c.have_geo = false;
+  c.have_rho = false;
   std::string err;
-  const int code = build_connectivity(c.geo, c.cfg.boundary == DG_BC_PERIODIC, c.stream, err);
-  if (code != DG_OK) {
-    free_geometry(c.geo);
-    return fail(ctx, code, err);
-  }
-  c.geo.h_mask.resize((size_t)c.geo.nx * c.geo.ny);
-  cudaError_t e = cudaMemcpyAsync(c.geo.h_mask.data(), c.geo.d_mask, c.geo.h_mask.size(),
-                                  cudaMemcpyDeviceToHost, c.stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
-  if (e != cudaSuccess) {
-    free_geometry(c.geo);
-    return cuda_fail(ctx, e, "mask copy");
-  }
+  const int code = build_geometry(c.geo, parts, c.cfg.boundary == DG_BC_PERIODIC, c.stream, err);
+  if (code != DG_OK) return fail(ctx, code, err);
   c.have_geo = true;
   return DG_OK;
 }
 
+bool check_disk_args(const double *cx, const double *cy, const double *r, int nd, double L,
+                     int n_cell, int tiles, std::string &why) {
+  if (nd < 0 || (nd > 0 && (!cx || !cy || !r)) || !(L > 0.0) || n_cell < 1 || tiles < 1 ||
+      tiles % 2 == 0) {
+    why = "bad disk geometry arguments (tiles must be odd)";
+    return false;
+  }
+  const long long nwin = (long long)n_cell * tiles;
+  if (nwin * nwin > (1ll << 31) - 1) {
+    why = "domain too large";
+    return false;
+  }
+  for (int d = 0; d < nd; ++d)
+    if (!(r[d] >= 0.0) || !std::isfinite(cx[d]) || !std::isfinite(cy[d])) {
+      why = "bad disk " + std::to_string(d);
+      return false;
+    }
+  return true;
+}
+
+PartSpec disk_part(const double *cx, const double *cy, const double *r, int nd, double L,
+                   int n_cell, int tiles) {
+  PartSpec q;
+  q.nx = q.ny = n_cell * tiles;
+  q.h = L / n_cell;
+  q.x0 = q.y0 = -(double)(tiles / 2) * L;
+  q.cx = cx; q.cy = cy; q.r = r; q.nd = nd;
+  q.L = L; q.n_cell = n_cell; q.tiles = tiles;
+  return q;
+}
+
+// xy holds m start points for each geometry: [G][m][2].
 int set_sources_impl(dg_ctx *ctx, const double *xy, int m) {
   Ctx &c = ctx->c;
   if (!c.have_geo) return fail(ctx, DG_ESTATE, "dg_set_sources before a geometry");
   if (!xy || m < 1 || m > 65535) return fail(ctx, DG_EINVAL, "need 1 <= m <= 65535 start points");
-  // validate: inside the domain and in a mesh element
-  const std::vector<uint8_t> &mask = c.geo.h_mask;
-  for (int s = 0; s < m; ++s) {
-    const double x = xy[2 * s], y = xy[2 * s + 1];
-    const double fx = (x - c.geo.x0) / c.geo.h, fy = (y - c.geo.y0) / c.geo.h;
-    if (!(fx >= 0.0 && fy >= 0.0 && fx < c.geo.nx && fy < c.geo.ny))
-      return fail(ctx, DG_EINVAL, "start point " + std::to_string(s) + " outside the domain");
-    const int ex = (int)fx, ey = (int)fy;
-    if (!mask[(size_t)ey * c.geo.nx + ex])
-      return fail(ctx, DG_EINVAL, "start point " + std::to_string(s) + " lies in an axon element");
+  const int G = c.geo.G();
+  // validate: inside the domain and in a mesh element of its geometry
+  for (int g = 0; g < G; ++g) {
+    const GeoPart &p = c.geo.parts[g];
+    const uint8_t *mask = c.geo.h_mask.data() + p.dense_off;
+    for (int s = 0; s < m; ++s) {
+      const double x = xy[2 * ((size_t)g * m + s)], y = xy[2 * ((size_t)g * m + s) + 1];
+      const double fx = (x - p.x0) / p.h, fy = (y - p.y0) / p.h;
+      const std::string who = "start point " + std::to_string(s) +
+                              (G > 1 ? " of geometry " + std::to_string(g) : std::string());
+      if (!(fx >= 0.0 && fy >= 0.0 && fx < p.nx && fy < p.ny))
+        return fail(ctx, DG_EINVAL, who + " outside the domain");
+      const int ex = (int)fx, ey = (int)fy;
+      if (!mask[(size_t)ey * p.nx + ex]) return fail(ctx, DG_EINVAL, who + " lies in an axon element");
+    }
   }
   // Same number of start points on the same geometry: keep the buffers (and
   // any captured graph, whose pointers stay valid).
   const bool reuse = c.m == m && c.d_state != nullptr;
+  const size_t nd = (size_t)G * m;
   if (!reuse) {
     free_state(c);
     const size_t need = state_bytes_for(c, m);
@@ -244,18 +274,19 @@ int set_sources_impl(dg_ctx *ctx, const double *xy, int m) {
     }
     c.state_bytes = need;
     c.m = m;
-    CK(cudaMalloc(&c.d_src, sizeof(double) * 2 * m), "source allocation");
-    CK(cudaMalloc(&c.d_mom, sizeof(double) * kMomFields * m), "moment allocation");
-    CK(cudaMalloc(&c.d_mom0, sizeof(double) * kMomFields * m), "moment allocation");
-    CK(cudaMalloc(&c.d_part, sizeof(double) * kMomFields * kMomBlocks * (size_t)m), "partial allocation");
-    CK(cudaMalloc(&c.d_out, sizeof(double) * 8), "output allocation");
+    CK(cudaMalloc(&c.d_src, sizeof(double) * 2 * nd), "source allocation");
+    CK(cudaMalloc(&c.d_srel, sizeof(float4) * nd), "source allocation");
+    CK(cudaMalloc(&c.d_mom, sizeof(double) * kMomFields * nd), "moment allocation");
+    CK(cudaMalloc(&c.d_mom0, sizeof(double) * kMomFields * nd), "moment allocation");
+    CK(cudaMalloc(&c.d_part, sizeof(double) * kMomFields * moment_blocks(G) * nd), "partial allocation");
+    CK(cudaMalloc(&c.d_out, sizeof(double) * 5 * G), "output allocation");
   }
-  c.src.assign(xy, xy + 2 * (size_t)m);
-  CK(cudaMemcpyAsync(c.d_src, c.src.data(), sizeof(double) * 2 * m, cudaMemcpyHostToDevice, c.stream), "source copy");
+  c.src.assign(xy, xy + 2 * nd);
+  CK(cudaMemcpyAsync(c.d_src, c.src.data(), sizeof(double) * 2 * nd, cudaMemcpyHostToDevice, c.stream), "source copy");
   CK(launch_init_sources(c, state_array(c, 0), c.stream), "init sources");
   int r = compute_moments(ctx, c.d_mom0);
   if (r != DG_OK) return r;
-  CK(cudaMemcpyAsync(c.d_mom, c.d_mom0, sizeof(double) * kMomFields * m, cudaMemcpyDeviceToDevice, c.stream), "moment copy");
+  CK(cudaMemcpyAsync(c.d_mom, c.d_mom0, sizeof(double) * kMomFields * nd, cudaMemcpyDeviceToDevice, c.stream), "moment copy");
   c.t = 0.0;
   c.steps = 0;
   return DG_OK;
@@ -263,13 +294,14 @@ int set_sources_impl(dg_ctx *ctx, const double *xy, int m) {
 
 int check_growth(dg_ctx *ctx) {
   Ctx &c = ctx->c;
-  std::vector<double> mom((size_t)c.m * kMomFields), mom0((size_t)c.m * kMomFields);
+  const int nd = c.m * c.geo.G();
+  std::vector<double> mom((size_t)nd * kMomFields), mom0((size_t)nd * kMomFields);
   int r = compute_moments(ctx, c.d_mom);
   if (r != DG_OK) return r;
   CK(cudaMemcpyAsync(mom.data(), c.d_mom, mom.size() * 8, cudaMemcpyDeviceToHost, c.stream), "moment copy");
   CK(cudaMemcpyAsync(mom0.data(), c.d_mom0, mom0.size() * 8, cudaMemcpyDeviceToHost, c.stream), "moment copy");
   CK(cudaStreamSynchronize(c.stream), "moments");
-  for (int s = 0; s < c.m; ++s) {
+  for (int s = 0; s < nd; ++s) {
     const double *q = &mom[(size_t)s * kMomFields];
     for (int f = 0; f < kMomFields; ++f)
       if (!std::isfinite(q[f]))
@@ -373,62 +405,60 @@ int dg_set_geometry_mask(dg_ctx *ctx, const uint8_t *active, int nx, int ny, dou
     return fail(ctx, DG_EINVAL, "bad mask geometry arguments");
   if ((long long)nx * ny > (1ll << 31) - 1) return fail(ctx, DG_EINVAL, "domain too large");
   CK(cudaSetDevice(c.device), "set device");
-  free_state(c);
-  free_geometry(c.geo);
-  c.have_geo = false;
-  c.have_rho = false;
-  c.geo.nx = nx; c.geo.ny = ny; c.geo.h = h; c.geo.x0 = x0; c.geo.y0 = y0;
-  CK(cudaMalloc(&c.geo.d_mask, (size_t)nx * ny), "mask allocation");
-  std::vector<uint8_t> m01((size_t)nx * ny);
-  for (size_t k = 0; k < m01.size(); ++k) m01[k] = active[k] ? 1 : 0;
-  CK(cudaMemcpyAsync(c.geo.d_mask, m01.data(), m01.size(), cudaMemcpyHostToDevice, c.stream), "mask copy");
-  CK(cudaStreamSynchronize(c.stream), "mask copy");
-  return finish_geometry(ctx);
+  PartSpec q;
+  q.nx = nx; q.ny = ny; q.h = h; q.x0 = x0; q.y0 = y0; q.host_mask = active;
+  try {
+    return set_parts(ctx, {q});
+  } catch (const std::bad_alloc &) {
+    return fail(ctx, DG_ENOMEM, "host allocation");
+  }
 }
 
 int dg_set_geometry_disks(dg_ctx *ctx, const double *cx, const double *cy, const double *r,
                           int ndisks, double L, int n_cell, int tiles) {
   if (!ctx) return DG_EINVAL;
   Ctx &c = ctx->c;
-  if (ndisks < 0 || (ndisks > 0 && (!cx || !cy || !r)) || !(L > 0.0) || n_cell < 1 ||
-      tiles < 1 || tiles % 2 == 0)
-    return fail(ctx, DG_EINVAL, "bad disk geometry arguments (tiles must be odd)");
-  const long long nwin = (long long)n_cell * tiles;
-  if (nwin * nwin > (1ll << 31) - 1) return fail(ctx, DG_EINVAL, "domain too large");
-  for (int d = 0; d < ndisks; ++d)
-    if (!(r[d] >= 0.0) || !std::isfinite(cx[d]) || !std::isfinite(cy[d]))
-      return fail(ctx, DG_EINVAL, "bad disk " + std::to_string(d));
+  std::string why;
+  if (!check_disk_args(cx, cy, r, ndisks, L, n_cell, tiles, why)) return fail(ctx, DG_EINVAL, why);
   CK(cudaSetDevice(c.device), "set device");
-  free_state(c);
-  free_geometry(c.geo);
-  c.have_geo = false;
-  c.have_rho = false;
-  c.geo.nx = c.geo.ny = (int)nwin;
-  c.geo.h = L / n_cell;
-  c.geo.x0 = c.geo.y0 = -(double)(tiles / 2) * L;
-  CK(cudaMalloc(&c.geo.d_mask, (size_t)nwin * nwin), "mask allocation");
-  double *d = nullptr;
-  const int nd = ndisks > 0 ? ndisks : 1;
-  CK(cudaMalloc(&d, sizeof(double) * 3 * nd), "disk allocation");
-  cudaError_t e = cudaSuccess;
-  if (ndisks > 0) {
-    e = cudaMemcpyAsync(d, cx, 8 * ndisks, cudaMemcpyHostToDevice, c.stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d + nd, cy, 8 * ndisks, cudaMemcpyHostToDevice, c.stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d + 2 * nd, r, 8 * ndisks, cudaMemcpyHostToDevice, c.stream);
+  try {
+    return set_parts(ctx, {disk_part(cx, cy, r, ndisks, L, n_cell, tiles)});
+  } catch (const std::bad_alloc &) {
+    return fail(ctx, DG_ENOMEM, "host allocation");
   }
-  if (e == cudaSuccess) e = build_mask_disks(d, d + nd, d + 2 * nd, ndisks, L, n_cell, tiles, c.geo.d_mask, c.stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
-  cudaFree(d);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "disk mask");
-  return finish_geometry(ctx);
+}
+
+int dg_set_geometry_batch(dg_ctx *ctx, int G, const int *ndisks, const double *cx,
+                          const double *cy, const double *r, const double *L,
+                          const int *n_cell, const int *tiles) {
+  if (!ctx) return DG_EINVAL;
+  Ctx &c = ctx->c;
+  if (G < 1 || !ndisks || !L || !n_cell || !tiles) return fail(ctx, DG_EINVAL, "bad batch arguments");
+  CK(cudaSetDevice(c.device), "set device");
+  try {
+    std::vector<PartSpec> parts;
+    long long off = 0;
+    for (int g = 0; g < G; ++g) {
+      std::string why;
+      const int nd = ndisks[g];
+      if (nd < 0) return fail(ctx, DG_EINVAL, "bad disk count of geometry " + std::to_string(g));
+      const double *gx = cx ? cx + off : nullptr, *gy = cy ? cy + off : nullptr, *gr = r ? r + off : nullptr;
+      if (!check_disk_args(gx, gy, gr, nd, L[g], n_cell[g], tiles[g], why))
+        return fail(ctx, DG_EINVAL, "geometry " + std::to_string(g) + ": " + why);
+      parts.push_back(disk_part(gx, gy, gr, nd, L[g], n_cell[g], tiles[g]));
+      off += nd;
+    }
+    return set_parts(ctx, parts);
+  } catch (const std::bad_alloc &) {
+    return fail(ctx, DG_ENOMEM, "host allocation");
+  }
 }
 
 int dg_get_mask(dg_ctx *ctx, uint8_t *active) {
   if (!ctx || !active) return DG_EINVAL;
   Ctx &c = ctx->c;
   if (!c.have_geo) return fail(ctx, DG_ESTATE, "no geometry");
-  CK(cudaMemcpyAsync(active, c.geo.d_mask, (size_t)c.geo.nx * c.geo.ny, cudaMemcpyDeviceToHost, c.stream), "mask copy");
-  CK(cudaStreamSynchronize(c.stream), "mask copy");
+  std::memcpy(active, c.geo.h_mask.data(), (size_t)c.geo.nx * c.geo.ny);
   return DG_OK;
 }
 
@@ -451,6 +481,8 @@ int dg_get_info(dg_ctx *ctx, dg_info *info) {
   info->steps = c.steps;
   info->state_bytes = c.state_bytes;
   info->halo_max = c.geo.halo_max;
+  info->n_geometries = c.geo.G();
+  info->n_elements_padded = c.geo.n_pad;
   return DG_OK;
 }
 
@@ -520,31 +552,42 @@ int dg_moments(dg_ctx *ctx, double *out) {
   CK(cudaSetDevice(c.device), "set device");
   int r = compute_moments(ctx, c.d_mom);
   if (r != DG_OK) return r;
-  std::vector<double> tmp((size_t)c.m * kMomFields);
+  const int nd = c.m * c.geo.G();
+  std::vector<double> tmp((size_t)nd * kMomFields);
   CK(cudaMemcpyAsync(tmp.data(), c.d_mom, tmp.size() * 8, cudaMemcpyDeviceToHost, c.stream), "moment copy");
   CK(cudaStreamSynchronize(c.stream), "moments");
-  for (int s = 0; s < c.m; ++s)
-    for (int f = 0; f < 6; ++f) out[s * 6 + f] = tmp[(size_t)s * kMomFields + f];
+  for (int s = 0; s < nd; ++s)
+    for (int f = 0; f < 6; ++f) out[(size_t)s * 6 + f] = tmp[(size_t)s * kMomFields + f];
   return DG_OK;
 }
 
-int dg_covariance(dg_ctx *ctx, double *sigma3, double *mu2, double *mass) {
+int dg_covariance_batch(dg_ctx *ctx, double *sigma3, double *mu2, double *mass) {
   if (!ctx || !sigma3 || !mu2) return DG_EINVAL;
   Ctx &c = ctx->c;
   if (c.m < 1) return fail(ctx, DG_ESTATE, "no sources");
   CK(cudaSetDevice(c.device), "set device");
   int r = compute_moments(ctx, c.d_mom);
   if (r != DG_OK) return r;
-  CK(launch_covariance(c.d_mom, c.d_mom0, c.m, c.d_out, c.stream), "covariance");
-  double out[5];
-  CK(cudaMemcpyAsync(out, c.d_out, sizeof(out), cudaMemcpyDeviceToHost, c.stream), "covariance copy");
+  const int G = c.geo.G();
+  CK(launch_covariance(c.d_mom, c.d_mom0, c.m, G, c.d_out, c.stream), "covariance");
+  std::vector<double> out((size_t)5 * G);
+  CK(cudaMemcpyAsync(out.data(), c.d_out, sizeof(double) * out.size(), cudaMemcpyDeviceToHost, c.stream),
+     "covariance copy");
   if (mass)
-    CK(cudaMemcpy2DAsync(mass, sizeof(double), c.d_mom, sizeof(double) * kMomFields, sizeof(double), c.m,
-                         cudaMemcpyDeviceToHost, c.stream), "mass copy");
+    CK(cudaMemcpy2DAsync(mass, sizeof(double), c.d_mom, sizeof(double) * kMomFields, sizeof(double),
+                         (size_t)c.m * G, cudaMemcpyDeviceToHost, c.stream), "mass copy");
   CK(cudaStreamSynchronize(c.stream), "covariance");
-  sigma3[0] = out[0]; sigma3[1] = out[1]; sigma3[2] = out[2];
-  mu2[0] = out[3]; mu2[1] = out[4];
+  for (int g = 0; g < G; ++g) {
+    sigma3[3 * g] = out[5 * g]; sigma3[3 * g + 1] = out[5 * g + 1]; sigma3[3 * g + 2] = out[5 * g + 2];
+    mu2[2 * g] = out[5 * g + 3]; mu2[2 * g + 1] = out[5 * g + 4];
+  }
   return DG_OK;
+}
+
+int dg_covariance(dg_ctx *ctx, double *sigma3, double *mu2, double *mass) {
+  if (!ctx || !sigma3 || !mu2) return DG_EINVAL;
+  if (ctx->c.geo.G() > 1) return fail(ctx, DG_EINVAL, "several geometries: use dg_covariance_batch");
+  return dg_covariance_batch(ctx, sigma3, mu2, mass);
 }
 
 int dg_mixture_covariance(dg_ctx *ctx, const double *mom, const double *mom0, int m,
@@ -563,7 +606,7 @@ int dg_mixture_covariance(dg_ctx *ctx, const double *mom, const double *mom0, in
   double out[5];
   cudaError_t e = cudaMemcpyAsync(d, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, c.stream);
   double *dout = d + h.size();
-  if (e == cudaSuccess) e = launch_covariance(d, d + (size_t)m * kMomFields, m, dout, c.stream);
+  if (e == cudaSuccess) e = launch_covariance(d, d + (size_t)m * kMomFields, m, 1, dout, c.stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, sizeof(out), cudaMemcpyDeviceToHost, c.stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
   cudaFree(d);
@@ -578,8 +621,7 @@ int dg_apply_operator(dg_ctx *ctx) {
   Ctx &c = ctx->c;
   if (c.m < 1) return fail(ctx, DG_ESTATE, "no sources");
   CK(cudaSetDevice(c.device), "set device");
-  const double J = 0.5 * c.geo.h;
-  const double kc = c.cfg.D / (J * J);
+  const double kc = c.cfg.D;
   const double pen = c.cfg.eta * (c.cfg.p + 1.0) * (c.cfg.p + 1.0) * 0.5;
   const int wallA = c.cfg.wall_mode == DG_WALL_PAPER;
   void *U0 = state_array(c, 0), *U1 = state_array(c, 1);
@@ -603,6 +645,7 @@ int dg_get_nodes(dg_ctx *ctx, double *host) {
   if (!ctx || !host) return DG_EINVAL;
   Ctx &c = ctx->c;
   if (c.m < 1) return fail(ctx, DG_ESTATE, "no sources");
+  if (c.geo.G() > 1) return fail(ctx, DG_EINVAL, "several geometries: use dg_get_elements_batch");
   CK(cudaSetDevice(c.device), "set device");
   const size_t nd = (size_t)c.m * c.geo.nx * c.geo.ny * c.np();
   double *d = nullptr;
@@ -620,6 +663,7 @@ int dg_set_nodes(dg_ctx *ctx, const double *host) {
   if (!ctx || !host) return DG_EINVAL;
   Ctx &c = ctx->c;
   if (c.m < 1) return fail(ctx, DG_ESTATE, "no sources");
+  if (c.geo.G() > 1) return fail(ctx, DG_EINVAL, "several geometries: not supported");
   CK(cudaSetDevice(c.device), "set device");
   const size_t nd = (size_t)c.m * c.geo.nx * c.geo.ny * c.np();
   double *d = nullptr;
@@ -632,22 +676,23 @@ int dg_set_nodes(dg_ctx *ctx, const double *host) {
   return DG_OK;
 }
 
-int dg_get_elements(dg_ctx *ctx, const int *idx, int k, double *out) {
+int dg_get_elements_batch(dg_ctx *ctx, const int *idx, int k, double *out) {
   if (!ctx || k < 0 || (k > 0 && (!idx || !out))) return DG_EINVAL;
   Ctx &c = ctx->c;
   if (c.m < 1) return fail(ctx, DG_ESTATE, "no sources");
   CK(cudaSetDevice(c.device), "set device");
   const int np = c.np();
-  std::vector<int> cidx((size_t)c.geo.nx * c.geo.ny);
-  CK(cudaMemcpyAsync(cidx.data(), c.geo.d_cidx, cidx.size() * sizeof(int), cudaMemcpyDeviceToHost, c.stream),
-     "index copy");
-  CK(cudaStreamSynchronize(c.stream), "index copy");
   std::vector<char> tmp((size_t)np * c.esize());
   for (int q = 0; q < k; ++q) {
-    const int s = idx[3 * q], ex = idx[3 * q + 1], ey = idx[3 * q + 2];
-    if (s < 0 || s >= c.m || ex < 0 || ex >= c.geo.nx || ey < 0 || ey >= c.geo.ny)
+    const int g = idx[4 * q], s = idx[4 * q + 1], ex = idx[4 * q + 2], ey = idx[4 * q + 3];
+    if (g < 0 || g >= c.geo.G()) return fail(ctx, DG_EINVAL, "geometry index out of range");
+    const GeoPart &p = c.geo.parts[g];
+    if (s < 0 || s >= c.m || ex < 0 || ex >= p.nx || ey < 0 || ey >= p.ny)
       return fail(ctx, DG_EINVAL, "element index out of range");
-    const int a = cidx[(size_t)ey * c.geo.nx + ex];
+    int a = -1;
+    CK(cudaMemcpyAsync(&a, c.geo.d_cidx + p.dense_off + (size_t)ey * p.nx + ex, sizeof(int),
+                       cudaMemcpyDeviceToHost, c.stream), "index copy");
+    CK(cudaStreamSynchronize(c.stream), "index copy");
     double *o = out + (size_t)q * np;
     if (a < 0) {
       for (int t = 0; t < np; ++t) o[t] = 0.0;
@@ -662,15 +707,28 @@ int dg_get_elements(dg_ctx *ctx, const int *idx, int k, double *out) {
   return DG_OK;
 }
 
-// Snapshot layout: 8 x uint64 header {magic, precision, p, m, n_active,
-// steps, bits of t, payload bytes}, m x 2 start points, m x 7 start moments,
-// then m x n_active x Np values of U (state precision, compact order).
+int dg_get_elements(dg_ctx *ctx, const int *idx, int k, double *out) {
+  if (!ctx || k < 0 || (k > 0 && (!idx || !out))) return DG_EINVAL;
+  std::vector<int> q4((size_t)4 * k);
+  for (int q = 0; q < k; ++q) {
+    q4[4 * q] = 0;
+    q4[4 * q + 1] = idx[3 * q];
+    q4[4 * q + 2] = idx[3 * q + 1];
+    q4[4 * q + 3] = idx[3 * q + 2];
+  }
+  return dg_get_elements_batch(ctx, q4.data(), k, out);
+}
+
+// Snapshot layout: 8 x uint64 header {magic, precision, p, m, padded element
+// count, steps, bits of t, payload bytes}, G x m x 2 start points, G x m x 7
+// start moments, then m x n_pad x Np values of U (state precision,
+// concatenated element order).
 int dg_state_size(dg_ctx *ctx, size_t *bytes) {
   if (!ctx || !bytes) return DG_EINVAL;
   const Ctx &c = ctx->c;
   if (c.m < 1) return fail(ctx, DG_ESTATE, "no sources");
-  *bytes = 64 + (size_t)c.m * 16 + (size_t)c.m * kMomFields * 8 +
-           (size_t)c.m * c.geo.n_active * c.np() * c.esize();
+  const size_t nd = (size_t)c.m * c.geo.G();
+  *bytes = 64 + nd * 16 + nd * kMomFields * 8 + (size_t)c.m * c.field_elems() * c.esize();
   return DG_OK;
 }
 
@@ -681,22 +739,21 @@ int dg_get_state(dg_ctx *ctx, void *host, size_t bytes) {
   if (!host || bytes < need) return fail(ctx, DG_EINVAL, "snapshot buffer too small");
   Ctx &c = ctx->c;
   CK(cudaSetDevice(c.device), "set device");
+  const size_t nd = (size_t)c.m * c.geo.G();
   uint64_t hdr[8];
   double tt = c.t;
   std::memcpy(&hdr[6], &tt, 8);
   hdr[0] = kStateMagic; hdr[1] = (uint64_t)c.cfg.precision; hdr[2] = (uint64_t)c.cfg.p;
-  hdr[3] = (uint64_t)c.m; hdr[4] = (uint64_t)c.geo.n_active; hdr[5] = (uint64_t)c.steps;
+  hdr[3] = (uint64_t)c.m; hdr[4] = (uint64_t)c.geo.n_pad; hdr[5] = (uint64_t)c.steps;
   hdr[7] = need;
   char *p = (char *)host;
   std::memcpy(p, hdr, 64);
-  std::memcpy(p + 64, c.src.data(), (size_t)c.m * 16);
-  char *pm = p + 64 + (size_t)c.m * 16;
-  CK(cudaMemcpyAsync(pm, c.d_mom0, (size_t)c.m * kMomFields * 8, cudaMemcpyDeviceToHost, c.stream), "snapshot");
-  char *pu = pm + (size_t)c.m * kMomFields * 8;
-  const size_t row = (size_t)c.geo.n_active * c.np() * c.esize();
-  for (int s = 0; s < c.m; ++s)
-    CK(cudaMemcpyAsync(pu + s * row, (char *)state_array(c, 0) + (size_t)s * c.field_elems() * c.esize(), row,
-                       cudaMemcpyDeviceToHost, c.stream), "snapshot");
+  std::memcpy(p + 64, c.src.data(), nd * 16);
+  char *pm = p + 64 + nd * 16;
+  CK(cudaMemcpyAsync(pm, c.d_mom0, nd * kMomFields * 8, cudaMemcpyDeviceToHost, c.stream), "snapshot");
+  char *pu = pm + nd * kMomFields * 8;
+  CK(cudaMemcpyAsync(pu, state_array(c, 0), (size_t)c.m * c.field_elems() * c.esize(), cudaMemcpyDeviceToHost,
+                     c.stream), "snapshot");
   CK(cudaStreamSynchronize(c.stream), "snapshot");
   return DG_OK;
 }
@@ -708,22 +765,21 @@ int dg_set_state(dg_ctx *ctx, const void *host, size_t bytes) {
   uint64_t hdr[8];
   std::memcpy(hdr, host, 64);
   if (hdr[0] != kStateMagic) return fail(ctx, DG_EINVAL, "not a snapshot");
-  if (hdr[1] != (uint64_t)c.cfg.precision || hdr[2] != (uint64_t)c.cfg.p || hdr[4] != (uint64_t)c.geo.n_active)
+  if (hdr[1] != (uint64_t)c.cfg.precision || hdr[2] != (uint64_t)c.cfg.p || hdr[4] != (uint64_t)c.geo.n_pad)
     return fail(ctx, DG_EINVAL, "snapshot does not match the context (precision, order or mesh)");
   if (hdr[7] > bytes || hdr[3] < 1 || hdr[3] > 65535) return fail(ctx, DG_EINVAL, "truncated snapshot");
   const int m = (int)hdr[3];
+  const size_t nd = (size_t)m * c.geo.G();
   const char *p = (const char *)host;
-  std::vector<double> xy(2 * (size_t)m);
-  std::memcpy(xy.data(), p + 64, (size_t)m * 16);
+  std::vector<double> xy(2 * nd);
+  std::memcpy(xy.data(), p + 64, nd * 16);
   int r = dg_set_sources(ctx, xy.data(), m);
   if (r != DG_OK) return r;
-  const char *pm = p + 64 + (size_t)m * 16;
-  CK(cudaMemcpyAsync(c.d_mom0, pm, (size_t)m * kMomFields * 8, cudaMemcpyHostToDevice, c.stream), "restore");
-  const char *pu = pm + (size_t)m * kMomFields * 8;
-  const size_t row = (size_t)c.geo.n_active * c.np() * c.esize();
-  for (int s = 0; s < m; ++s)
-    CK(cudaMemcpyAsync((char *)state_array(c, 0) + (size_t)s * c.field_elems() * c.esize(), pu + s * row, row,
-                       cudaMemcpyHostToDevice, c.stream), "restore");
+  const char *pm = p + 64 + nd * 16;
+  CK(cudaMemcpyAsync(c.d_mom0, pm, nd * kMomFields * 8, cudaMemcpyHostToDevice, c.stream), "restore");
+  const char *pu = pm + nd * kMomFields * 8;
+  CK(cudaMemcpyAsync(state_array(c, 0), pu, (size_t)m * c.field_elems() * c.esize(), cudaMemcpyHostToDevice,
+                     c.stream), "restore");
   CK(cudaStreamSynchronize(c.stream), "restore");
   std::memcpy(&c.t, &hdr[6], 8);
   c.steps = (long long)hdr[5];

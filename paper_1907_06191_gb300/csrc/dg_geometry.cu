@@ -3,6 +3,7 @@
 //
 // Substrate (Sec. 2.2): disks in a periodic square cell; the pixel mesh of
 // Sec. 3.3 keeps an element when its centre lies outside every disk.
+#include <algorithm>
 #include <cstdio>
 #include <vector>
 
@@ -125,9 +126,10 @@ __global__ void k_scan_counts(const int *__restrict__ count, int n, int *__restr
   if (threadIdx.x == 0) off[n] = carry_s;
 }
 
-// block = kTile*kTile threads, one block per tile
+// block = kTile*kTile threads, one block per tile; element numbers start at
+// elem0 (the geometry's place in the concatenated numbering)
 __global__ void k_assign(const uint8_t *__restrict__ mask, int nx, int ny,
-                         const int *__restrict__ off, int *__restrict__ cidx,
+                         const int *__restrict__ off, int elem0, int *__restrict__ cidx,
                          int2 *__restrict__ exy) {
   __shared__ int wsum[kTile * kTile / 32];
   int ex, ey;
@@ -141,18 +143,19 @@ __global__ void k_assign(const uint8_t *__restrict__ mask, int nx, int ny,
   for (int w = 0; w < wid; ++w) pre += wsum[w];
   pre += __popc(bal & ((1u << lane) - 1u));
   if (in) {
-    const int idx = f ? off[blockIdx.x] + pre : -1;
+    const int idx = f ? elem0 + off[blockIdx.x] + pre : -1;
     cidx[(size_t)ey * nx + ex] = idx;
     if (f) exy[idx] = make_int2(ex, ey);
   }
 }
 
-// one thread per mesh element: E, W, N, S neighbours
+// one thread per mesh element of one geometry (elements elem0 .. elem0+nA-1):
+// E, W, N, S neighbours as concatenated indices, kWall or kEdge
 __global__ void k_neighbours(const int2 *__restrict__ exy, const int *__restrict__ cidx,
-                             int nA, int nx, int ny, int periodic, int4 *__restrict__ nb,
-                             int *__restrict__ bad) {
-  const int a = blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= nA) return;
+                             int elem0, int nA, int nx, int ny, int periodic, int lo, int hi,
+                             int4 *__restrict__ nb, int *__restrict__ bad) {
+  const int a = elem0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= elem0 + nA) return;
   const int2 e = exy[a];
   int res[4];
   const int dx[4] = {1, -1, 0, 0}, dy[4] = {0, 0, 1, -1};
@@ -166,7 +169,7 @@ __global__ void k_neighbours(const int2 *__restrict__ exy, const int *__restrict
     }
     const int c = cidx[(size_t)qy * nx + qx];
     res[d] = c >= 0 ? c : kWall;
-    if (c >= nA) atomicExch(bad, 1);
+    if (c >= 0 && (c < lo || c >= hi)) atomicExch(bad, 1);
   }
   nb[a] = make_int4(res[0], res[1], res[2], res[3]);
 }
@@ -177,15 +180,17 @@ __global__ void k_neighbours(const int2 *__restrict__ exy, const int *__restrict
 // consecutive halo slots (block-wide prefix of a ballot), so the table does
 // not depend on scheduling.  A halo entry is {neighbour, neighbour's face
 // toward the chunk element} = {k, f ^ 1}.
-__global__ void k_halo(const int4 *__restrict__ nb, int nA, int4 *__restrict__ loc,
-                       int2 *__restrict__ halo, int *__restrict__ halo_cnt) {
+__global__ void k_halo(const int4 *__restrict__ nb, const int2 *__restrict__ chunk_tab,
+                       int4 *__restrict__ loc, int2 *__restrict__ halo,
+                       int *__restrict__ halo_cnt) {
   __shared__ int wsum[kBlock / 32];
   __shared__ int base_s;
   const int c = blockIdx.x;
   const int a0 = c * kBlock;
   const int el = threadIdx.x;
   const int a = a0 + el;
-  const bool live = a < nA;
+  const int cnt = chunk_tab[c].x;
+  const bool live = el < cnt;
   const int4 q = live ? nb[a] : make_int4(kEdge, kEdge, kEdge, kEdge);
   int qn[4] = {q.x, q.y, q.z, q.w};
   int out[4];
@@ -194,7 +199,7 @@ __global__ void k_halo(const int4 *__restrict__ nb, int nA, int4 *__restrict__ l
   __syncthreads();
   for (int f = 0; f < 4; ++f) {
     const int k = qn[f];
-    const bool inside = k >= a0 && k < a0 + kBlock && k < nA;
+    const bool inside = k >= a0 && k < a0 + cnt;
     const bool need = live && k >= 0 && !inside;
     const unsigned bal = __ballot_sync(0xffffffffu, need);
     if (lane == 0) wsum[wid] = __popc(bal);
@@ -217,7 +222,7 @@ __global__ void k_halo(const int4 *__restrict__ nb, int nA, int4 *__restrict__ l
     if (el == 0) base_s = base + tot;
     __syncthreads();
   }
-  if (live) loc[a] = make_int4(out[0], out[1], out[2], out[3]);
+  loc[a] = live ? make_int4(out[0], out[1], out[2], out[3]) : make_int4(kEdge, kEdge, kEdge, kEdge);
   if (el == 0) halo_cnt[c] = base_s;
 }
 
@@ -235,110 +240,203 @@ __global__ void k_max_int(const int *__restrict__ v, int n, int *__restrict__ ou
 }
 
 void free_geometry(Geometry &geo) {
-  cudaFree(geo.d_mask);
-  cudaFree(geo.d_cidx);
-  cudaFree(geo.d_nb);
-  cudaFree(geo.d_exy);
-  cudaFree(geo.d_loc);
-  cudaFree(geo.d_halo);
-  cudaFree(geo.d_halo_cnt);
-  geo.d_mask = nullptr;
-  geo.d_cidx = nullptr;
-  geo.d_nb = nullptr;
-  geo.d_exy = nullptr;
-  geo.d_loc = nullptr;
-  geo.d_halo = nullptr;
-  geo.d_halo_cnt = nullptr;
-  geo.n_active = 0;
-  geo.halo_max = 0;
+  void *ptrs[] = {geo.d_mask, geo.d_cidx, geo.d_nb, geo.d_exy, geo.d_chunk, geo.d_gpar,
+                  geo.d_gscale_f, geo.d_gscale_d, geo.d_grange, geo.d_loc, geo.d_halo,
+                  geo.d_halo_cnt};
+  for (void *p : ptrs) cudaFree(p);
+  geo = Geometry();
 }
 
-// geo.d_mask, nx, ny must be set.  Returns a DG_* code.
-int build_connectivity(Geometry &geo, int periodic, cudaStream_t s, std::string &err) {
-  const int nx = geo.nx, ny = geo.ny;
-  const int tx = (nx + kTile - 1) / kTile, ty = (ny + kTile - 1) / kTile;
-  const int nt = tx * ty;
-  int *d_count = nullptr, *d_off = nullptr, *d_bad = nullptr;
-  cudaError_t e;
-  int code = DG_OK;
-  int total = 0, bad = 0;
-  if ((e = cudaMalloc(&d_count, sizeof(int) * (size_t)nt)) != cudaSuccess ||
-      (e = cudaMalloc(&d_off, sizeof(int) * ((size_t)nt + 1))) != cudaSuccess ||
-      (e = cudaMalloc(&d_bad, sizeof(int))) != cudaSuccess ||
-      (e = cudaMalloc(&geo.d_cidx, sizeof(int) * (size_t)nx * ny)) != cudaSuccess) {
-    err = std::string("connectivity allocation: ") + cudaGetErrorString(e);
-    code = DG_ENOMEM;
-    goto done;
+__global__ void k_fill_int4(int4 *__restrict__ p, long long n, int4 v) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+namespace {
+struct Tmp {
+  std::vector<void *> ptrs;
+  ~Tmp() {
+    for (void *p : ptrs) cudaFree(p);
   }
-  k_tile_count<<<nt, kTile * kTile, 0, s>>>(geo.d_mask, nx, ny, d_count);
-  k_scan_counts<<<1, 1024, 0, s>>>(d_count, nt, d_off);
-  if ((e = cudaMemcpyAsync(&total, d_off + nt, sizeof(int), cudaMemcpyDeviceToHost, s)) !=
-          cudaSuccess ||
-      (e = cudaStreamSynchronize(s)) != cudaSuccess) {
-    err = std::string("connectivity scan: ") + cudaGetErrorString(e);
-    code = DG_ECUDA;
-    goto done;
+  template <typename X>
+  cudaError_t alloc(X **p, size_t n) {
+    cudaError_t e = cudaMalloc(p, sizeof(X) * (n ? n : 1));
+    if (e == cudaSuccess) ptrs.push_back(*p);
+    return e;
   }
-  if (total <= 0) {
-    err = "the mask has no element in the mesh";
-    code = DG_EINVAL;
-    goto done;
+};
+}  // namespace
+
+int build_geometry(Geometry &geo, const std::vector<PartSpec> &specs, int periodic,
+                   cudaStream_t s, std::string &err) {
+  free_geometry(geo);
+  const int G = (int)specs.size();
+  if (G < 1) {
+    err = "no geometry";
+    return DG_EINVAL;
   }
-  geo.n_active = total;
-  geo.n_pad = ((long long)total + 31) / 32 * 32;
-  if ((e = cudaMalloc(&geo.d_nb, sizeof(int4) * (size_t)total)) != cudaSuccess ||
-      (e = cudaMalloc(&geo.d_exy, sizeof(int2) * (size_t)total)) != cudaSuccess) {
-    err = std::string("neighbour table allocation: ") + cudaGetErrorString(e);
-    code = DG_ENOMEM;
-    goto done;
+  cudaError_t e = cudaSuccess;
+  Tmp tmp;
+#define GK(expr, what, code)                                            \
+  do {                                                                  \
+    if ((e = (expr)) != cudaSuccess) {                                  \
+      err = std::string(what) + ": " + cudaGetErrorString(e);           \
+      free_geometry(geo);                                               \
+      return code;                                                      \
+    }                                                                   \
+  } while (0)
+  // dense masks, geometry after geometry
+  geo.parts.resize(G);
+  long long dense = 0;
+  for (int g = 0; g < G; ++g) {
+    GeoPart &p = geo.parts[g];
+    const PartSpec &q = specs[g];
+    p.nx = q.nx; p.ny = q.ny; p.h = q.h; p.x0 = q.x0; p.y0 = q.y0;
+    p.periodic = periodic;
+    p.dense_off = dense;
+    dense += (long long)q.nx * q.ny;
   }
-  k_assign<<<nt, kTile * kTile, 0, s>>>(geo.d_mask, nx, ny, d_off, geo.d_cidx, geo.d_exy);
+  if (dense > (1ll << 31) - 1) {
+    err = "domains too large";
+    free_geometry(geo);
+    return DG_EINVAL;
+  }
+  GK(cudaMalloc(&geo.d_mask, (size_t)dense), "mask allocation", DG_ENOMEM);
+  GK(cudaMalloc(&geo.d_cidx, sizeof(int) * (size_t)dense), "index map allocation", DG_ENOMEM);
+  int max_nd = 1;
+  for (const PartSpec &q : specs) max_nd = std::max(max_nd, q.nd);
+  double *d_disk = nullptr;
+  GK(tmp.alloc(&d_disk, 3 * (size_t)max_nd), "disk allocation", DG_ENOMEM);
+  for (int g = 0; g < G; ++g) {
+    const PartSpec &q = specs[g];
+    uint8_t *m = geo.d_mask + geo.parts[g].dense_off;
+    const size_t cells = (size_t)q.nx * q.ny;
+    if (q.host_mask) {
+      std::vector<uint8_t> m01(cells);
+      for (size_t k = 0; k < cells; ++k) m01[k] = q.host_mask[k] ? 1 : 0;
+      GK(cudaMemcpyAsync(m, m01.data(), cells, cudaMemcpyHostToDevice, s), "mask copy", DG_ECUDA);
+      GK(cudaStreamSynchronize(s), "mask copy", DG_ECUDA);
+    } else {
+      if (q.nd > 0) {
+        GK(cudaMemcpyAsync(d_disk, q.cx, 8 * (size_t)q.nd, cudaMemcpyHostToDevice, s), "disk copy", DG_ECUDA);
+        GK(cudaMemcpyAsync(d_disk + max_nd, q.cy, 8 * (size_t)q.nd, cudaMemcpyHostToDevice, s), "disk copy", DG_ECUDA);
+        GK(cudaMemcpyAsync(d_disk + 2 * max_nd, q.r, 8 * (size_t)q.nd, cudaMemcpyHostToDevice, s), "disk copy", DG_ECUDA);
+      }
+      GK(build_mask_disks(d_disk, d_disk + max_nd, d_disk + 2 * max_nd, q.nd, q.L, q.n_cell, q.tiles, m, s),
+         "disk mask", DG_ECUDA);
+      GK(cudaStreamSynchronize(s), "disk mask", DG_ECUDA);
+    }
+  }
+  // per geometry: tile counts and their scan -> elements in the mesh
+  std::vector<int *> offs(G, nullptr);
+  long long elems = 0;
+  for (int g = 0; g < G; ++g) {
+    GeoPart &p = geo.parts[g];
+    const int tx = (p.nx + kTile - 1) / kTile, ty = (p.ny + kTile - 1) / kTile;
+    const int nt = tx * ty;
+    int *d_count = nullptr;
+    GK(tmp.alloc(&d_count, (size_t)nt), "tile count allocation", DG_ENOMEM);
+    GK(tmp.alloc(&offs[g], (size_t)nt + 1), "tile offset allocation", DG_ENOMEM);
+    const uint8_t *m = geo.d_mask + p.dense_off;
+    k_tile_count<<<nt, kTile * kTile, 0, s>>>(m, p.nx, p.ny, d_count);
+    k_scan_counts<<<1, 1024, 0, s>>>(d_count, nt, offs[g]);
+    int total = 0;
+    GK(cudaMemcpyAsync(&total, offs[g] + nt, sizeof(int), cudaMemcpyDeviceToHost, s), "tile scan", DG_ECUDA);
+    GK(cudaStreamSynchronize(s), "tile scan", DG_ECUDA);
+    if (total <= 0) {
+      err = "geometry " + std::to_string(g) + " has no element in the mesh";
+      free_geometry(geo);
+      return DG_EINVAL;
+    }
+    p.n_active = total;
+    p.off = elems;
+    elems += ((long long)total + kBlock - 1) / kBlock * kBlock;
+  }
+  if (elems > (1ll << 31) - 1) {
+    err = "too many elements";
+    free_geometry(geo);
+    return DG_EINVAL;
+  }
+  geo.n_pad = elems;
+  long long active = 0;
+  for (const GeoPart &p : geo.parts) active += p.n_active;
+  geo.n_active = active;
+  GK(cudaMalloc(&geo.d_nb, sizeof(int4) * (size_t)elems), "neighbour table allocation", DG_ENOMEM);
+  GK(cudaMalloc(&geo.d_exy, sizeof(int2) * (size_t)elems), "coordinate allocation", DG_ENOMEM);
+  const int4 pad = make_int4(kEdge, kEdge, kEdge, kEdge);
+  k_fill_int4<<<(unsigned)((elems + 255) / 256), 256, 0, s>>>(geo.d_nb, elems, pad);
+  cudaMemsetAsync(geo.d_exy, 0, sizeof(int2) * (size_t)elems, s);
+  int *d_bad = nullptr;
+  GK(tmp.alloc(&d_bad, 1), "flag allocation", DG_ENOMEM);
   cudaMemsetAsync(d_bad, 0, sizeof(int), s);
-  k_neighbours<<<(total + 255) / 256, 256, 0, s>>>(geo.d_exy, geo.d_cidx, total, nx, ny,
-                                                   periodic, geo.d_nb, d_bad);
-  if ((e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s)) !=
-          cudaSuccess ||
-      (e = cudaStreamSynchronize(s)) != cudaSuccess) {
-    err = std::string("neighbour table: ") + cudaGetErrorString(e);
-    code = DG_ECUDA;
-    goto done;
+  for (int g = 0; g < G; ++g) {
+    const GeoPart &p = geo.parts[g];
+    const int tx = (p.nx + kTile - 1) / kTile, ty = (p.ny + kTile - 1) / kTile;
+    const uint8_t *m = geo.d_mask + p.dense_off;
+    int *ci = geo.d_cidx + p.dense_off;
+    k_assign<<<tx * ty, kTile * kTile, 0, s>>>(m, p.nx, p.ny, offs[g], (int)p.off, ci, geo.d_exy);
+    k_neighbours<<<(unsigned)((p.n_active + 255) / 256), 256, 0, s>>>(
+        geo.d_exy, ci, (int)p.off, (int)p.n_active, p.nx, p.ny, p.periodic, (int)p.off,
+        (int)(p.off + p.n_active), geo.d_nb, d_bad);
   }
+  int bad = 0;
+  GK(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s), "neighbour table", DG_ECUDA);
+  GK(cudaStreamSynchronize(s), "neighbour table", DG_ECUDA);
   if (bad) {
     err = "neighbour table out of range";
-    code = DG_ECUDA;
-    goto done;
+    free_geometry(geo);
+    return DG_ECUDA;
   }
-  {
-    const int nch = (int)((total + kBlock - 1) / kBlock);
-    int hmax = 0;
-    if ((e = cudaMalloc(&geo.d_loc, sizeof(int4) * (size_t)total)) != cudaSuccess ||
-        (e = cudaMalloc(&geo.d_halo, sizeof(int2) * (size_t)nch * kHaloCap)) != cudaSuccess ||
-        (e = cudaMalloc(&geo.d_halo_cnt, sizeof(int) * ((size_t)nch + 1))) != cudaSuccess) {
-      err = std::string("halo table allocation: ") + cudaGetErrorString(e);
-      code = DG_ENOMEM;
-      goto done;
-    }
-    k_halo<<<nch, kBlock, 0, s>>>(geo.d_nb, total, geo.d_loc, geo.d_halo, geo.d_halo_cnt);
-    k_max_int<<<1, 256, 0, s>>>(geo.d_halo_cnt, nch, geo.d_halo_cnt + nch);
-    if ((e = cudaMemcpyAsync(&hmax, geo.d_halo_cnt + nch, sizeof(int), cudaMemcpyDeviceToHost, s)) !=
-            cudaSuccess ||
-        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
-      err = std::string("halo table: ") + cudaGetErrorString(e);
-      code = DG_ECUDA;
-      goto done;
-    }
-    if (hmax < 0 || hmax > kHaloCap) {
-      err = "halo table out of range";
-      code = DG_ECUDA;
-      goto done;
-    }
-    geo.halo_max = hmax;
+  // chunk table and per-geometry parameters
+  const long long nch = elems / kBlock;
+  std::vector<int2> chunk((size_t)nch);
+  std::vector<double4> gpar(G);
+  std::vector<float> gsf(G);
+  std::vector<double> gsd(G);
+  std::vector<int2> grange(G);
+  for (int g = 0; g < G; ++g) {
+    const GeoPart &p = geo.parts[g];
+    const long long c0 = p.off / kBlock;
+    const long long nc = (p.n_active + kBlock - 1) / kBlock;
+    for (long long c = 0; c < nc; ++c)
+      chunk[(size_t)(c0 + c)] = make_int2((int)std::min<long long>(kBlock, p.n_active - c * kBlock), g);
+    const double J = 0.5 * p.h;
+    gpar[g] = make_double4(p.x0, p.y0, p.h, 1.0 / (J * J));
+    gsf[g] = (float)(1.0 / (J * J));
+    gsd[g] = 1.0 / (J * J);
+    grange[g] = make_int2((int)p.off, (int)p.n_active);
   }
-done:
-  cudaFree(d_count);
-  cudaFree(d_off);
-  cudaFree(d_bad);
-  return code;
+  GK(cudaMalloc(&geo.d_chunk, sizeof(int2) * (size_t)nch), "chunk table allocation", DG_ENOMEM);
+  GK(cudaMalloc(&geo.d_gpar, sizeof(double4) * G), "parameter allocation", DG_ENOMEM);
+  GK(cudaMalloc(&geo.d_gscale_f, sizeof(float) * G), "parameter allocation", DG_ENOMEM);
+  GK(cudaMalloc(&geo.d_gscale_d, sizeof(double) * G), "parameter allocation", DG_ENOMEM);
+  GK(cudaMalloc(&geo.d_grange, sizeof(int2) * G), "parameter allocation", DG_ENOMEM);
+  GK(cudaMemcpyAsync(geo.d_chunk, chunk.data(), sizeof(int2) * chunk.size(), cudaMemcpyHostToDevice, s), "copy", DG_ECUDA);
+  GK(cudaMemcpyAsync(geo.d_gpar, gpar.data(), sizeof(double4) * G, cudaMemcpyHostToDevice, s), "copy", DG_ECUDA);
+  GK(cudaMemcpyAsync(geo.d_gscale_f, gsf.data(), sizeof(float) * G, cudaMemcpyHostToDevice, s), "copy", DG_ECUDA);
+  GK(cudaMemcpyAsync(geo.d_gscale_d, gsd.data(), sizeof(double) * G, cudaMemcpyHostToDevice, s), "copy", DG_ECUDA);
+  GK(cudaMemcpyAsync(geo.d_grange, grange.data(), sizeof(int2) * G, cudaMemcpyHostToDevice, s), "copy", DG_ECUDA);
+  // halo lists of every chunk
+  int hmax = 0;
+  GK(cudaMalloc(&geo.d_loc, sizeof(int4) * (size_t)elems), "halo table allocation", DG_ENOMEM);
+  GK(cudaMalloc(&geo.d_halo, sizeof(int2) * (size_t)nch * kHaloCap), "halo table allocation", DG_ENOMEM);
+  GK(cudaMalloc(&geo.d_halo_cnt, sizeof(int) * ((size_t)nch + 1)), "halo table allocation", DG_ENOMEM);
+  k_halo<<<(unsigned)nch, kBlock, 0, s>>>(geo.d_nb, geo.d_chunk, geo.d_loc, geo.d_halo, geo.d_halo_cnt);
+  k_max_int<<<1, 256, 0, s>>>(geo.d_halo_cnt, (int)nch, geo.d_halo_cnt + nch);
+  GK(cudaMemcpyAsync(&hmax, geo.d_halo_cnt + nch, sizeof(int), cudaMemcpyDeviceToHost, s), "halo table", DG_ECUDA);
+  geo.h_mask.resize((size_t)dense);
+  GK(cudaMemcpyAsync(geo.h_mask.data(), geo.d_mask, (size_t)dense, cudaMemcpyDeviceToHost, s), "mask copy", DG_ECUDA);
+  GK(cudaStreamSynchronize(s), "halo table", DG_ECUDA);
+  if (hmax < 0 || hmax > kHaloCap) {
+    err = "halo table out of range";
+    free_geometry(geo);
+    return DG_ECUDA;
+  }
+  geo.halo_max = hmax;
+  const GeoPart &p0 = geo.parts[0];
+  geo.nx = p0.nx; geo.ny = p0.ny; geo.h = p0.h; geo.x0 = p0.x0; geo.y0 = p0.y0;
+#undef GK
+  return DG_OK;
 }
 
 }  // namespace dg

@@ -33,8 +33,9 @@ struct Gll {
 bool gll_tables(int p, Gll *g);
 double rk3_real_axis_limit();
 
-// Operator scalars of one stage launch: out = u0 + beta (u - u0) + gamma R
-// (or beta u + gamma R without u0), where L u = (k / J^2) R.
+// Operator scalars of one stage launch: out = u0 + beta (u - u0) + gamma s_g R
+// (or beta u + gamma s_g R without u0), where L u = k s_g R and s_g = 1/J^2
+// of the element's geometry (J = h/2): gamma = beta dt k.
 template <typename T>
 struct StageCoef {
   T alpha, beta, gamma;  // alpha = 1 - beta, kept for reference only
@@ -50,25 +51,57 @@ struct StageTab {
   T inv_w;  // 1 / w_0 = 1 / w_p
 };
 
-// Device geometry of one domain.
-struct Geometry {
+// One geometry (domain) of a context.  A context holds G >= 1 of them; their
+// mesh elements are concatenated, each geometry padded to a multiple of
+// kBlock elements so that every block of kBlock consecutive elements (a
+// "chunk") belongs to one geometry.
+struct GeoPart {
   int nx = 0, ny = 0;
   double h = 0, x0 = 0, y0 = 0;
-  long long n_active = 0;
-  long long n_pad = 0;     // n_active rounded up to 32 (per-source stride in elements)
-  uint8_t *d_mask = nullptr;    // [ny*nx]
-  int *d_cidx = nullptr;        // [ny*nx] compact index or -1
-  int4 *d_nb = nullptr;         // [n_active] E, W, N, S
-  int2 *d_exy = nullptr;        // [n_active] element coordinates
+  long long n_active = 0;     // elements in the mesh
+  long long off = 0;          // first element in the concatenated numbering
+  long long dense_off = 0;    // offset of its [ny][nx] mask / index map
+  int periodic = 0;
+};
+
+// Host description of a geometry to build: a mask, or disks in a periodic
+// cell tiled into a window.
+struct PartSpec {
+  int nx = 0, ny = 0;
+  double h = 0, x0 = 0, y0 = 0;
+  const uint8_t *host_mask = nullptr;  // [ny][nx] or null
+  const double *cx = nullptr, *cy = nullptr, *r = nullptr;
+  int nd = 0;
+  double L = 0;
+  int n_cell = 0, tiles = 0;
+};
+
+struct Geometry {
+  std::vector<GeoPart> parts;
+  // geometry 0, for the single-geometry calls
+  int nx = 0, ny = 0;
+  double h = 0, x0 = 0, y0 = 0;
+  long long n_active = 0;       // all geometries
+  long long n_pad = 0;          // concatenated, padded element count = per-density stride
+  uint8_t *d_mask = nullptr;    // dense masks, geometry after geometry
+  int *d_cidx = nullptr;        // dense maps to the concatenated element index, or -1
+  int4 *d_nb = nullptr;         // [n_pad] E, W, N, S (concatenated indices, kWall, kEdge)
+  int2 *d_exy = nullptr;        // [n_pad] element coordinates inside its geometry
+  int2 *d_chunk = nullptr;      // [n_pad / kBlock] {live elements, geometry}
+  double4 *d_gpar = nullptr;    // [G] {x0, y0, h, 1/J^2}
+  float *d_gscale_f = nullptr;  // [G] 1/J^2
+  double *d_gscale_d = nullptr; // [G] 1/J^2
+  int2 *d_grange = nullptr;     // [G] {first element, elements in the mesh}
   std::vector<uint8_t> h_mask;  // host copy of d_mask
-  // Per block of kBlock consecutive elements ("chunk"): face neighbours
-  // outside the chunk are halo entries {element, its face toward the chunk}.
-  // d_loc gives, per element and face, the chunk-local index (0..kBlock-1),
-  // kBlock + halo slot, kWall or kEdge.
-  int4 *d_loc = nullptr;        // [n_active]
+  // Per chunk: face neighbours outside the chunk are halo entries
+  // {element, its face toward the chunk}.  d_loc gives, per element and face,
+  // the chunk-local index (0..kBlock-1), kBlock + halo slot, kWall or kEdge.
+  int4 *d_loc = nullptr;        // [n_pad]
   int2 *d_halo = nullptr;       // [n_chunks][kHaloCap]
-  int *d_halo_cnt = nullptr;    // [n_chunks]
+  int *d_halo_cnt = nullptr;    // [n_chunks + 1]
   int halo_max = 0;             // largest halo of any chunk
+  int G() const { return (int)parts.size(); }
+  long long n_chunks() const { return n_pad / kBlock; }
 };
 
 struct Ctx {
@@ -90,7 +123,8 @@ struct Ctx {
   double t = 0;
   long long steps = 0;
   std::vector<double> src;        // [m][2]
-  double *d_src = nullptr;        // [m][2]
+  double *d_src = nullptr;        // [G][m][2]
+  float4 *d_srel = nullptr;       // [G][m] start points in element units (hi, lo pairs)
   void *d_state = nullptr;        // 3 arrays of m * n_pad * Np elements
   size_t state_bytes = 0;
   bool state_owned = true;
@@ -110,7 +144,7 @@ struct Ctx {
 
   int np() const { return (cfg.p + 1) * (cfg.p + 1); }
   size_t esize() const { return cfg.precision == DG_FP64 ? 8 : 4; }
-  size_t field_elems() const { return (size_t)geo.n_pad * np(); }  // one source
+  size_t field_elems() const { return (size_t)geo.n_pad * np(); }  // one density slot
 };
 
 // ---- launchers (defined in the .cu files) ----
@@ -122,20 +156,19 @@ cudaError_t launch_stage_f32(int p, const float *u, const float *u0, float *out,
                              const Geometry &geo, long long stride, int m,
                              const Gll &g, const StageCoef<float> &c, cudaStream_t s);
 
-// Geometry construction.
-cudaError_t build_mask_disks(const double *d_cx, const double *d_cy, const double *d_r,
-                             int nd, double L, int n_cell, int tiles, uint8_t *d_mask,
-                             cudaStream_t s);
-// Compaction in tile order and the neighbour table; fills geo (allocates).
-int build_connectivity(Geometry &geo, int periodic, cudaStream_t s, std::string &err);
+// Geometry construction: masks, compaction in tile order, neighbour and halo
+// tables for every part; fills geo (allocates).  Returns a DG_* code.
+int build_geometry(Geometry &geo, const std::vector<PartSpec> &parts, int periodic,
+                   cudaStream_t s, std::string &err);
 void free_geometry(Geometry &geo);
 
 // Densities, moments, covariance.
 cudaError_t launch_init_sources(const Ctx &c, void *u, cudaStream_t s);
 cudaError_t launch_moments(const Ctx &c, const void *u, double *d_part, double *d_mom,
                            cudaStream_t s);
-cudaError_t launch_covariance(const double *d_mom, const double *d_mom0, int m,
+cudaError_t launch_covariance(const double *d_mom, const double *d_mom0, int m, int G,
                               double *d_out, cudaStream_t s);
+int moment_blocks(int G);  // first-pass blocks per density of the moment reduction
 cudaError_t launch_nodes_to_dense(const Ctx &c, const void *u, double *d_dense,
                                   cudaStream_t s);
 cudaError_t launch_dense_to_nodes(const Ctx &c, const double *d_dense, void *u,

@@ -1,5 +1,6 @@
 // dg_reduce.cu -- start densities, FP64 moment reduction, covariance of the
 // mixture (Sec. 4.1), node layout conversion, power-iteration helpers.
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 
@@ -30,48 +31,68 @@ static NodeGeo node_geo(const Ctx &c) {
 // Normalised Gaussian of width sigma0 about each start point (stand-in for the
 // Dirac data of Sec. 4.1), interpolated at the GLL nodes; FP64 arithmetic,
 // stored in the state precision.  grid (ceil(nA/256), m).
+// ---- start points in element units ------------------------------------------
+// For density (g, s): sx = (xs - x0_g)/h_g - 1/2, so that the centre of element
+// column ex sits at (ex - sx) h_g from the start point; stored as two floats
+// (hi + lo) so that FP32 arithmetic forms ex - sx with an error relative to
+// the displacement itself, not to the window size.
+__global__ void k_src_rel(const double *__restrict__ src, const int2 *__restrict__ grange,
+                          const double4 *__restrict__ gpar, int m, int G,
+                          float4 *__restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= G * m) return;
+  const int g = i / m;
+  const double4 gp = gpar[g];
+  const double sx = (src[2 * i] - gp.x) / gp.z - 0.5;
+  const double sy = (src[2 * i + 1] - gp.y) / gp.z - 0.5;
+  const float sxh = (float)sx, syh = (float)sy;
+  out[i] = make_float4(sxh, (float)(sx - (double)sxh), syh, (float)(sy - (double)syh));
+}
+
+__device__ __forceinline__ float rel_coord(int e, float hi, float lo, float h) {
+  return (((float)e - hi) - lo) * h;
+}
+
 template <typename T, int P>
-__global__ void k_init(const int2 *__restrict__ exy, long long nA, long long stride,
-                       const double *__restrict__ src, double sigma0, const NodeGeo g,
-                       T *__restrict__ u) {
+__global__ void k_init(const int2 *__restrict__ exy, const int2 *__restrict__ chunk_tab,
+                       const double4 *__restrict__ gpar, long long stride, int m,
+                       const double *__restrict__ src, const float4 *__restrict__ srel,
+                       double cnorm, double inv2s2, const NodeGeo g, T *__restrict__ u) {
   constexpr int n = P + 1, NP = n * n;
-  const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= nA) return;
+  const int chunk = blockIdx.x;
+  const int2 ci = chunk_tab[chunk];
+  if ((int)threadIdx.x >= ci.x) return;
+  const long long a = (long long)chunk * kBlock + threadIdx.x;
   const int s = blockIdx.y;
-  const double xs = src[2 * s], ys = src[2 * s + 1];
+  const size_t ds = (size_t)ci.y * m + s;
   const int2 e = exy[a];
-  const double c = 1.0 / (2.0 * M_PI * sigma0 * sigma0);
-  const double inv2s2 = 1.0 / (2.0 * sigma0 * sigma0);
   T *out = u + ((size_t)s * stride + a) * NP;
-  // exp(-(dx^2 + dy^2)/(2 s^2)) = exp(-dx^2/(2 s^2)) exp(-dy^2/(2 s^2)): 2n
-  // exponentials per element instead of n^2; elements whose largest
-  // exponent already underflows the state precision are written as zeros.
-  double ax[n], ay[n], amax_x = -1e300, amax_y = -1e300;
-#pragma unroll
-  for (int i = 0; i < n; ++i) {
-    const double dx = g.x0 + (e.x + 0.5) * g.h + 0.5 * g.h * g.xi[i] - xs;
-    const double dy = g.y0 + (e.y + 0.5) * g.h + 0.5 * g.h * g.xi[i] - ys;
-    ax[i] = -(dx * dx) * inv2s2;
-    ay[i] = -(dy * dy) * inv2s2;
-    amax_x = fmax(amax_x, ax[i]);
-    amax_y = fmax(amax_y, ay[i]);
-  }
-  const double floor_exp = sizeof(T) == 4 ? -110.0 : -760.0;
   T v[NP];
-  if (amax_x + amax_y < floor_exp) {
 #pragma unroll
-    for (int k = 0; k < NP; ++k) v[k] = (T)0;
-  } else {
+  for (int k = 0; k < NP; ++k) v[k] = (T)0;
+  // element-level test: the nearest point of the element to the start point
+  // already underflows the state precision -> the element is zero
+  const double4 gp = gpar[ci.y];
+  const float4 sr = srel[ds];
+  const float hf = (float)gp.z;
+  const float X = rel_coord(e.x, sr.x, sr.y, hf), Y = rel_coord(e.y, sr.z, sr.w, hf);
+  const float dxm = fmaxf(fabsf(X) - 0.5f * hf, 0.0f), dym = fmaxf(fabsf(Y) - 0.5f * hf, 0.0f);
+  const float floor_exp = sizeof(T) == 4 ? 110.0f : 760.0f;
+  if ((dxm * dxm + dym * dym) * (float)inv2s2 < floor_exp) {
+    // exp(-(dx^2 + dy^2)/(2 s^2)) = exp(-dx^2/(2 s^2)) exp(-dy^2/(2 s^2)), FP64
+    const double xs = src[2 * ds], ys = src[2 * ds + 1];
     double gx[n], gy[n];
 #pragma unroll
     for (int i = 0; i < n; ++i) {
-      gx[i] = exp(ax[i]);
-      gy[i] = exp(ay[i]);
+      const double dx = gp.x + (e.x + 0.5) * gp.z + 0.5 * gp.z * g.xi[i] - xs;
+      const double dy = gp.y + (e.y + 0.5) * gp.z + 0.5 * gp.z * g.xi[i] - ys;
+      gx[i] = exp(-(dx * dx) * inv2s2);
+      gy[i] = exp(-(dy * dy) * inv2s2);
     }
 #pragma unroll
     for (int j = 0; j < n; ++j)
 #pragma unroll
-      for (int i = 0; i < n; ++i) v[j * n + i] = (T)(c * (gx[i] * gy[j]));
+      for (int i = 0; i < n; ++i) v[j * n + i] = (T)(cnorm * (gx[i] * gy[j]));
   }
   store_elem<T, NP>(out, v);
 }
@@ -158,15 +179,20 @@ __device__ __forceinline__ void add_element_moments(double X, double Y, double J
   acc[6] += J2 * lm[6];
 }
 
+// grid (B, m, G): blocks b of density s of geometry g stride over that
+// geometry's elements; partial sums part[((g m + s) B + b)][7].
 template <typename T, int P>
 __global__ void __launch_bounds__(256)
-    k_moments(const int2 *__restrict__ exy, long long nA, long long stride,
-              const double *__restrict__ src, const NodeGeo g, const T *__restrict__ u,
-              double *__restrict__ part) {
+    k_moments(const int2 *__restrict__ exy, const int2 *__restrict__ grange,
+              const double4 *__restrict__ gpar, long long stride, int m,
+              const double *__restrict__ src, const float4 *__restrict__ srel, const NodeGeo g,
+              const T *__restrict__ u, double *__restrict__ part) {
   constexpr int n = P + 1, NP = n * n;
-  const int s = blockIdx.y;
-  const double xs = src[2 * s], ys = src[2 * s + 1];
-  const double J = 0.5 * g.h;
+  const int s = blockIdx.y, gi = blockIdx.z;
+  const int2 rg = grange[gi];
+  const double4 gp = gpar[gi];
+  const double xs = src[2 * ((size_t)gi * m + s)], ys = src[2 * ((size_t)gi * m + s) + 1];
+  const double J = 0.5 * gp.z;
   T w[n], wx[n], wxx[n];
 #pragma unroll
   for (int i = 0; i < n; ++i) {
@@ -176,21 +202,38 @@ __global__ void __launch_bounds__(256)
   }
   double acc[kMomFields] = {0, 0, 0, 0, 0, 0, 0};
   const T *U = u + (size_t)s * stride * NP;
-  for (long long a = (long long)blockIdx.x * 256 + threadIdx.x; a < nA;
-       a += (long long)gridDim.x * 256) {
+  const float4 sr = srel[(size_t)gi * m + s];
+  const float hf = (float)gp.z, Jf = 0.5f * hf, J2f = Jf * Jf;
+  for (long long k = (long long)blockIdx.x * 256 + threadIdx.x; k < rg.y;
+       k += (long long)gridDim.x * 256) {
+    const long long a = rg.x + k;
     const int2 e = exy[a];
     T lmT[7];
     local_moments<T, P>(U + (size_t)a * NP, w, wx, wxx, lmT);
-    double lm[7];
+    if constexpr (sizeof(T) == 4) {
+      // FP32 state: the element's contribution in FP32, accumulated in FP64
+      const float X = rel_coord(e.x, sr.x, sr.y, hf), Y = rel_coord(e.y, sr.z, sr.w, hf);
+      const float m00 = lmT[0], m10 = Jf * lmT[1], m01 = Jf * lmT[2];
+      const float m20 = J2f * lmT[3], m11 = J2f * lmT[4], m02 = J2f * lmT[5];
+      acc[0] += (double)(J2f * m00);
+      acc[1] += (double)(J2f * (X * m00 + m10));
+      acc[2] += (double)(J2f * (Y * m00 + m01));
+      acc[3] += (double)(J2f * (X * (X * m00 + 2.0f * m10) + m20));
+      acc[4] += (double)(J2f * (X * (Y * m00 + m01) + Y * m10 + m11));
+      acc[5] += (double)(J2f * (Y * (Y * m00 + 2.0f * m01) + m02));
+      acc[6] += (double)(J2f * lmT[6]);
+    } else {
+      double lm[7];
 #pragma unroll
-    for (int k = 0; k < 7; ++k) lm[k] = (double)lmT[k];
-    const double X = g.x0 + (e.x + 0.5) * g.h - xs;
-    const double Y = g.y0 + (e.y + 0.5) * g.h - ys;
-    add_element_moments(X, Y, J, lm, acc);
+      for (int q = 0; q < 7; ++q) lm[q] = (double)lmT[q];
+      const double X = gp.x + (e.x + 0.5) * gp.z - xs;
+      const double Y = gp.y + (e.y + 0.5) * gp.z - ys;
+      add_element_moments(X, Y, J, lm, acc);
+    }
   }
   block_sum7(acc);
   if (threadIdx.x == 0) {
-    double *o = part + ((size_t)s * gridDim.x + blockIdx.x) * kMomFields;
+    double *o = part + (((size_t)gi * m + s) * gridDim.x + blockIdx.x) * kMomFields;
 #pragma unroll
     for (int f = 0; f < kMomFields; ++f) o[f] = acc[f];
   }
@@ -215,14 +258,15 @@ __global__ void __launch_bounds__(256)
 // ---- covariance (Sec. 4.1) ---------------------------------------------------
 // Each density normalised by its mass, mixed with weights 1/m; moment-matched
 // Gaussian: mu = mean M1/M0, Sigma_mix = mean M2/M0 - mu mu^T; reported
-// Sigma = Sigma_mix(t) - Sigma_mix(0).  One thread, sources in order.
-// out = {Sxx, Sxy, Syy, mux, muy}.
+// Sigma = Sigma_mix(t) - Sigma_mix(0).  One thread per geometry, densities in
+// order.  out[g] = {Sxx, Sxy, Syy, mux, muy}.
 __global__ void k_covariance(const double *__restrict__ mom, const double *__restrict__ mom0,
-                             int m, double *__restrict__ out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+                             int m, int G, double *__restrict__ out) {
+  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= G) return;
   double r[2][5];
   for (int k = 0; k < 2; ++k) {
-    const double *M = k == 0 ? mom : mom0;
+    const double *M = (k == 0 ? mom : mom0) + (size_t)gi * m * kMomFields;
     double mx = 0, my = 0, sxx = 0, sxy = 0, syy = 0;
     for (int s = 0; s < m; ++s) {
       const double *q = M + (size_t)s * kMomFields;
@@ -241,11 +285,12 @@ __global__ void k_covariance(const double *__restrict__ mom, const double *__res
     r[k][3] = mx;
     r[k][4] = my;
   }
-  out[0] = r[0][0] - r[1][0];
-  out[1] = r[0][1] - r[1][1];
-  out[2] = r[0][2] - r[1][2];
-  out[3] = r[0][3];
-  out[4] = r[0][4];
+  double *o = out + (size_t)gi * 5;
+  o[0] = r[0][0] - r[1][0];
+  o[1] = r[0][1] - r[1][1];
+  o[2] = r[0][2] - r[1][2];
+  o[3] = r[0][3];
+  o[4] = r[0][4];
 }
 
 // ---- node layout conversion ------------------------------------------------
@@ -285,27 +330,30 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
   return x ^ (x >> 31);
 }
 
-__global__ void k_random_field(long long nvals, unsigned long long seed, double *__restrict__ v) {
+__global__ void k_random_field(long long nvals, int np, const int2 *__restrict__ chunk_tab,
+                               unsigned long long seed, double *__restrict__ v) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nvals) return;
-  v[t] = (double)(splitmix64(seed + (unsigned long long)t) >> 11) * 0x1.0p-53 - 0.5;
+  const long long a = t / np;
+  const bool live = (int)(a % kBlock) < chunk_tab[a / kBlock].x;
+  v[t] = live ? (double)(splitmix64(seed + (unsigned long long)t) >> 11) * 0x1.0p-53 - 0.5 : 0.0;
 }
 
 template <int P>
 __global__ void __launch_bounds__(256)
-    k_wnorm2(long long nA, const double *__restrict__ v, double J2w0, const NodeGeo g,
-             double *__restrict__ part) {
+    k_wnorm2(long long n_elems, const int2 *__restrict__ chunk_tab, const double *__restrict__ v,
+             const NodeGeo g, double *__restrict__ part) {
   constexpr int n = P + 1, NP = n * n;
   double acc[kMomFields] = {0, 0, 0, 0, 0, 0, 0};
-  for (long long a = (long long)blockIdx.x * 256 + threadIdx.x; a < nA;
+  for (long long a = (long long)blockIdx.x * 256 + threadIdx.x; a < n_elems;
        a += (long long)gridDim.x * 256) {
+    if ((int)(a % kBlock) >= chunk_tab[a / kBlock].x) continue;
     const double *ve = v + (size_t)a * NP;
 #pragma unroll
     for (int j = 0; j < n; ++j)
 #pragma unroll
       for (int i = 0; i < n; ++i) acc[0] += g.w[i] * g.w[j] * ve[j * n + i] * ve[j * n + i];
   }
-  (void)J2w0;
   block_sum7(acc);
   if (threadIdx.x == 0) {
     double *o = part + (size_t)blockIdx.x * kMomFields;
@@ -338,48 +386,56 @@ __global__ void k_scale_rnorm(long long nvals, const double *__restrict__ in,
   }
 
 cudaError_t launch_init_sources(const Ctx &c, void *u, cudaStream_t s) {
-  const long long nA = c.geo.n_active;
-  const dim3 grid((unsigned)((nA + 255) / 256), (unsigned)c.m);
+  const int G = c.geo.G();
+  k_src_rel<<<(G * c.m + 127) / 128, 128, 0, s>>>(c.d_src, c.geo.d_grange, c.geo.d_gpar, c.m, G,
+                                                   c.d_srel);
+  const dim3 grid((unsigned)c.geo.n_chunks(), (unsigned)c.m);
   const NodeGeo g = node_geo(c);
+  const double s2 = c.cfg.sigma0 * c.cfg.sigma0;
+  const double cnorm = 1.0 / (2.0 * M_PI * s2), inv2s2 = 1.0 / (2.0 * s2);
   if (c.cfg.precision == DG_FP64) {
-    DG_P_SWITCH(c.cfg.p, (k_init<double, PP><<<grid, 256, 0, s>>>(
-                             c.geo.d_exy, nA, c.geo.n_pad, c.d_src, c.cfg.sigma0, g,
-                             (double *)u)));
+    DG_P_SWITCH(c.cfg.p, (k_init<double, PP><<<grid, kBlock, 0, s>>>(
+                             c.geo.d_exy, c.geo.d_chunk, c.geo.d_gpar, c.geo.n_pad, c.m,
+                             c.d_src, c.d_srel, cnorm, inv2s2, g, (double *)u)));
   } else {
-    DG_P_SWITCH(c.cfg.p, (k_init<float, PP><<<grid, 256, 0, s>>>(
-                             c.geo.d_exy, nA, c.geo.n_pad, c.d_src, c.cfg.sigma0, g,
-                             (float *)u)));
+    DG_P_SWITCH(c.cfg.p, (k_init<float, PP><<<grid, kBlock, 0, s>>>(
+                             c.geo.d_exy, c.geo.d_chunk, c.geo.d_gpar, c.geo.n_pad, c.m,
+                             c.d_src, c.d_srel, cnorm, inv2s2, g, (float *)u)));
   }
   return cudaGetLastError();
 }
+
+int moment_blocks(int G) { return std::max(8, std::min(kMomBlocks, 4864 / std::max(G, 1))); }
 
 cudaError_t launch_moments(const Ctx &c, const void *u, double *d_part, double *d_mom,
                            cudaStream_t s) {
-  const long long nA = c.geo.n_active;
-  const dim3 grid(kMomBlocks, (unsigned)c.m);
+  const int G = c.geo.G();
+  const int B = moment_blocks(G);
+  const dim3 grid((unsigned)B, (unsigned)c.m, (unsigned)G);
   const NodeGeo g = node_geo(c);
   if (c.cfg.precision == DG_FP64) {
     DG_P_SWITCH(c.cfg.p, (k_moments<double, PP><<<grid, 256, 0, s>>>(
-                             c.geo.d_exy, nA, c.geo.n_pad, c.d_src, g, (const double *)u,
-                             d_part)));
+                             c.geo.d_exy, c.geo.d_grange, c.geo.d_gpar, c.geo.n_pad, c.m,
+                             c.d_src, c.d_srel, g, (const double *)u, d_part)));
   } else {
     DG_P_SWITCH(c.cfg.p, (k_moments<float, PP><<<grid, 256, 0, s>>>(
-                             c.geo.d_exy, nA, c.geo.n_pad, c.d_src, g, (const float *)u,
-                             d_part)));
+                             c.geo.d_exy, c.geo.d_grange, c.geo.d_gpar, c.geo.n_pad, c.m,
+                             c.d_src, c.d_srel, g, (const float *)u, d_part)));
   }
-  k_moments_final<<<c.m, 256, 0, s>>>(d_part, kMomBlocks, d_mom);
+  k_moments_final<<<(unsigned)(c.m * G), 256, 0, s>>>(d_part, B, d_mom);
   return cudaGetLastError();
 }
 
-cudaError_t launch_covariance(const double *d_mom, const double *d_mom0, int m,
+cudaError_t launch_covariance(const double *d_mom, const double *d_mom0, int m, int G,
                               double *d_out, cudaStream_t s) {
-  k_covariance<<<1, 32, 0, s>>>(d_mom, d_mom0, m, d_out);
+  k_covariance<<<(G + 127) / 128, 128, 0, s>>>(d_mom, d_mom0, m, G, d_out);
   return cudaGetLastError();
 }
 
+// Dense node layout of geometry 0 (single-geometry contexts).
 cudaError_t launch_nodes_to_dense(const Ctx &c, const void *u, double *d_dense,
                                   cudaStream_t s) {
-  const long long nA = c.geo.n_active;
+  const long long nA = c.geo.parts[0].n_active;
   const dim3 grid((unsigned)((nA + 255) / 256), (unsigned)c.m);
   if (c.cfg.precision == DG_FP64) {
     DG_P_SWITCH(c.cfg.p, (k_to_dense<double, PP><<<grid, 256, 0, s>>>(
@@ -395,7 +451,7 @@ cudaError_t launch_nodes_to_dense(const Ctx &c, const void *u, double *d_dense,
 
 cudaError_t launch_dense_to_nodes(const Ctx &c, const double *d_dense, void *u,
                                   cudaStream_t s) {
-  const long long nA = c.geo.n_active;
+  const long long nA = c.geo.parts[0].n_active;
   const dim3 grid((unsigned)((nA + 255) / 256), (unsigned)c.m);
   if (c.cfg.precision == DG_FP64) {
     DG_P_SWITCH(c.cfg.p, (k_from_dense<double, PP><<<grid, 256, 0, s>>>(
@@ -411,15 +467,15 @@ cudaError_t launch_dense_to_nodes(const Ctx &c, const double *d_dense, void *u,
 
 cudaError_t launch_random_field(const Ctx &c, double *v, unsigned long long seed,
                                 cudaStream_t s) {
-  const long long nv = c.geo.n_active * c.np();
-  k_random_field<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(nv, seed, v);
+  const long long nv = c.geo.n_pad * c.np();
+  k_random_field<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(nv, c.np(), c.geo.d_chunk, seed, v);
   return cudaGetLastError();
 }
 
 cudaError_t launch_wnorm2(const Ctx &c, const double *v, double *d_part, double *d_res,
                           cudaStream_t s) {
   const NodeGeo g = node_geo(c);
-  DG_P_SWITCH(c.cfg.p, (k_wnorm2<PP><<<kMomBlocks, 256, 0, s>>>(c.geo.n_active, v, 0.0, g,
+  DG_P_SWITCH(c.cfg.p, (k_wnorm2<PP><<<kMomBlocks, 256, 0, s>>>(c.geo.n_pad, c.geo.d_chunk, v, g,
                                                                  d_part)));
   k_moments_final<<<1, 256, 0, s>>>(d_part, kMomBlocks, d_res);
   return cudaGetLastError();
@@ -427,7 +483,7 @@ cudaError_t launch_wnorm2(const Ctx &c, const double *v, double *d_part, double 
 
 cudaError_t launch_scale_by_rnorm(const Ctx &c, const double *in, const double *d_res,
                                   double *out, cudaStream_t s) {
-  const long long nv = c.geo.n_active * c.np();
+  const long long nv = c.geo.n_pad * c.np();
   k_inv_norm<<<1, 32, 0, s>>>(const_cast<double *>(d_res));
   k_scale_rnorm<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(nv, in, d_res, out);
   return cudaGetLastError();

@@ -4,6 +4,7 @@
 // nodal values sit in registers, the four face neighbours are read whole
 // (through L1/L2; they are other threads' elements) and the stage result
 //   out = u0 + beta (u - u0) + gamma R(u),   L u = (k / J^2) R(u),
+// (gamma = beta dt k / J^2, J = h/2 of the element's geometry),
 // is written once (u0 absent: out = beta u + gamma R).  This increment form
 // of the Shu-Osher combination (1 - beta) u0 + beta (u + dt L u) keeps the
 // weight of u0 exactly 1 - beta in any precision, so FP32 rounding of 1/3
@@ -284,7 +285,8 @@ template <typename T, int P, bool HAS_U0>
 __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
     k_stage(const T *__restrict__ uin, const T *u0, T *out,
             const int4 *__restrict__ loc, const int2 *__restrict__ halo,
-            const int *__restrict__ halo_cnt, long long nA, long long stride, int nrec,
+            const int *__restrict__ halo_cnt, const int2 *__restrict__ chunk_tab,
+            const T *__restrict__ gscale, long long stride, int nrec,
             const StageTab<T, P> tb, const StageCoef<T> c) {
   constexpr int n = P + 1, NP = n * n;
   using St = Stage<T, NP>;
@@ -301,7 +303,9 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
 
   const int chunk = blockIdx.x;
   const long long a0 = (long long)chunk * kBlock;
-  const int cnt = (int)min((long long)kBlock, nA - a0);
+  const int2 ci = __ldg(chunk_tab + chunk);  // {elements in the mesh, geometry}
+  const int cnt = ci.x;
+  const T gam = c.gamma * __ldg(gscale + ci.y);  // beta dt D / J^2 of this geometry
   const int el = threadIdx.x;
   const bool live = el < cnt;
   const size_t sbase = (size_t)blockIdx.y * (size_t)stride * NP;
@@ -438,10 +442,10 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
     if constexpr (HAS_U0) {
       St::read(so, el, o);
 #pragma unroll
-      for (int k = 0; k < NP; ++k) o[k] = o[k] + c.beta * (u[k] - o[k]) + c.gamma * R[k];
+      for (int k = 0; k < NP; ++k) o[k] = o[k] + c.beta * (u[k] - o[k]) + gam * R[k];
     } else {
 #pragma unroll
-      for (int k = 0; k < NP; ++k) o[k] = c.beta * u[k] + c.gamma * R[k];
+      for (int k = 0; k < NP; ++k) o[k] = c.beta * u[k] + gam * R[k];
     }
     St::write(so, el, o);
   }
@@ -478,9 +482,11 @@ template <typename T, int P>
 cudaError_t launch_stage_p(const T *u, const T *u0, T *out, const Geometry &geo,
                            long long stride, int m, const Gll &g, const StageCoef<T> &c,
                            cudaStream_t s) {
-  const long long nA = geo.n_active;
-  if (nA <= 0 || m <= 0) return cudaSuccess;
-  const dim3 grid((unsigned)((nA + kBlock - 1) / kBlock), (unsigned)m);
+  if (geo.n_pad <= 0 || m <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)geo.n_chunks(), (unsigned)m);
+  const T *gscale;
+  if constexpr (sizeof(T) == 8) gscale = geo.d_gscale_d;
+  else gscale = geo.d_gscale_f;
   const StageTab<T, P> tb = make_tab<T, P>(g);
   const int nrec = 4 * kBlock + geo.halo_max + 1;
   const int smem = stage_smem_bytes<T, P>(geo.halo_max);
@@ -496,10 +502,12 @@ cudaError_t launch_stage_p(const T *u, const T *u0, T *out, const Geometry &geo,
   }
   if (u0)
     k_stage<T, P, true><<<grid, kBlock, smem, s>>>(u, u0, out, geo.d_loc, geo.d_halo,
-                                                   geo.d_halo_cnt, nA, stride, nrec, tb, c);
+                                                   geo.d_halo_cnt, geo.d_chunk, gscale, stride,
+                                                   nrec, tb, c);
   else
     k_stage<T, P, false><<<grid, kBlock, smem, s>>>(u, u0, out, geo.d_loc, geo.d_halo,
-                                                    geo.d_halo_cnt, nA, stride, nrec, tb, c);
+                                                    geo.d_halo_cnt, geo.d_chunk, gscale, stride,
+                                                    nrec, tb, c);
   return cudaGetLastError();
 }
 
