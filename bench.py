@@ -41,7 +41,14 @@ import dginputs  # noqa: E402
 
 METRIC = "DoF-steps/s"
 BYTES_PER_DOF_STEP = {"f32": 32, "f64": 64}   # 8 state accesses per RK step
-FLOPS_PER_DOF_STEP = {3: 120}                  # 3 stages x (2n^3 + 12n^2) * 2 / n^2 at n = 4
+
+
+def flops_per_dof_step(p: int) -> float:
+    """Sum-factorised FMAs per element and stage: volume 2n^3, own face
+    derivatives 4n^2, lifting 4n^2, fluxes ~4n^2 -> 2 flops each, per node,
+    times 3 stages."""
+    n = p + 1
+    return 3 * 2 * (2 * n ** 3 + 12 * n ** 2) / n ** 2
 
 
 def _peaks():
@@ -297,7 +304,7 @@ def main():
                     help="start points per GPU (64 = the workload; fewer for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
-    ap.add_argument("--workload", default="cell40", choices=["cell40", "batch"])
+    ap.add_argument("--workload", default="cell40", choices=["cell40", "batch", "p5"])
     ap.add_argument("--batch-geometries", type=int, default=512)
     ap.add_argument("--batch-gb", type=float, default=60.0)
     args = ap.parse_args()
@@ -321,7 +328,10 @@ def main():
     torch.cuda.set_device(local)
     dev = local
 
-    w = dginputs.workload_cell40(args.seed, m=64)
+    if args.workload == "p5":
+        w = dginputs.workload_p5(args.seed, m=32)
+    else:
+        w = dginputs.workload_cell40(args.seed, m=64)
     w.sources = w.sources[:args.densities]
     # weak scaling: every rank its own 64 start points
     if world > 1:
@@ -388,7 +398,7 @@ def main():
     if args.precision == "f64":
         # FP64 is bound by the FP64 pipe (2 FMA/clk/SM): 152 x 2 x 2 x 2.07 GHz
         peak_f64 = 152 * 2 * 2 * 2.07e9 / 1e12
-        roofline = {"bound": "alu", "achieved": FLOPS_PER_DOF_STEP.get(w.p, 120) * dof / 3.0
+        roofline = {"bound": "alu", "achieved": flops_per_dof_step(w.p) * dof / 3.0
                     / (stage_ms * 1e-3) / 1e12, "peak": peak_f64, "unit": "TFLOP/s",
                     "traffic": traffic, "peak_source": "derived from unit counts and max clock"}
         roofline["frac"] = roofline["achieved"] / peak_f64

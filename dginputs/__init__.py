@@ -81,6 +81,16 @@ def gamma_disks(seed: int, L: float, shape: float, scale: float, *,
     cx = np.empty(radii.size)
     cy = np.empty(radii.size)
     rr_out = np.empty(radii.size)
+    # cell lists: two disks can only conflict when their centres are closer
+    # than 2 r_max + gap, so a candidate is checked against the disks of its
+    # own and the 8 neighbouring cells (periodic); the accepted candidate is
+    # the same as with an all-pairs check
+    r_max = float(radii[0]) if radii.size else 0.0
+    ncell = int(L // (2.0 * r_max + min_gap)) if radii.size else 0
+    use_cells = ncell >= 3
+    cap = 8
+    members = np.zeros((max(ncell, 1) ** 2, cap), dtype=np.int64)
+    count = np.zeros(max(ncell, 1) ** 2, dtype=np.int64)
     k = 0
     for r in radii:
         placed = False
@@ -91,15 +101,39 @@ def gamma_disks(seed: int, L: float, shape: float, scale: float, *,
             tries += nb
             if k == 0:
                 ok = np.ones(nb, dtype=bool)
-            else:
+            elif not use_cells:
                 dx = _min_image(cand[:, 0:1] - cx[None, :k], L)
                 dy = _min_image(cand[:, 1:2] - cy[None, :k], L)
                 need = (rr_out[None, :k] + r + min_gap) ** 2
                 ok = np.all(dx * dx + dy * dy >= need, axis=1)
+            else:
+                ci = np.minimum((cand[:, 0] * ncell / L).astype(np.int64), ncell - 1)
+                cj = np.minimum((cand[:, 1] * ncell / L).astype(np.int64), ncell - 1)
+                ok = np.ones(nb, dtype=bool)
+                for di in (-1, 0, 1):
+                    for dj in (-1, 0, 1):
+                        cid = ((cj + dj) % ncell) * ncell + (ci + di) % ncell
+                        w = int(count[cid].max())
+                        if w == 0:
+                            continue
+                        idx = members[cid, :w]
+                        msk = np.arange(w)[None, :] < count[cid][:, None]
+                        dx = _min_image(cand[:, 0:1] - cx[idx], L)
+                        dy = _min_image(cand[:, 1:2] - cy[idx], L)
+                        need = (rr_out[idx] + r + min_gap) ** 2
+                        ok &= np.all((dx * dx + dy * dy >= need) | ~msk, axis=1)
             idx = np.flatnonzero(ok)
             if idx.size:
                 cx[k], cy[k] = cand[idx[0]]
                 rr_out[k] = r
+                if use_cells:
+                    c0 = min(int(cy[k] * ncell / L), ncell - 1) * ncell + \
+                        min(int(cx[k] * ncell / L), ncell - 1)
+                    if count[c0] == cap:
+                        members = np.concatenate([members, np.zeros_like(members)], axis=1)
+                        cap *= 2
+                    members[c0, count[c0]] = k
+                    count[c0] += 1
                 k += 1
                 placed = True
     cx, cy, rr_out = cx[:k].copy(), cy[:k].copy(), rr_out[:k].copy()
