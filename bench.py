@@ -393,7 +393,7 @@ def main():
     achieved = bytes_per_launch / (stage_ms * 1e-3) / 1e9
     rec = _traffic_record(os.path.join(ROOT, "paper_1907_06191_gb300", "csrc", "dg_stage.cuh"))
     traffic = None
-    if rec and rec.get("precision") == args.precision:
+    if rec and rec.get("precision") == args.precision and rec.get("p") == w.p:
         traffic = rec["dram_bytes_per_launch_per_dof"] * dof
     if args.precision == "f64":
         # FP64 is bound by the FP64 pipe (2 FMA/clk/SM): 152 x 2 x 2 x 2.07 GHz
