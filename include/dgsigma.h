@@ -211,6 +211,15 @@ int dg_covariance(dg_ctx *ctx, double *sigma3, double *mu2, double *mass);
  * mass [G][m] (or NULL); the mixture of geometry g is its own m densities. */
 int dg_covariance_batch(dg_ctx *ctx, double *sigma3, double *mu2, double *mass);
 
+/* Least-squares residual of the Gaussian fit (Sec. 4.2, the sum over nodes of
+ * [f(x; Sigma) - u_ij]^2 by which the paper judges the fit).  For each
+ * density, normalised by its mass and centred at its start point, the sum
+ * runs over its own nodes against the bivariate Gaussian f of the mixture
+ * fit (mean mu and covariance Sigma_mix(t), the start width not removed);
+ * out[g] (one value per geometry) is the mean over the densities, in um^-4.
+ * Computed on the device in FP64. */
+int dg_ls_residual(dg_ctx *ctx, double *out);
+
 /* Mixture covariance (Sec. 4.1) of raw moments supplied by the caller, e.g.
  * moments of densities propagated on several GPUs and gathered: mom and mom0
  * are host arrays [m][6] = {M0, Mx, My, Mxx, Mxy, Myy} at t and at t = 0.

@@ -248,6 +248,40 @@ def aggregate(mom: np.ndarray, mom0: np.ndarray | None = None):
     return s, mu, m0
 
 
+def mixture_fit(mom: np.ndarray):
+    """Moment-matched Gaussian of the mixture (Sec. 4.1) without removing the
+    start width: (mu [2], Sigma_mix [2, 2])."""
+    mm = np.asarray(mom, dtype=np.float64).reshape(-1, 6)
+    m0 = mm[:, 0]
+    mu = np.array([np.mean(mm[:, 1] / m0), np.mean(mm[:, 2] / m0)])
+    S = np.array([[np.mean(mm[:, 3] / m0), np.mean(mm[:, 4] / m0)],
+                  [np.mean(mm[:, 4] / m0), np.mean(mm[:, 5] / m0)]])
+    return mu, S - np.outer(mu, mu)
+
+
+def ls_residual(mesh: Mesh, fields, sources, mom) -> float:
+    """Least-squares residual of the Gaussian fit (Sec. 4.2): the sum over
+    nodes of [f(x; Sigma) - u_ij]^2, f the fitted bivariate Gaussian density.
+    For a mixture of densities centred at their own start points, each
+    normalised density u_s / M0_s is compared at its own nodes with
+    f(x - x_s - mu; Sigma_mix), and the sums are averaged over densities."""
+    mu, S = mixture_fit(mom)
+    Si = np.linalg.inv(S)
+    norm = 1.0 / (2.0 * math.pi * math.sqrt(np.linalg.det(S)))
+    X, Y = node_coords(mesh)
+    act = np.repeat(np.repeat(mesh.active[:, :, None, None], mesh.n, 2), mesh.n, 3).astype(bool)
+    total = 0.0
+    mm = np.asarray(mom).reshape(-1, 6)
+    for f, (xs, ys), q in zip(fields, np.asarray(sources).reshape(-1, 2), mm):
+        dx = X - xs - mu[0]
+        dy = Y - ys - mu[1]
+        quad = Si[0, 0] * dx * dx + 2 * Si[0, 1] * dx * dy + Si[1, 1] * dy * dy
+        g = norm * np.exp(-0.5 * quad)
+        r = (g - np.asarray(f).reshape(mesh.field_shape) / q[0])[act]
+        total += float(np.sum(r * r))
+    return total / len(mm)
+
+
 def dense_operator(mesh: Mesh) -> np.ndarray:
     """Matrix of L in the dense node ordering, from unit vectors (tiny meshes)."""
     N = int(np.prod(mesh.field_shape))

@@ -74,6 +74,7 @@ EXPORTS = {
     "dg_moments": (_I, [_P, _DP]),
     "dg_covariance": (_I, [_P, _DP, _DP, _DP]),
     "dg_covariance_batch": (_I, [_P, _DP, _DP, _DP]),
+    "dg_ls_residual": (_I, [_P, _DP]),
     "dg_mixture_covariance": (_I, [_P, _DP, _DP, _I, _DP, _DP]),
     "dg_apply_operator": (_I, [_P]),
     "dg_get_nodes": (_I, [_P, _DP]),
@@ -205,6 +206,12 @@ class DGSolver:
         self._ck(self._L.dg_covariance_batch(self.ctx, _dp(s3), _dp(mu), _dp(mass)),
                  "dg_covariance_batch")
         return s3, mu, mass
+
+    def ls_residual(self) -> np.ndarray:
+        """Least-squares residual of the Gaussian fit, one value per geometry."""
+        out = np.zeros(self.info().n_geometries)
+        self._ck(self._L.dg_ls_residual(self.ctx, _dp(out)), "dg_ls_residual")
+        return out
 
     def get_elements_batch(self, idx) -> np.ndarray:
         """Node values [k, n, n] of elements idx = [(geometry, source, ex, ey), ...]."""

@@ -279,7 +279,7 @@ int set_sources_impl(dg_ctx *ctx, const double *xy, int m) {
     CK(cudaMalloc(&c.d_mom, sizeof(double) * kMomFields * nd), "moment allocation");
     CK(cudaMalloc(&c.d_mom0, sizeof(double) * kMomFields * nd), "moment allocation");
     CK(cudaMalloc(&c.d_part, sizeof(double) * kMomFields * moment_blocks(G) * nd), "partial allocation");
-    CK(cudaMalloc(&c.d_out, sizeof(double) * 5 * G), "output allocation");
+    CK(cudaMalloc(&c.d_out, sizeof(double) * (kCovOut + 1) * G), "output allocation");
   }
   c.src.assign(xy, xy + 2 * nd);
   CK(cudaMemcpyAsync(c.d_src, c.src.data(), sizeof(double) * 2 * nd, cudaMemcpyHostToDevice, c.stream), "source copy");
@@ -570,7 +570,7 @@ int dg_covariance_batch(dg_ctx *ctx, double *sigma3, double *mu2, double *mass) 
   if (r != DG_OK) return r;
   const int G = c.geo.G();
   CK(launch_covariance(c.d_mom, c.d_mom0, c.m, G, c.d_out, c.stream), "covariance");
-  std::vector<double> out((size_t)5 * G);
+  std::vector<double> out((size_t)kCovOut * G);
   CK(cudaMemcpyAsync(out.data(), c.d_out, sizeof(double) * out.size(), cudaMemcpyDeviceToHost, c.stream),
      "covariance copy");
   if (mass)
@@ -578,9 +578,30 @@ int dg_covariance_batch(dg_ctx *ctx, double *sigma3, double *mu2, double *mass) 
                          (size_t)c.m * G, cudaMemcpyDeviceToHost, c.stream), "mass copy");
   CK(cudaStreamSynchronize(c.stream), "covariance");
   for (int g = 0; g < G; ++g) {
-    sigma3[3 * g] = out[5 * g]; sigma3[3 * g + 1] = out[5 * g + 1]; sigma3[3 * g + 2] = out[5 * g + 2];
-    mu2[2 * g] = out[5 * g + 3]; mu2[2 * g + 1] = out[5 * g + 4];
+    const double *o = &out[(size_t)kCovOut * g];
+    sigma3[3 * g] = o[0]; sigma3[3 * g + 1] = o[1]; sigma3[3 * g + 2] = o[2];
+    mu2[2 * g] = o[3]; mu2[2 * g + 1] = o[4];
   }
+  return DG_OK;
+}
+
+int dg_ls_residual(dg_ctx *ctx, double *out) {
+  if (!ctx || !out) return DG_EINVAL;
+  Ctx &c = ctx->c;
+  if (c.m < 1) return fail(ctx, DG_ESTATE, "no sources");
+  CK(cudaSetDevice(c.device), "set device");
+  int r = compute_moments(ctx, c.d_mom);
+  if (r != DG_OK) return r;
+  const int G = c.geo.G();
+  CK(launch_covariance(c.d_mom, c.d_mom0, c.m, G, c.d_out, c.stream), "covariance");
+  double *d_res = nullptr;
+  CK(cudaMalloc(&d_res, sizeof(double) * kMomFields * (size_t)c.m * G), "residual buffer");
+  double *d_ls = c.d_out + (size_t)kCovOut * G;  // G slots after the covariance outputs
+  cudaError_t e = launch_ls_residual(c, state_array(c, 0), c.d_out, c.d_part, d_res, d_ls, c.stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_ls, sizeof(double) * G, cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  cudaFree(d_res);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "least-squares residual");
   return DG_OK;
 }
 
@@ -602,7 +623,7 @@ int dg_mixture_covariance(dg_ctx *ctx, const double *mom, const double *mom0, in
       h[((size_t)m + s) * kMomFields + f] = mom0[s * 6 + f];
     }
   double *d = nullptr;
-  CK(cudaMalloc(&d, sizeof(double) * (h.size() + 8)), "moment buffer");
+  CK(cudaMalloc(&d, sizeof(double) * (h.size() + kCovOut)), "moment buffer");
   double out[5];
   cudaError_t e = cudaMemcpyAsync(d, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, c.stream);
   double *dout = d + h.size();

@@ -18,6 +18,7 @@ constexpr int kTile = 16;           // element ordering: 16 x 16 tiles, row-majo
 constexpr int kMomBlocks = 608;     // fixed grid of the moment reduction (4 x 152 SMs)
 constexpr int kMomFields = 7;       // M0, Mx, My, Mxx, Mxy, Myy, |u| mass
 constexpr int kHaloCap = 4 * 256;   // halo entries a chunk can have (4 faces x kBlock)
+constexpr int kCovOut = 8;          // per geometry: Sigma(t)-Sigma(0) [3], mu [2], Sigma_mix(t) [3]
 
 // Face codes in the neighbour table (>= 0: neighbour element index).
 constexpr int kWall = -1;
@@ -133,7 +134,7 @@ struct Ctx {
   double *d_mom = nullptr;        // [m][7] current moments
   double *d_mom0 = nullptr;       // [m][7] start moments
   double *d_part = nullptr;       // [m][kMomBlocks][7] partial sums
-  double *d_out = nullptr;        // [8] covariance results
+  double *d_out = nullptr;        // [G][kCovOut] covariance results
   size_t part_elems = 0;
 
   // graph of a chunk of steps
@@ -169,6 +170,10 @@ cudaError_t launch_moments(const Ctx &c, const void *u, double *d_part, double *
 cudaError_t launch_covariance(const double *d_mom, const double *d_mom0, int m, int G,
                               double *d_out, cudaStream_t s);
 int moment_blocks(int G);  // first-pass blocks per density of the moment reduction
+// Least-squares residual of the Gaussian fit per geometry (needs d_mom and the
+// covariance output d_cov of the same t); d_res is [G m][7] scratch.
+cudaError_t launch_ls_residual(const Ctx &c, const void *u, const double *d_cov,
+                               double *d_part, double *d_res, double *d_out, cudaStream_t s);
 cudaError_t launch_nodes_to_dense(const Ctx &c, const void *u, double *d_dense,
                                   cudaStream_t s);
 cudaError_t launch_dense_to_nodes(const Ctx &c, const double *d_dense, void *u,

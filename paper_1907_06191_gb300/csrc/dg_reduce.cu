@@ -285,12 +285,74 @@ __global__ void k_covariance(const double *__restrict__ mom, const double *__res
     r[k][3] = mx;
     r[k][4] = my;
   }
-  double *o = out + (size_t)gi * 5;
+  double *o = out + (size_t)gi * kCovOut;
   o[0] = r[0][0] - r[1][0];
   o[1] = r[0][1] - r[1][1];
   o[2] = r[0][2] - r[1][2];
   o[3] = r[0][3];
   o[4] = r[0][4];
+  o[5] = r[0][0];  // Sigma_mix(t) itself, for the Gaussian fit
+  o[6] = r[0][1];
+  o[7] = r[0][2];
+}
+
+// ---- least-squares residual of the Gaussian fit (Sec. 4.2) -----------------
+// Per density (g, s): sum over its nodes of [f(x - x_s - mu) - u / M0]^2 with
+// f the bivariate Gaussian of the mixture fit (mu, Sigma_mix) of geometry g.
+// grid (B, m, G); partial sums in field 0 of part[((g m + s) B + b)][7].
+template <typename T, int P>
+__global__ void __launch_bounds__(256)
+    k_lsres(const int2 *__restrict__ exy, const int2 *__restrict__ grange,
+            const double4 *__restrict__ gpar, long long stride, int m,
+            const double *__restrict__ src, const double *__restrict__ cov,
+            const double *__restrict__ mom, const NodeGeo g, const T *__restrict__ u,
+            double *__restrict__ part) {
+  constexpr int n = P + 1, NP = n * n;
+  const int s = blockIdx.y, gi = blockIdx.z;
+  const int2 rg = grange[gi];
+  const double4 gp = gpar[gi];
+  const double *cv = cov + (size_t)gi * kCovOut;
+  const double mux = cv[3], muy = cv[4], sxx = cv[5], sxy = cv[6], syy = cv[7];
+  const double det = sxx * syy - sxy * sxy;
+  const double ixx = syy / det, ixy = -sxy / det, iyy = sxx / det;
+  const double fnorm = 1.0 / (2.0 * M_PI * sqrt(det));
+  const double inv_m0 = 1.0 / mom[((size_t)gi * m + s) * kMomFields];
+  const double xs = src[2 * ((size_t)gi * m + s)] + mux, ys = src[2 * ((size_t)gi * m + s) + 1] + muy;
+  const double J = 0.5 * gp.z;
+  double acc[kMomFields] = {0, 0, 0, 0, 0, 0, 0};
+  const T *U = u + (size_t)s * stride * NP;
+  for (long long k = (long long)blockIdx.x * 256 + threadIdx.x; k < rg.y;
+       k += (long long)gridDim.x * 256) {
+    const long long a = rg.x + k;
+    const int2 e = exy[a];
+    const T *ue = U + (size_t)a * NP;
+#pragma unroll
+    for (int j = 0; j < n; ++j) {
+      const double dy = gp.y + (e.y + 0.5) * gp.z + J * g.xi[j] - ys;
+#pragma unroll
+      for (int i = 0; i < n; ++i) {
+        const double dx = gp.x + (e.x + 0.5) * gp.z + J * g.xi[i] - xs;
+        const double q = ixx * dx * dx + 2.0 * ixy * dx * dy + iyy * dy * dy;
+        const double d = fnorm * exp(-0.5 * q) - (double)ue[j * n + i] * inv_m0;
+        acc[0] += d * d;
+      }
+    }
+  }
+  block_sum7(acc);
+  if (threadIdx.x == 0) {
+    double *o = part + (((size_t)gi * m + s) * gridDim.x + blockIdx.x) * kMomFields;
+#pragma unroll
+    for (int f = 0; f < kMomFields; ++f) o[f] = acc[f];
+  }
+}
+
+// out[g] = mean over the densities of geometry g of res[(g m + s)][0]
+__global__ void k_ls_mean(const double *__restrict__ res, int m, int G, double *__restrict__ out) {
+  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= G) return;
+  double t = 0.0;
+  for (int s = 0; s < m; ++s) t += res[((size_t)gi * m + s) * kMomFields];
+  out[gi] = t / (double)m;
 }
 
 // ---- node layout conversion ------------------------------------------------
@@ -429,6 +491,26 @@ cudaError_t launch_moments(const Ctx &c, const void *u, double *d_part, double *
 cudaError_t launch_covariance(const double *d_mom, const double *d_mom0, int m, int G,
                               double *d_out, cudaStream_t s) {
   k_covariance<<<(G + 127) / 128, 128, 0, s>>>(d_mom, d_mom0, m, G, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ls_residual(const Ctx &c, const void *u, const double *d_cov,
+                               double *d_part, double *d_res, double *d_out, cudaStream_t s) {
+  const int G = c.geo.G();
+  const int B = moment_blocks(G);
+  const dim3 grid((unsigned)B, (unsigned)c.m, (unsigned)G);
+  const NodeGeo g = node_geo(c);
+  if (c.cfg.precision == DG_FP64) {
+    DG_P_SWITCH(c.cfg.p, (k_lsres<double, PP><<<grid, 256, 0, s>>>(
+                             c.geo.d_exy, c.geo.d_grange, c.geo.d_gpar, c.geo.n_pad, c.m,
+                             c.d_src, d_cov, c.d_mom, g, (const double *)u, d_part)));
+  } else {
+    DG_P_SWITCH(c.cfg.p, (k_lsres<float, PP><<<grid, 256, 0, s>>>(
+                             c.geo.d_exy, c.geo.d_grange, c.geo.d_gpar, c.geo.n_pad, c.m,
+                             c.d_src, d_cov, c.d_mom, g, (const float *)u, d_part)));
+  }
+  k_moments_final<<<(unsigned)(c.m * G), 256, 0, s>>>(d_part, B, d_res);
+  k_ls_mean<<<(G + 127) / 128, 128, 0, s>>>(d_res, c.m, G, d_out);
   return cudaGetLastError();
 }
 

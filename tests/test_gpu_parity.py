@@ -181,6 +181,23 @@ def test_small_cell_sigma_parity(small_ref, prec):
     assert s3[0] > 0 and s3[0] * s3[2] > s3[1] ** 2
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_ls_residual_parity(small_ref, prec):
+    """Least-squares residual of the Gaussian fit (Sec. 4.2) against the
+    oracle on the full small-cell solve."""
+    w, mesh, rho, (nsteps, dt), r = small_ref
+    with _solver(w.p, prec, D=w.D, sigma0=w.sigma0) as s:
+        s.set_geometry_disks(w.disks.cx, w.disks.cy, w.disks.r, w.L, w.n_cell, w.tiles)
+        s.set_sources(w.sources)
+        s.step(nsteps, dt)
+        got = s.ls_residual()
+    ref = O.ls_residual(mesh, r["fields"], w.sources, r["moments"][0])
+    # the residual is a sum of squared small differences: FP32 node errors of
+    # 1e-7 move it by ~1e-4 relative
+    tol = 1e-9 if prec == "f64" else 1e-3
+    assert abs(got[0] / ref - 1) < tol
+
+
 def test_propagate_and_checkpoint_bitwise(small_ref):
     w = small_ref[0]
     kw = dict(D=w.D, sigma0=w.sigma0)

@@ -432,3 +432,39 @@ def test_mask_matches_brute_force():
                     ref[j, i] = 0
     assert np.array_equal(cell, ref)
     assert 0.3 < cell.mean() < 0.9
+
+
+# --------------------------------------------------------------------------
+# Least-squares residual of the Gaussian fit (Sec. 4.2)
+# --------------------------------------------------------------------------
+
+def test_ls_residual_pins():
+    """The residual vanishes when the density is the fitted Gaussian itself,
+    equals eps^2 sum g^2 for a perturbation eps g, and for free diffusion
+    shrinks as the mesh is refined (the DG density approaches the Gaussian)."""
+    n = 24
+    m = O.Mesh(p=3, active=np.ones((n, n), np.uint8), h=0.5, x0=-6.0, y0=-6.0, k0=1.0)
+    X, Y = O.node_coords(m)
+    s = 1.1
+    g = np.exp(-(X ** 2 + Y ** 2) / (2 * s * s)) / (2 * math.pi * s * s)
+    mom = O.moments(m, g, 0.0, 0.0)
+    mu, S = O.mixture_fit(mom)
+    Si = np.linalg.inv(S)
+    f = np.exp(-0.5 * (Si[0, 0] * (X - mu[0]) ** 2 + 2 * Si[0, 1] * (X - mu[0]) * (Y - mu[1])
+                       + Si[1, 1] * (Y - mu[1]) ** 2)) / (2 * math.pi * math.sqrt(np.linalg.det(S)))
+    u = f * mom[0]
+    mom_u = O.moments(m, u, 0.0, 0.0)
+    # the moments of the sampled Gaussian reproduce (mu, S) to quadrature accuracy
+    assert O.ls_residual(m, [f * mom_u[0]], [(0.0, 0.0)], [mom_u]) < 1e-9
+    pert = np.sin(X) * np.cos(0.5 * Y) * 1e-3
+    r0 = O.ls_residual(m, [f * mom_u[0]], [(0.0, 0.0)], [mom_u])
+    r1 = O.ls_residual(m, [(f + pert) * mom_u[0]], [(0.0, 0.0)], [mom_u])
+    assert abs(r1 - r0 - np.sum(pert ** 2)) < 1e-3 * np.sum(pert ** 2) + 2 * math.sqrt(r0 * np.sum(pert ** 2))
+    # refinement: free diffusion from a resolved Gaussian
+    res = []
+    for nel in (12, 24):
+        h = 16.0 / nel
+        mm = O.Mesh(p=2, active=np.ones((nel, nel), np.uint8), h=h, x0=-8.0, y0=-8.0, k0=0.5)
+        r = O.solve(mm, np.array([[0.1, -0.1]]), 1.5, [2.0])
+        res.append(O.ls_residual(mm, r["fields"], [[0.1, -0.1]], r["moments"][0]) / (nel * nel))
+    assert res[1] < res[0]
