@@ -291,6 +291,73 @@ def run_batch(args):
     return 0
 
 
+def run_surrogate(args):
+    """Learned covariance surrogate: DG Sigma of seeded 10 um cells (batched
+    FP32 solves, Delta = 1..5 ms) trains the CNN; held-out cells judge it.
+    value = Sigma evaluations/s of batch-4096 network inference; the DG
+    rate on the same cells and the network's error against DG are reported
+    beside it."""
+    import torch
+    import paper_1907_06191_gb300 as dg
+    from paper_1907_06191_gb300 import _build, surrogate as sgm
+    _build.build()
+    torch.cuda.set_device(0)
+    ntr, nte = args.sg_train, args.sg_test
+    ws_tr = [dginputs.workload_surrogate_member(s) for s in range(ntr)]
+    ws_te = [dginputs.workload_surrogate_member(100000 + s) for s in range(nte)]
+    sig_tr, t_tr = sgm.dg_sigma(ws_tr)
+    sig_te, t_te = sgm.dg_sigma(ws_te)
+    occ, cond, tgt = sgm.build_samples(ws_tr, sig_tr)
+    occ_e, cond_e, tgt_e = sgm.build_samples(ws_te, sig_te)
+    to = lambda a, dt: torch.from_numpy(a).to("cuda:0", dt)
+    net = dg.Surrogate(max_batch=4096, seed=1, device=0)
+    t0 = time.perf_counter()
+    hist = sgm.train(net, to(occ, torch.uint8), to(cond, torch.float32), to(tgt, torch.float32),
+                     epochs=args.sg_epochs)
+    t_train = time.perf_counter() - t0
+    # held-out error against the DG solve (the judge)
+    pe = torch.zeros((occ_e.shape[0], 3), device="cuda:0")
+    oe, ce = to(occ_e, torch.uint8), to(cond_e, torch.float32)
+    for b0 in range(0, oe.shape[0], 4096):
+        net.predict(oe[b0:b0 + 4096], ce[b0:b0 + 4096], pe[b0:b0 + 4096])
+    pred = pe.cpu().numpy()
+    rel = np.linalg.norm(pred - tgt_e, axis=1) / np.linalg.norm(tgt_e, axis=1)
+    # batch-4096 inference throughput (inputs resident)
+    B = 4096
+    reps = (B + oe.shape[0] - 1) // oe.shape[0]
+    ob = oe.repeat(reps, 1, 1)[:B].contiguous()
+    cb = ce.repeat(reps, 1)[:B].contiguous()
+    out = torch.zeros((B, 3), device="cuda:0")
+    for _ in range(args.warmup):
+        net.predict(ob, cb, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        net.predict(ob, cb, out)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    value = B / (ms * 1e-3)
+    dg_rate = (nte * len(ws_te[0].deltas)) / t_te
+    line = {"metric": "Sigma evaluations/s", "value": value, "unit": "Sigma/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic",
+            "config": {"workload": "surrogate_cell10_p2", "batch": B, "train_geometries": ntr,
+                       "test_geometries": nte, "deltas_ms": ws_tr[0].deltas,
+                       "params": net.param_count(), "epochs": args.sg_epochs,
+                       "l2": "batch inputs 64 MB, resident"},
+            "dg_sigma_per_s": dg_rate, "speedup_vs_dg": value / dg_rate,
+            "heldout_rel_err": {"mean": float(rel.mean()), "p95": float(np.percentile(rel, 95)),
+                                "max": float(rel.max())},
+            "train_loss_first_last": [hist[0], hist[-1]], "train_seconds": t_train,
+            "dg_seconds_train_set": t_tr}
+    net.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -304,13 +371,18 @@ def main():
                     help="start points per GPU (64 = the workload; fewer for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
-    ap.add_argument("--workload", default="cell40", choices=["cell40", "batch", "p5"])
+    ap.add_argument("--workload", default="cell40", choices=["cell40", "batch", "p5", "surrogate"])
+    ap.add_argument("--sg-train", type=int, default=512)
+    ap.add_argument("--sg-test", type=int, default=128)
+    ap.add_argument("--sg-epochs", type=int, default=60)
     ap.add_argument("--batch-geometries", type=int, default=512)
     ap.add_argument("--batch-gb", type=float, default=60.0)
     args = ap.parse_args()
     world, rank, local = _dist()
     if args.workload == "batch" and args.impl == "ours":
         return run_batch(args) if rank == 0 else 0
+    if args.workload == "surrogate" and args.impl == "ours":
+        return run_surrogate(args) if rank == 0 else 0
 
     if args.impl == "reference":
         return run_reference(args, world, rank)

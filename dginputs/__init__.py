@@ -24,7 +24,7 @@ import numpy as np
 __all__ = [
     "Disks", "gamma_disks", "sample_sources", "window_tiles", "source_box",
     "Workload", "workload_small", "workload_cell40", "workload_batch_member",
-    "workload_p5", "free_diffusion_paper",
+    "workload_p5", "free_diffusion_paper", "workload_surrogate_member",
 ]
 
 
@@ -268,6 +268,19 @@ def workload_batch_member(seed: int, m: int = 16) -> Workload:
     h = 40.0 / 256
     return _workload(f"batch{seed}", seed, p, n_cell * h, n_cell, 2.0, 0.2,
                      [20.0], shape, 0.5, m, packing=packing)
+
+
+def workload_surrogate_member(seed: int, m: int = 16) -> Workload:
+    """One geometry of the surrogate's training set: 10 um periodic cell of
+    32 x 32 elements (h = 0.3125 um), p = 2, Gamma(shape, 0.4 um) disks with
+    shape uniform in [1.5, 3.0] at a packing uniform in [0.40, 0.75], 16
+    start points, Delta in {1, 2, 3, 4, 5} ms, D = 2 um^2/ms."""
+    rng = np.random.default_rng(seed + 32452843)
+    packing = float(rng.uniform(0.40, 0.75))
+    shape = float(rng.uniform(1.5, 3.0))
+    return _workload(f"surrogate{seed}", seed, 2, 10.0, 32, 2.0, 0.2,
+                     [1.0, 2.0, 3.0, 4.0, 5.0], shape, 0.4, m, packing=packing,
+                     min_gap=0.05)
 
 
 def workload_p5(seed: int = 0, m: int = 32) -> Workload:

@@ -159,6 +159,14 @@ int dg_set_geometry_batch(dg_ctx *ctx, int G, const int *ndisks, const double *c
                           const double *cy, const double *r, const double *L,
                           const int *n_cell, const int *tiles);
 
+/* Occupancy raster of disks in a periodic cell (the substrate of Sec. 2.2):
+ * out[npix][npix] bytes, 1 where the pixel centre ((i + 1/2) L/npix,
+ * (j + 1/2) L/npix) lies strictly inside a disk (the complement of the mesh
+ * rule of dg_set_geometry_disks), computed on the calling thread's current
+ * device.  Errors: DG_EINVAL, DG_ENOMEM, DG_ECUDA. */
+int dg_rasterize_disks(const double *cx, const double *cy, const double *r, int ndisks,
+                       double L, int npix, uint8_t *out);
+
 /* Copy the element mask as built, [ny][nx] bytes (1 = in the mesh); the
  * first geometry of a batch. */
 int dg_get_mask(dg_ctx *ctx, uint8_t *active);

@@ -87,6 +87,17 @@ EXPORTS = {
     "dg_state_bytes": (_I, [_P, _I, ctypes.POINTER(_SZ)]),
     "dg_bind_state": (_I, [_P, _P, _SZ]),
     "dg_moments_dense_static": (_I, [_P, _I, _I, _I, _I, _I, _D, _D, _D, _P, _P, _P]),
+    "dg_rasterize_disks": (_I, [_DP, _DP, _DP, _I, _D, _I, _P]),
+    # learned surrogate (include/dgsurrogate.h)
+    "sg_create": (_I, [_I, ctypes.c_ulonglong, _I, ctypes.POINTER(_P)]),
+    "sg_destroy": (None, [_P]),
+    "sg_last_error": (ctypes.c_char_p, [_P]),
+    "sg_param_count": (_I, [_P, ctypes.POINTER(_SZ)]),
+    "sg_get_params": (_I, [_P, _P]),
+    "sg_set_params": (_I, [_P, _P]),
+    "sg_predict": (_I, [_P, _P, _P, _I, _P]),
+    "sg_gradients": (_I, [_P, _P, _P, _P, _I, _P, _P]),
+    "sg_train_step": (_I, [_P, _P, _P, _P, _I, ctypes.c_float, _P]),
 }
 
 _lib = None
@@ -329,3 +340,80 @@ class DGSolver:
     def set_stream(self, stream_ptr: int | None):
         self._ck(self._L.dg_set_stream(self.ctx, ctypes.c_void_p(stream_ptr) if stream_ptr else None),
                  "dg_set_stream")
+
+
+def rasterize_disks(cx, cy, r, L: float, npix: int = 128) -> np.ndarray:
+    """Occupancy raster [npix, npix] (1 inside a disk) of a periodic cell."""
+    cx, cy, r = _f64(cx), _f64(cy), _f64(r)
+    out = np.zeros((npix, npix), dtype=np.uint8)
+    rc = lib().dg_rasterize_disks(_dp(cx), _dp(cy), _dp(r), int(r.size), float(L), int(npix),
+                                  out.ctypes.data)
+    if rc != DG_OK:
+        raise DgError(rc, f"dg_rasterize_disks: {lib().dg_strerror(rc).decode()}")
+    return out
+
+
+class Surrogate:
+    """The learned covariance surrogate (include/dgsurrogate.h).  Batches are
+    CUDA tensors: occ uint8 [B, 128, 128], cond float32 [B, 2], target
+    float32 [B, 3]."""
+
+    def __init__(self, max_batch: int = 4096, seed: int = 1, device: int = 0):
+        self._L = lib()
+        h = _P()
+        rc = self._L.sg_create(int(max_batch), int(seed), int(device), ctypes.byref(h))
+        if rc != DG_OK:
+            raise DgError(rc, "sg_create")
+        self.net = h
+        self.max_batch = max_batch
+
+    def _ck(self, rc, what):
+        if rc != DG_OK:
+            raise DgError(rc, f"{what}: {self._L.sg_last_error(self.net).decode()}")
+
+    def close(self):
+        if getattr(self, "net", None):
+            self._L.sg_destroy(self.net)
+            self.net = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def param_count(self) -> int:
+        n = ctypes.c_size_t()
+        self._ck(self._L.sg_param_count(self.net, ctypes.byref(n)), "sg_param_count")
+        return n.value
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.param_count(), dtype=np.float32)
+        self._ck(self._L.sg_get_params(self.net, out.ctypes.data), "sg_get_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._ck(self._L.sg_set_params(self.net, p.ctypes.data), "sg_set_params")
+
+    @staticmethod
+    def _ptr(t):
+        return ctypes.c_void_p(t.data_ptr())
+
+    def predict(self, occ, cond, out):
+        B = occ.shape[0]
+        self._ck(self._L.sg_predict(self.net, self._ptr(occ), self._ptr(cond), B, self._ptr(out)),
+                 "sg_predict")
+
+    def gradients(self, occ, cond, target):
+        loss = np.zeros(1, dtype=np.float32)
+        g = np.zeros(self.param_count(), dtype=np.float32)
+        self._ck(self._L.sg_gradients(self.net, self._ptr(occ), self._ptr(cond), self._ptr(target),
+                                      occ.shape[0], loss.ctypes.data, g.ctypes.data), "sg_gradients")
+        return float(loss[0]), g
+
+    def train_step(self, occ, cond, target, lr: float) -> float:
+        loss = np.zeros(1, dtype=np.float32)
+        self._ck(self._L.sg_train_step(self.net, self._ptr(occ), self._ptr(cond), self._ptr(target),
+                                       occ.shape[0], float(lr), loss.ctypes.data), "sg_train_step")
+        return float(loss[0])

@@ -454,6 +454,35 @@ int dg_set_geometry_batch(dg_ctx *ctx, int G, const int *ndisks, const double *c
   }
 }
 
+int dg_rasterize_disks(const double *cx, const double *cy, const double *r, int ndisks,
+                       double L, int npix, uint8_t *out) {
+  if (!out || ndisks < 0 || (ndisks > 0 && (!cx || !cy || !r)) || !(L > 0.0) || npix < 1 ||
+      npix > 16384)
+    return DG_EINVAL;
+  const int nd = ndisks > 0 ? ndisks : 1;
+  double *d = nullptr;
+  uint8_t *m = nullptr;
+  if (cudaMalloc(&d, sizeof(double) * 3 * nd) != cudaSuccess) return DG_ENOMEM;
+  if (cudaMalloc(&m, (size_t)npix * npix) != cudaSuccess) {
+    cudaFree(d);
+    return DG_ENOMEM;
+  }
+  cudaError_t e = cudaSuccess;
+  if (ndisks > 0) {
+    e = cudaMemcpy(d, cx, 8 * (size_t)ndisks, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d + nd, cy, 8 * (size_t)ndisks, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d + 2 * nd, r, 8 * (size_t)ndisks, cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = build_mask_disks(d, d + nd, d + 2 * nd, ndisks, L, npix, 1, m, 0);
+  std::vector<uint8_t> h((size_t)npix * npix);
+  if (e == cudaSuccess) e = cudaMemcpy(h.data(), m, h.size(), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  cudaFree(m);
+  if (e != cudaSuccess) return DG_ECUDA;
+  for (size_t k = 0; k < h.size(); ++k) out[k] = h[k] ? 0 : 1;
+  return DG_OK;
+}
+
 int dg_get_mask(dg_ctx *ctx, uint8_t *active) {
   if (!ctx || !active) return DG_EINVAL;
   Ctx &c = ctx->c;

@@ -157,6 +157,9 @@ cudaError_t launch_stage_f32(int p, const float *u, const float *u0, float *out,
                              const Geometry &geo, long long stride, int m,
                              const Gll &g, const StageCoef<float> &c, cudaStream_t s);
 
+cudaError_t build_mask_disks(const double *d_cx, const double *d_cy, const double *d_r,
+                             int nd, double L, int n_cell, int tiles, uint8_t *d_mask,
+                             cudaStream_t s);
 // Geometry construction: masks, compaction in tile order, neighbour and halo
 // tables for every part; fills geo (allocates).  Returns a DG_* code.
 int build_geometry(Geometry &geo, const std::vector<PartSpec> &parts, int periodic,

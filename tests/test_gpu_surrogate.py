@@ -1,0 +1,79 @@
+"""Surrogate kernels (forward, backward, Adam) against the FP64 numpy
+reference with the same BF16 rounding points; the raster against the
+oracle's mask."""
+import numpy as np
+import pytest
+
+import dginputs
+import oracle as O
+from oracle import surrogate as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1907_06191_gb300 as dg  # noqa: E402
+
+
+def _batch(n, seed):
+    occ, cond = [], []
+    for k in range(n):
+        w = dginputs.workload_surrogate_member(seed + k)
+        occ.append(dg.rasterize_disks(w.disks.cx, w.disks.cy, w.disks.r, w.L, 128))
+        cond.append([np.log(w.D * (1.0 + k)), w.D])
+    return np.stack(occ), np.array(cond, dtype=np.float32)
+
+
+def test_raster_is_complement_of_oracle_mask():
+    w = dginputs.workload_surrogate_member(3)
+    occ = dg.rasterize_disks(w.disks.cx, w.disks.cy, w.disks.r, w.L, 128)
+    ref = 1 - O.mask_disks(w.L, 128, w.disks.cx, w.disks.cy, w.disks.r)
+    assert np.array_equal(occ, ref)
+
+
+def test_gradients_and_prediction_match_reference():
+    net = dg.Surrogate(max_batch=8, seed=3, device=0)
+    occ, cond = _batch(4, 100)
+    rng = np.random.default_rng(1)
+    tgt = rng.uniform(0.3, 1.0, size=(4, 3)).astype(np.float32)
+    to = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0", dt)
+    occ_t, cond_t, tgt_t = to(occ, torch.uint8), to(cond, torch.float32), to(tgt, torch.float32)
+    params = net.get_params()
+    loss, grad = net.gradients(occ_t, cond_t, tgt_t)
+    out = torch.zeros((4, 3), dtype=torch.float32, device="cuda:0")
+    net.predict(occ_t, cond_t, out)
+    rloss, rgrad, ry = S.loss_and_grad(params.astype(np.float64), occ, cond, tgt)
+    assert np.abs(out.cpu().numpy() - ry).max() <= 1e-2 * np.abs(ry).max()
+    assert abs(loss / rloss - 1) < 1e-2
+    off = 0
+    for name, shp in S.layout():
+        size = int(np.prod(shp))
+        g, r = grad[off:off + size], rgrad[off:off + size]
+        assert np.linalg.norm(g - r) <= 3e-2 * np.linalg.norm(r) + 1e-9, name
+        off += size
+    net.close()
+
+
+def test_training_reduces_loss():
+    net = dg.Surrogate(max_batch=64, seed=5, device=0)
+    occ, cond = _batch(64, 200)
+    frac = occ.reshape(64, -1).mean(1)
+    tgt = np.stack([1 - 0.6 * frac, 0.02 * np.sin(cond[:, 0]), 1 - 0.5 * frac], 1).astype(np.float32)
+    to = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0", dt)
+    occ_t, cond_t, tgt_t = to(occ, torch.uint8), to(cond, torch.float32), to(tgt, torch.float32)
+    first = net.train_step(occ_t, cond_t, tgt_t, 2e-3)
+    for _ in range(150):
+        last = net.train_step(occ_t, cond_t, tgt_t, 2e-3)
+    assert last < first / 10
+    p = net.get_params()
+    net2 = dg.Surrogate(max_batch=64, seed=9, device=0)
+    net2.set_params(p)
+    a = torch.zeros((64, 3), device="cuda:0")
+    b = torch.zeros((64, 3), device="cuda:0")
+    net.predict(occ_t, cond_t, a)
+    net2.predict(occ_t, cond_t, b)
+    assert torch.equal(a, b)
+    net.close()
+    net2.close()
