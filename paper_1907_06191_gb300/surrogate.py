@@ -59,10 +59,31 @@ def build_samples(workloads, sigma):
             np.stack(tgt).astype(np.float32))
 
 
-def train(net: Surrogate, occ, cond, tgt, epochs: int = 60, batch: int = 128,
-          lr: float = 2e-3, seed: int = 0):
-    """Adam on the mean squared error; returns the loss history per epoch.
-    occ/cond/tgt are CUDA tensors."""
+def augment(occ, tgt, k: int, dy: int, dx: int):
+    """Exact symmetries of a periodic cell applied to a batch: a periodic
+    shift (Sigma unchanged), then for bit 0 of k a flip in x and for bit 1 a
+    flip in y (each negates Sxy), for bit 2 a transposition (swaps Sxx and
+    Syy).  occ [B, y, x], tgt [B, 3] = (Sxx, Sxy, Syy)."""
+    import torch
+    o = torch.roll(occ, shifts=(dy, dx), dims=(1, 2))
+    t = tgt.clone()
+    if k & 1:
+        o = torch.flip(o, dims=[2])
+        t[:, 1] = -t[:, 1]
+    if k & 2:
+        o = torch.flip(o, dims=[1])
+        t[:, 1] = -t[:, 1]
+    if k & 4:
+        o = o.transpose(1, 2)
+        t = t[:, [2, 1, 0]]
+    return o.contiguous(), t.contiguous()
+
+
+def train(net: Surrogate, occ, cond, tgt, epochs: int = 100, batch: int = 128,
+          lr: float = 2e-3, seed: int = 0, augmented: bool = True):
+    """Adam on the mean squared error, each batch under a random symmetry of
+    the periodic cell; returns the loss history per epoch.  occ/cond/tgt are
+    CUDA tensors."""
     import torch
     n = occ.shape[0]
     g = torch.Generator(device="cpu").manual_seed(seed)
@@ -73,8 +94,11 @@ def train(net: Surrogate, occ, cond, tgt, epochs: int = 60, batch: int = 128,
         tot, cnt = 0.0, 0
         for b0 in range(0, n - batch + 1, batch):
             idx = perm[b0:b0 + batch]
-            loss = net.train_step(occ[idx].contiguous(), cond[idx].contiguous(),
-                                  tgt[idx].contiguous(), rate)
+            o, t = occ[idx], tgt[idx]
+            if augmented:
+                k, dy, dx = (int(v) for v in torch.randint(0, RES, (3,), generator=g))
+                o, t = augment(o, t, k % 8, dy, dx)
+            loss = net.train_step(o.contiguous(), cond[idx].contiguous(), t.contiguous(), rate)
             tot += loss
             cnt += 1
         hist.append(tot / max(cnt, 1))

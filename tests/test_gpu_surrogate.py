@@ -77,3 +77,26 @@ def test_training_reduces_loss():
     assert torch.equal(a, b)
     net.close()
     net2.close()
+
+
+def test_augmentation_is_an_exact_symmetry_of_the_dg_sigma():
+    """A flipped / transposed / shifted cell solved by DG gives the Sigma that
+    augment() predicts from the original (up to the start-point sampling,
+    which is carried along by transforming the start points too)."""
+    from paper_1907_06191_gb300 import surrogate as sgm
+    w = dginputs.workload_surrogate_member(7, m=8)
+    w.deltas = [1.0]
+    L = w.L
+    # transpose: swap x and y of disks and start points
+    t = dginputs.Workload(w.name, w.p, L, w.n_cell, w.tiles, w.D, w.sigma0, w.deltas,
+                          dginputs.Disks(w.disks.cy.copy(), w.disks.cx.copy(), w.disks.r.copy(), L,
+                                         w.disks.target_packing, w.disks.packing),
+                          w.sources[:, ::-1].copy(), w.meta)
+    s0, _ = sgm.dg_sigma([w])
+    s1, _ = sgm.dg_sigma([t])
+    occ0 = torch.from_numpy(dg.rasterize_disks(w.disks.cx, w.disks.cy, w.disks.r, L)[None]).cuda()
+    occ1 = torch.from_numpy(dg.rasterize_disks(t.disks.cx, t.disks.cy, t.disks.r, L)[None]).cuda()
+    tg = torch.from_numpy(s0[:, 0].astype(np.float32)).cuda()
+    o, tt = sgm.augment(occ0, tg, 4, 0, 0)
+    assert torch.equal(o, occ1)
+    assert np.allclose(tt.cpu().numpy(), s1[:, 0], rtol=1e-5, atol=1e-7)
