@@ -400,6 +400,12 @@ def main():
                     help="start points per GPU (64 = the workload; fewer for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--check-delta", type=float, default=0.0,
+                    help="compare FP32 with the FP64 GPU path over a solve to this Delta (ms) "
+                         "on 4 densities instead of over R steps")
+    ap.add_argument("--full-delta", type=float, default=0.0,
+                    help="after the timed steps, solve every density to each of the workload's "
+                         "diffusion times up to this Delta (ms) and report Sigma and the time")
     ap.add_argument("--workload", default="cell40", choices=["cell40", "batch", "p5", "surrogate"])
     ap.add_argument("--sg-train", type=int, default=512)
     ap.add_argument("--sg-test", type=int, default=128)
@@ -531,7 +537,27 @@ def main():
 
     # agreement with the FP64 GPU path on the same steps
     check = None
-    if not args.no_check and args.precision == "f32" and rank == 0:
+    if args.check_delta and args.precision == "f32" and rank == 0:
+        # a longer solve: the first 4 densities to Delta in both precisions
+        nd = 4
+        res = {}
+        for pr in (dg.DG_FP32, dg.DG_FP64):
+            with dg.DGSolver(p=w.p, precision=pr, D=w.D, sigma0=w.sigma0, device=dev) as c2:
+                c2.set_geometry_disks(w.disks.cx, w.disks.cy, w.disks.r, w.L, w.n_cell, w.tiles)
+                c2.set_sources(w.sources[:nd])
+                t0 = time.perf_counter()
+                c2.propagate_to(args.check_delta)
+                secs = time.perf_counter() - t0
+                sg3, mu2, mass = c2.covariance()
+                res[pr] = (sg3, mass, secs, c2.info().steps)
+        s32, m32, t32, n32 = res[dg.DG_FP32]
+        s64, m64, t64, n64 = res[dg.DG_FP64]
+        check = {"delta_ms": args.check_delta, "densities": nd, "rk_steps": n32,
+                 "sigma_fp64": s64.tolist(), "sigma_fp32": s32.tolist(),
+                 "sigma_rel_err": float(np.abs(s32 - s64).max() / np.abs(s64).max()),
+                 "mass_rel_err": float(np.abs(m32 - m64).max() / np.abs(m64).max()),
+                 "seconds_fp32": t32, "seconds_fp64": t64}
+    elif not args.no_check and args.precision == "f32" and rank == 0:
         s.set_sources(w.sources)
         s.step(R, dt)
         sig32 = s.covariance()[0]
@@ -547,6 +573,23 @@ def main():
         check = {"steps": R, "sigma_rel_err": float(np.abs(sig32 - sig64).max() / np.abs(sig64).max()),
                  "second_moment_rel_err": float(np.abs(m2_32 - m2_64).max() / np.abs(m2_64).max())}
 
+    full = None
+    if args.full_delta > 0 and rank == 0:
+        s.set_sources(w.sources)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        snaps = []
+        for d in [d for d in w.deltas if d <= args.full_delta]:
+            s.propagate_to(d)
+            sg3, mu2, mass = s.covariance()
+            snaps.append({"delta_ms": d, "elapsed_s": time.perf_counter() - t0,
+                          "rk_steps": s.info().steps, "sigma": sg3.tolist(), "mu": mu2.tolist(),
+                          "mass_min": float(mass.min()), "mass_max": float(mass.max()),
+                          "free_value": 2 * w.D * d})
+        el = time.perf_counter() - t0
+        full = {"snapshots": snaps, "seconds": el, "densities": m,
+                "sigma_solves_per_s_measured": m / el,
+                "note": "one propagation through every snapshot; solves = densities carried to the last Delta"}
     s.close()
     if rank != 0:
         return 0
@@ -570,6 +613,8 @@ def main():
         "clocks": clk.summary(),
         "fp64_check": check,
     }
+    if full is not None:
+        line["full_solve"] = full
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline_sample(w)
     print(json.dumps(line), flush=True)
