@@ -403,6 +403,9 @@ def main():
     ap.add_argument("--check-delta", type=float, default=0.0,
                     help="compare FP32 with the FP64 GPU path over a solve to this Delta (ms) "
                          "on 4 densities instead of over R steps")
+    ap.add_argument("--growing-window", type=float, default=0.0,
+                    help="with --full-delta: also solve on the growing window of this radius "
+                         "factor and report its time and Sigma against the fixed window")
     ap.add_argument("--full-delta", type=float, default=0.0,
                     help="after the timed steps, solve every density to each of the workload's "
                          "diffusion times up to this Delta (ms) and report Sigma and the time")
@@ -575,21 +578,35 @@ def main():
 
     full = None
     if args.full_delta > 0 and rank == 0:
-        s.set_sources(w.sources)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        snaps = []
-        for d in [d for d in w.deltas if d <= args.full_delta]:
-            s.propagate_to(d)
-            sg3, mu2, mass = s.covariance()
-            snaps.append({"delta_ms": d, "elapsed_s": time.perf_counter() - t0,
-                          "rk_steps": s.info().steps, "sigma": sg3.tolist(), "mu": mu2.tolist(),
-                          "mass_min": float(mass.min()), "mass_max": float(mass.max()),
-                          "free_value": 2 * w.D * d})
-        el = time.perf_counter() - t0
-        full = {"snapshots": snaps, "seconds": el, "densities": m,
-                "sigma_solves_per_s_measured": m / el,
-                "note": "one propagation through every snapshot; solves = densities carried to the last Delta"}
+        def full_solve(r_factor):
+            s.set_growing_window(r_factor)
+            s.set_sources(w.sources)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            snaps = []
+            for d in [d for d in w.deltas if d <= args.full_delta]:
+                s.propagate_to(d)
+                sg3, mu2, mass = s.covariance()
+                snaps.append({"delta_ms": d, "elapsed_s": time.perf_counter() - t0,
+                              "rk_steps": s.info().steps, "sigma": sg3.tolist(), "mu": mu2.tolist(),
+                              "mass_min": float(mass.min()), "mass_max": float(mass.max()),
+                              "free_value": 2 * w.D * d})
+            el = time.perf_counter() - t0
+            s.set_growing_window(0.0)
+            return {"snapshots": snaps, "seconds": el, "densities": m,
+                    "sigma_solves_per_s_measured": m / el,
+                    "note": "one propagation through every snapshot; solves = densities "
+                            "carried to the last Delta"}
+        full = full_solve(0.0)
+        if args.growing_window > 0:
+            g = full_solve(args.growing_window)
+            g["r_factor"] = args.growing_window
+            g["sigma_rel_diff_vs_fixed"] = [
+                float(np.abs(np.array(a["sigma"]) - np.array(b["sigma"])).max()
+                      / np.abs(np.array(b["sigma"])).max())
+                for a, b in zip(g["snapshots"], full["snapshots"])]
+            g["speedup_vs_fixed"] = full["seconds"] / g["seconds"]
+            full["growing_window"] = g
     s.close()
     if rank != 0:
         return 0

@@ -167,6 +167,16 @@ int dg_set_geometry_batch(dg_ctx *ctx, int G, const int *ndisks, const double *c
 int dg_rasterize_disks(const double *cx, const double *cy, const double *r, int ndisks,
                        double L, int npix, uint8_t *out);
 
+/* The nodal tables the stage kernels use for order p (Eq. 8: Lagrange basis
+ * on the p+1 Gauss-Lobatto-Legendre nodes of [-1, 1], quadrature at the
+ * nodes, Sec. 3.2).  Host only, no device call.  xi[p+1], w[p+1],
+ * D[(p+1)^2] with D[a*(p+1) + i] = l_i'(xi_a), D2[(p+1)^2] = D D.  With
+ * precision DG_FP32 the matrices are the FP32 values the FP32 kernels use,
+ * widened to double: within a few FP32 ulps of the FP64 ones, every row
+ * summing to exactly zero.  Any output pointer may be NULL.  Errors:
+ * DG_EINVAL (p outside 1..5 or an unknown precision). */
+int dg_basis_tables(int p, int precision, double *xi, double *w, double *D, double *D2);
+
 /* Copy the element mask as built, [ny][nx] bytes (1 = in the mesh); the
  * first geometry of a batch. */
 int dg_get_mask(dg_ctx *ctx, uint8_t *active);
@@ -195,6 +205,23 @@ int dg_query_dt(dg_ctx *ctx, double *dt_max, double *rho);
  * No host synchronisation.  Errors: DG_EINVAL (nsteps < 0, dt <= 0),
  * DG_ESTATE (no sources). */
 int dg_step(dg_ctx *ctx, int nsteps, double dt);
+
+/* Growing window (the Sec. 4.1 window sized to the density instead of to
+ * the largest Delta).  r_factor > 0 turns it on, 0 off (the default).  While
+ * on, dg_step and dg_propagate_to advance steps in groups of at most 64; in
+ * each group an element advances only if the squared distance from its
+ * centre (x0 + (ex + 1/2) h, y0 + (ey + 1/2) h) to the box spanned by its
+ * geometry's start points is <= r_factor^2 (sigma0^2 + 2 D t_end), t_end the
+ * time at the group's end (FP64, each operation rounded on its own).  Other
+ * elements keep their values and act as frozen neighbours; chunks of the
+ * element order with no advancing element are not launched.  For a
+ * Gaussian tail the density beyond the radius is of relative size
+ * exp(-r_factor^2 / 2) and Sigma moves by about 70 times that (r_factor = 7:
+ * 2e-9); odd p with the central fluxes and start densities narrower than
+ * about 2h have heavier tails (p = 3, sigma0 = 1.2 h: 4e-6 at r_factor = 7,
+ * 1e-8 at 10).  Once the radius covers every mesh element, stepping is the
+ * fixed-window path.  Errors: DG_EINVAL (negative or non-finite r_factor). */
+int dg_set_growing_window(dg_ctx *ctx, double r_factor);
 
 /* Advance from the current t to Delta in N = ceil((Delta - t)/dt_max) equal
  * steps, then check the moments: DG_ENONFINITE on NaN/Inf, DG_EUNSTABLE when

@@ -63,6 +63,8 @@ def _load():
         lib.orc_gll.argtypes = [ctypes.c_int, dp, dp, dp]
         lib.orc_apply_L.argtypes = [ctypes.c_void_p, dp, dp]
         lib.orc_rk3.argtypes = [ctypes.c_void_p, dp, ctypes.c_int, ctypes.c_double]
+        lib.orc_rk3_adv.argtypes = [ctypes.c_void_p, dp, ctypes.c_int, ctypes.c_double,
+                                    ctypes.c_void_p]
         lib.orc_init_gaussian.argtypes = [ctypes.c_void_p, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, dp]
         lib.orc_moments.argtypes = [ctypes.c_void_p, dp, ctypes.c_double,
@@ -151,12 +153,53 @@ def apply_L(mesh: Mesh, u: np.ndarray) -> np.ndarray:
     return out
 
 
-def rk3(mesh: Mesh, u: np.ndarray, nsteps: int, dt: float) -> np.ndarray:
-    """nsteps SSP-RK3 steps of size dt; returns a new array."""
+def rk3(mesh: Mesh, u: np.ndarray, nsteps: int, dt: float, advance=None) -> np.ndarray:
+    """nsteps SSP-RK3 steps of size dt; returns a new array.  advance: None
+    (every element) or a [ny, nx] mask of the elements that advance; the
+    others keep their values."""
     v = np.array(u, dtype=np.float64, order="C").reshape(mesh.field_shape)
     cm = mesh.c()
-    if _load().orc_rk3(ctypes.byref(cm), _dp(v), int(nsteps), float(dt)) != 0:
+    if advance is None:
+        rc = _load().orc_rk3(ctypes.byref(cm), _dp(v), int(nsteps), float(dt))
+    else:
+        adv = np.ascontiguousarray(advance, dtype=np.uint8)
+        assert adv.shape == (mesh.ny, mesh.nx)
+        rc = _load().orc_rk3_adv(ctypes.byref(cm), _dp(v), int(nsteps), float(dt),
+                                 adv.ctypes.data)
+    if rc != 0:
         raise RuntimeError("orc_rk3 failed")
+    return v
+
+
+def window_d2(mesh: Mesh, box) -> np.ndarray:
+    """Squared distance [ny, nx] from each element centre to the box
+    (x_lo, x_hi, y_lo, y_hi) spanned by the start points, in FP64 with the
+    operations in this order (the library's growing window takes the same
+    decisions from the same values)."""
+    x = mesh.x0 + (np.arange(mesh.nx) + 0.5) * mesh.h
+    y = mesh.y0 + (np.arange(mesh.ny) + 0.5) * mesh.h
+    dx = np.maximum(np.maximum(box[0] - x, x - box[1]), 0.0)
+    dy = np.maximum(np.maximum(box[2] - y, y - box[3]), 0.0)
+    return (dx * dx)[None, :] + (dy * dy)[:, None]
+
+
+def rk3_growing(mesh: Mesh, u: np.ndarray, nsteps: int, dt: float, box, r_factor: float,
+                sigma0: float, t0: float = 0.0, group: int = 64) -> np.ndarray:
+    """RK3 on a window that grows with the density (Sec. 4.1 window of
+    radius R = r_factor sqrt(sigma0^2 + 2 k0 t) around the start-point box).
+    Steps go in groups of ``group``; in each group an element advances when
+    its centre lies within R of the box at the group's end time, the rest
+    keep their values."""
+    d2 = window_d2(mesh, box)
+    v = np.array(u, dtype=np.float64)
+    done = 0
+    while done < nsteps:
+        k = min(group, nsteps - done)
+        t_end = t0 + (done + k) * dt
+        r2 = r_factor * r_factor * (sigma0 * sigma0 + 2.0 * mesh.k0 * t_end)
+        adv = (mesh.active != 0) & (d2 <= r2)
+        v = rk3(mesh, v, k, dt, advance=adv)
+        done += k
     return v
 
 

@@ -331,33 +331,45 @@ int orc_apply_L(const orc_mesh *M, const double *u, double *Lu) {
 
 /* nsteps steps of SSP-RK3 (Shu-Osher form) with step dt, in place:
  *   u1 = u + dt L u;  u2 = 3/4 u + 1/4 (u1 + dt L u1);
- *   u <- 1/3 u + 2/3 (u2 + dt L u2). */
-int orc_rk3(const orc_mesh *M, double *u, int nsteps, double dt) {
+ *   u <- 1/3 u + 2/3 (u2 + dt L u2).
+ * adv (NULL = every element) marks the elements that advance; the others
+ * keep their values through all three stages (growing window: elements
+ * beyond the window's current radius are held fixed and act as frozen
+ * neighbours of the advancing ones). */
+int orc_rk3_adv(const orc_mesh *M, double *u, int nsteps, double dt,
+                const unsigned char *adv) {
   orc_tables T;
   if (tables(M, &T)) return -1;
   const size_t N = field_size(M);
+  const long nn = (long)(M->p + 1) * (M->p + 1);
   double *buf = (double *)malloc(5 * N * sizeof(double));
   if (!buf) return -1;
   double *u1 = buf, *u2 = buf + N, *L = buf + 2 * N, *qx = buf + 3 * N,
          *qy = buf + 4 * N;
+#define ORC_ADV(t) (!adv || adv[(t) / nn])
   for (int s = 0; s < nsteps; ++s) {
     grad_pass(M, T.xi, T.w, T.D, u, qx, qy);
     div_pass(M, T.w, T.D, u, qx, qy, L);
 #pragma omp parallel for schedule(static)
-    for (long t = 0; t < (long)N; ++t) u1[t] = u[t] + dt * L[t];
+    for (long t = 0; t < (long)N; ++t) u1[t] = ORC_ADV(t) ? u[t] + dt * L[t] : u[t];
     grad_pass(M, T.xi, T.w, T.D, u1, qx, qy);
     div_pass(M, T.w, T.D, u1, qx, qy, L);
 #pragma omp parallel for schedule(static)
     for (long t = 0; t < (long)N; ++t)
-      u2[t] = 0.75 * u[t] + 0.25 * (u1[t] + dt * L[t]);
+      u2[t] = ORC_ADV(t) ? 0.75 * u[t] + 0.25 * (u1[t] + dt * L[t]) : u[t];
     grad_pass(M, T.xi, T.w, T.D, u2, qx, qy);
     div_pass(M, T.w, T.D, u2, qx, qy, L);
 #pragma omp parallel for schedule(static)
     for (long t = 0; t < (long)N; ++t)
-      u[t] = u[t] / 3.0 + 2.0 * (u2[t] + dt * L[t]) / 3.0;
+      if (ORC_ADV(t)) u[t] = u[t] / 3.0 + 2.0 * (u2[t] + dt * L[t]) / 3.0;
   }
+#undef ORC_ADV
   free(buf);
   return 0;
+}
+
+int orc_rk3(const orc_mesh *M, double *u, int nsteps, double dt) {
+  return orc_rk3_adv(M, u, nsteps, dt, NULL);
 }
 
 /* ------------------------------------------------------------------------ */

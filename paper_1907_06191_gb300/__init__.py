@@ -88,6 +88,8 @@ EXPORTS = {
     "dg_bind_state": (_I, [_P, _P, _SZ]),
     "dg_moments_dense_static": (_I, [_P, _I, _I, _I, _I, _I, _D, _D, _D, _P, _P, _P]),
     "dg_rasterize_disks": (_I, [_DP, _DP, _DP, _I, _D, _I, _P]),
+    "dg_basis_tables": (_I, [_I, _I, _DP, _DP, _DP, _DP]),
+    "dg_set_growing_window": (_I, [_P, _D]),
     # learned surrogate (include/dgsurrogate.h)
     "sg_create": (_I, [_I, ctypes.c_ulonglong, _I, ctypes.POINTER(_P)]),
     "sg_destroy": (None, [_P]),
@@ -258,6 +260,11 @@ class DGSolver:
         self._ck(self._L.dg_query_dt(self.ctx, ctypes.byref(dt), ctypes.byref(rho)), "dg_query_dt")
         return dt.value, rho.value
 
+    def set_growing_window(self, r_factor: float):
+        """Advance only elements within r_factor sqrt(sigma0^2 + 2 D t) of the
+        start-point box (0 turns it off)."""
+        self._ck(self._L.dg_set_growing_window(self.ctx, float(r_factor)), "dg_set_growing_window")
+
     def step(self, nsteps: int, dt: float):
         self._ck(self._L.dg_step(self.ctx, int(nsteps), float(dt)), "dg_step")
 
@@ -351,6 +358,17 @@ def rasterize_disks(cx, cy, r, L: float, npix: int = 128) -> np.ndarray:
     if rc != DG_OK:
         raise DgError(rc, f"dg_rasterize_disks: {lib().dg_strerror(rc).decode()}")
     return out
+
+
+def basis_tables(p: int, precision: int = DG_FP64):
+    """(xi, w, D, D2) of order p as the kernels of that precision use them."""
+    n = p + 1
+    xi, w = np.zeros(n), np.zeros(n)
+    D, D2 = np.zeros((n, n)), np.zeros((n, n))
+    rc = lib().dg_basis_tables(int(p), int(precision), _dp(xi), _dp(w), _dp(D), _dp(D2))
+    if rc != DG_OK:
+        raise DgError(rc, f"dg_basis_tables: {lib().dg_strerror(rc).decode()}")
+    return xi, w, D, D2
 
 
 class Surrogate:

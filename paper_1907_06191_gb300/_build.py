@@ -51,7 +51,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
-    common = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC",
+    common = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
               "-I" + os.path.join(ROOT, "include")]
 
     def compile_one(src):

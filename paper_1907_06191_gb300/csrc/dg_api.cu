@@ -3,6 +3,7 @@
 // Host code here validates arguments, owns device memory and sequences the
 // kernels; every arithmetic step of the path runs in the kernels of
 // dg_stage.cuh, dg_geometry.cu and dg_reduce.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -45,6 +46,18 @@ void drop_graph(Ctx &c) {
   c.graph_steps = 0;
 }
 
+void free_window(Ctx &c) {
+  cudaFree(c.d_gw_d2);
+  cudaFree(c.d_gw_adv);
+  cudaFree(c.d_gw_order);
+  c.d_gw_d2 = nullptr;
+  c.d_gw_adv = nullptr;
+  c.d_gw_order = nullptr;
+  c.gw_cmin.clear();
+  c.gw_ready = false;
+  c.gw_synced = false;
+}
+
 void free_state(Ctx &c) {
   drop_graph(c);
   if (c.state_owned && c.d_state) cudaFree(c.d_state);
@@ -57,6 +70,7 @@ void free_state(Ctx &c) {
   cudaFree(c.d_part);
   cudaFree(c.d_out);
   c.d_src = c.d_mom = c.d_mom0 = c.d_part = c.d_out = nullptr;
+  free_window(c);
   c.m = 0;
   c.t = 0;
   c.steps = 0;
@@ -75,7 +89,7 @@ size_t state_bytes_for(const Ctx &c, int m) {
 
 // One SSP-RK3 step: U1 = U + dt L U; U2 = 3/4 U + 1/4 (U1 + dt L U1);
 // U <- 1/3 U + 2/3 (U2 + dt L U2).  L = (k/J^2) R.
-cudaError_t rk3_step(Ctx &c, double dt, cudaStream_t s) {
+cudaError_t rk3_step(Ctx &c, double dt, cudaStream_t s, const ChunkSel &sel = ChunkSel{}) {
   const double kc = c.cfg.D;  // the kernel applies 1/J^2 of each element's geometry
   const double pen = c.cfg.eta * (c.cfg.p + 1.0) * (c.cfg.p + 1.0) * 0.5;
   const int wallA = c.cfg.wall_mode == DG_WALL_PAPER;
@@ -92,19 +106,20 @@ cudaError_t rk3_step(Ctx &c, double dt, cudaStream_t s) {
     if (c.cfg.precision == DG_FP64) {
       StageCoef<double> sc{co[k][0], co[k][1], co[k][2], pen, wallA};
       e = launch_stage_f64(c.cfg.p, (const double *)in[k], (const double *)base[k],
-                           (double *)outp[k], c.geo, st, c.m, c.gll, sc, s);
+                           (double *)outp[k], c.geo, st, c.m, c.gll, sc, s, sel);
     } else {
       StageCoef<float> sc{(float)co[k][0], (float)co[k][1], (float)co[k][2], (float)pen,
                           wallA};
       e = launch_stage_f32(c.cfg.p, (const float *)in[k], (const float *)base[k],
-                           (float *)outp[k], c.geo, st, c.m, c.gll, sc, s);
+                           (float *)outp[k], c.geo, st, c.m, c.gll, sc, s, sel);
     }
   }
   return e;
 }
 
-int run_steps(dg_ctx *ctx, int nsteps, double dt) {
+int run_steps_fixed(dg_ctx *ctx, int nsteps, double dt) {
   Ctx &c = ctx->c;
+  c.gw_synced = false;  // arrays 1 and 2 now hold stage values everywhere
   int left = nsteps;
   if (left >= kGraphChunk) {
     if (!c.graph || c.graph_dt != dt || c.graph_stream != c.stream) {
@@ -134,6 +149,108 @@ int run_steps(dg_ctx *ctx, int nsteps, double dt) {
   for (int k = 0; k < left; ++k) CK(rk3_step(c, dt, c.stream), "stage launch");
   c.steps += nsteps;
   return DG_OK;
+}
+
+// Window tables for the current sources: per element the squared distance to
+// its geometry's start-point box, chunks ordered by their nearest element.
+int prepare_window(dg_ctx *ctx) {
+  Ctx &c = ctx->c;
+  const int G = c.geo.G();
+  const long long n = c.geo.n_pad, nch = c.geo.n_chunks();
+  std::vector<double> box((size_t)4 * G);
+  for (int g = 0; g < G; ++g) {
+    double *b = &box[(size_t)4 * g];
+    b[0] = b[2] = INFINITY;
+    b[1] = b[3] = -INFINITY;
+    for (int s = 0; s < c.m; ++s) {
+      const double x = c.src[2 * ((size_t)g * c.m + s)], y = c.src[2 * ((size_t)g * c.m + s) + 1];
+      b[0] = std::min(b[0], x); b[1] = std::max(b[1], x);
+      b[2] = std::min(b[2], y); b[3] = std::max(b[3], y);
+    }
+  }
+  if (!c.d_gw_d2) {
+    CK(cudaMalloc(&c.d_gw_d2, sizeof(double) * (size_t)n), "window allocation");
+    CK(cudaMalloc(&c.d_gw_adv, (size_t)n), "window allocation");
+    CK(cudaMalloc(&c.d_gw_order, sizeof(int) * (size_t)nch), "window allocation");
+  }
+  double *d_box = nullptr;
+  CK(cudaMalloc(&d_box, sizeof(double) * box.size()), "window allocation");
+  std::vector<double> d2((size_t)n);
+  cudaError_t e = cudaMemcpyAsync(d_box, box.data(), sizeof(double) * box.size(),
+                                  cudaMemcpyHostToDevice, c.stream);
+  if (e == cudaSuccess) e = launch_window_d2(c, d_box, c.d_gw_d2, c.stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d2.data(), c.d_gw_d2, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost,
+                        c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  cudaFree(d_box);
+  CK(e, "window distances");
+  std::vector<double> cmin((size_t)nch, INFINITY);
+  c.gw_dmax = 0.0;
+  for (long long a = 0; a < n; ++a) {
+    const double v = d2[(size_t)a];
+    if (std::isinf(v)) continue;  // padding
+    cmin[(size_t)(a / kBlock)] = std::min(cmin[(size_t)(a / kBlock)], v);
+    c.gw_dmax = std::max(c.gw_dmax, v);
+  }
+  std::vector<int> order((size_t)nch);
+  for (long long k = 0; k < nch; ++k) order[(size_t)k] = (int)k;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return cmin[(size_t)a] < cmin[(size_t)b]; });
+  c.gw_cmin.resize((size_t)nch);
+  for (long long k = 0; k < nch; ++k) c.gw_cmin[(size_t)k] = cmin[(size_t)order[(size_t)k]];
+  CK(cudaMemcpyAsync(c.d_gw_order, order.data(), sizeof(int) * (size_t)nch, cudaMemcpyHostToDevice,
+                     c.stream), "window order");
+  CK(cudaStreamSynchronize(c.stream), "window order");
+  c.gw_ready = true;
+  return DG_OK;
+}
+
+// Steps on the growing window, starting at time t0.  Chunks that have not
+// been launched since the stage arrays were synchronised hold array 0's
+// values in arrays 1 and 2, so launched chunks read their halos correctly.
+int run_steps_window(dg_ctx *ctx, int nsteps, double dt, double t0) {
+  Ctx &c = ctx->c;
+  if (!c.gw_ready) {
+    const int r = prepare_window(ctx);
+    if (r != DG_OK) return r;
+  }
+  if (!c.gw_synced) {
+    const size_t bytes = (size_t)c.m * c.field_elems() * c.esize();
+    CK(cudaMemcpyAsync(state_array(c, 1), state_array(c, 0), bytes, cudaMemcpyDeviceToDevice,
+                       c.stream), "window sync");
+    CK(cudaMemcpyAsync(state_array(c, 2), state_array(c, 0), bytes, cudaMemcpyDeviceToDevice,
+                       c.stream), "window sync");
+    c.gw_synced = true;
+  }
+  const double s0 = c.cfg.sigma0, D = c.cfg.D;
+  int done = 0;
+  while (done < nsteps) {
+    const int k = std::min(kGraphChunk, nsteps - done);
+    const double t_end = t0 + (double)(done + k) * dt;
+    const double r2 = c.gw_r * c.gw_r * (s0 * s0 + 2.0 * D * t_end);
+    if (r2 >= c.gw_dmax) {
+      // every mesh element advances from here on: the fixed-window path
+      c.steps += done;
+      return run_steps_fixed(ctx, nsteps - done, dt);
+    }
+    const long long nact =
+        std::upper_bound(c.gw_cmin.begin(), c.gw_cmin.end(), r2) - c.gw_cmin.begin();
+    CK(launch_window_flags(c, c.d_gw_d2, r2, c.d_gw_adv, c.stream), "window flags");
+    ChunkSel sel;
+    sel.list = c.d_gw_order;
+    sel.count = nact;
+    sel.adv = c.d_gw_adv;
+    for (int j = 0; j < k; ++j) CK(rk3_step(c, dt, c.stream, sel), "stage launch");
+    done += k;
+  }
+  c.steps += nsteps;
+  return DG_OK;
+}
+
+int run_steps(dg_ctx *ctx, int nsteps, double dt, double t0) {
+  if (ctx->c.gw_r > 0.0) return run_steps_window(ctx, nsteps, dt, t0);
+  return run_steps_fixed(ctx, nsteps, dt);
 }
 
 int compute_moments(dg_ctx *ctx, double *d_dst) {
@@ -282,6 +399,8 @@ int set_sources_impl(dg_ctx *ctx, const double *xy, int m) {
     CK(cudaMalloc(&c.d_out, sizeof(double) * (kCovOut + 1) * G), "output allocation");
   }
   c.src.assign(xy, xy + 2 * nd);
+  c.gw_ready = false;
+  c.gw_synced = false;
   CK(cudaMemcpyAsync(c.d_src, c.src.data(), sizeof(double) * 2 * nd, cudaMemcpyHostToDevice, c.stream), "source copy");
   CK(launch_init_sources(c, state_array(c, 0), c.stream), "init sources");
   int r = compute_moments(ctx, c.d_mom0);
@@ -483,6 +602,22 @@ int dg_rasterize_disks(const double *cx, const double *cy, const double *r, int 
   return DG_OK;
 }
 
+int dg_basis_tables(int p, int precision, double *xi, double *w, double *D, double *D2) {
+  if (precision != DG_FP32 && precision != DG_FP64) return DG_EINVAL;
+  Gll g;
+  if (!gll_tables(p, &g)) return DG_EINVAL;
+  const int n = p + 1;
+  for (int i = 0; i < n; ++i) {
+    if (xi) xi[i] = g.xi[i];
+    if (w) w[i] = g.w[i];
+  }
+  for (int k = 0; k < n * n; ++k) {
+    if (D) D[k] = precision == DG_FP32 ? (double)g.Df[k] : g.D[k];
+    if (D2) D2[k] = precision == DG_FP32 ? (double)g.D2f[k] : g.D2[k];
+  }
+  return DG_OK;
+}
+
 int dg_get_mask(dg_ctx *ctx, uint8_t *active) {
   if (!ctx || !active) return DG_EINVAL;
   Ctx &c = ctx->c;
@@ -525,6 +660,15 @@ int dg_set_sources(dg_ctx *ctx, const double *xy, int m) {
   }
 }
 
+int dg_set_growing_window(dg_ctx *ctx, double r_factor) {
+  if (!ctx) return DG_EINVAL;
+  Ctx &c = ctx->c;
+  if (!(r_factor >= 0.0) || !std::isfinite(r_factor))
+    return fail(ctx, DG_EINVAL, "r_factor must be finite and >= 0");
+  c.gw_r = r_factor;
+  return DG_OK;
+}
+
 int dg_query_dt(dg_ctx *ctx, double *dt_max, double *rho) {
   if (!ctx) return DG_EINVAL;
   CK(cudaSetDevice(ctx->c.device), "set device");
@@ -541,7 +685,7 @@ int dg_step(dg_ctx *ctx, int nsteps, double dt) {
   if (c.m < 1) return fail(ctx, DG_ESTATE, "dg_step before dg_set_sources");
   if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, DG_EINVAL, "need nsteps >= 0 and dt > 0");
   CK(cudaSetDevice(c.device), "set device");
-  const int r = run_steps(ctx, nsteps, dt);
+  const int r = run_steps(ctx, nsteps, dt, c.t);
   if (r == DG_OK) c.t += nsteps * dt;
   return r;
 }
@@ -564,7 +708,7 @@ int dg_propagate_to(dg_ctx *ctx, double Delta) {
   long long done = 0;
   while (done < N) {
     const int chunk = (int)std::min<long long>(kCheckChunk, N - done);
-    r = run_steps(ctx, chunk, dt);
+    r = run_steps(ctx, chunk, dt, c.t + (double)done * dt);
     if (r != DG_OK) return r;
     done += chunk;
     r = check_growth(ctx);
@@ -675,6 +819,7 @@ int dg_apply_operator(dg_ctx *ctx) {
   const double pen = c.cfg.eta * (c.cfg.p + 1.0) * (c.cfg.p + 1.0) * 0.5;
   const int wallA = c.cfg.wall_mode == DG_WALL_PAPER;
   void *U0 = state_array(c, 0), *U1 = state_array(c, 1);
+  c.gw_synced = false;
   cudaError_t e;
   if (c.cfg.precision == DG_FP64) {
     StageCoef<double> sc{0.0, 0.0, kc, pen, wallA};
@@ -715,6 +860,7 @@ int dg_set_nodes(dg_ctx *ctx, const double *host) {
   if (c.m < 1) return fail(ctx, DG_ESTATE, "no sources");
   if (c.geo.G() > 1) return fail(ctx, DG_EINVAL, "several geometries: not supported");
   CK(cudaSetDevice(c.device), "set device");
+  c.gw_synced = false;
   const size_t nd = (size_t)c.m * c.geo.nx * c.geo.ny * c.np();
   double *d = nullptr;
   CK(cudaMalloc(&d, nd * 8), "dense buffer");

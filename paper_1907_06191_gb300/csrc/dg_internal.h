@@ -30,6 +30,11 @@ struct Gll {
   double xi[kMaxN], w[kMaxN];
   double D[kMaxN * kMaxN];   // D[a*n + i] = l_i'(xi_a)
   double D2[kMaxN * kMaxN];  // (D D)[a*n + i]
+  // FP32 copies of D and D D whose rows sum to exactly zero (a constant has
+  // exactly zero derivative, so the volume term adds no mass) and that keep
+  // the centro-(anti)symmetry of the FP64 tables; each entry within a few
+  // FP32 ulps of the FP64 value
+  float Df[kMaxN * kMaxN], D2f[kMaxN * kMaxN];
 };
 bool gll_tables(int p, Gll *g);
 double rk3_real_axis_limit();
@@ -137,6 +142,19 @@ struct Ctx {
   double *d_out = nullptr;        // [G][kCovOut] covariance results
   size_t part_elems = 0;
 
+  // Growing window (off while gw_r <= 0): in each group of up to 64 steps an
+  // element advances only if its centre lies within
+  // R = gw_r sqrt(sigma0^2 + 2 D t_end) of its geometry's start-point box;
+  // chunks with no such element are not launched.
+  double gw_r = 0;
+  bool gw_ready = false;          // tables below match the current sources
+  bool gw_synced = false;         // arrays 1 and 2 equal array 0 (held chunks)
+  double *d_gw_d2 = nullptr;      // [n_pad] squared centre-to-box distance (inf: padding)
+  uint8_t *d_gw_adv = nullptr;    // [n_pad] 1 = advances in the current group
+  int *d_gw_order = nullptr;      // [n_chunks] chunks by increasing nearest distance
+  std::vector<double> gw_cmin;    // nearest squared distance of each chunk, same order
+  double gw_dmax = 0;             // largest squared distance of a mesh element
+
   // graph of a chunk of steps
   cudaGraphExec_t graph = nullptr;
   double graph_dt = 0;
@@ -149,13 +167,24 @@ struct Ctx {
 };
 
 // ---- launchers (defined in the .cu files) ----
-// One stage over all m densities: out = alpha u0 + beta u + gamma R(u).
+// Which chunks a stage launch covers.  Default: every chunk, every element
+// advances.  list: the first count entries are the chunks to launch (the
+// others are not touched); adv (per element, may be null): 0 holds the
+// element's value (gamma = 0), 1 advances it.
+struct ChunkSel {
+  const int *list = nullptr;
+  long long count = -1;
+  const uint8_t *adv = nullptr;
+};
+// One stage over all m densities: out = u0 + beta (u - u0) + gamma R(u).
 cudaError_t launch_stage_f64(int p, const double *u, const double *u0, double *out,
                              const Geometry &geo, long long stride, int m,
-                             const Gll &g, const StageCoef<double> &c, cudaStream_t s);
+                             const Gll &g, const StageCoef<double> &c, cudaStream_t s,
+                             const ChunkSel &sel = ChunkSel{});
 cudaError_t launch_stage_f32(int p, const float *u, const float *u0, float *out,
                              const Geometry &geo, long long stride, int m,
-                             const Gll &g, const StageCoef<float> &c, cudaStream_t s);
+                             const Gll &g, const StageCoef<float> &c, cudaStream_t s,
+                             const ChunkSel &sel = ChunkSel{});
 
 cudaError_t build_mask_disks(const double *d_cx, const double *d_cy, const double *d_r,
                              int nd, double L, int n_cell, int tiles, uint8_t *d_mask,
@@ -177,6 +206,12 @@ int moment_blocks(int G);  // first-pass blocks per density of the moment reduct
 // covariance output d_cov of the same t); d_res is [G m][7] scratch.
 cudaError_t launch_ls_residual(const Ctx &c, const void *u, const double *d_cov,
                                double *d_part, double *d_res, double *d_out, cudaStream_t s);
+// Growing window: squared distance of every element centre to its
+// geometry's box d_box [G][4] = {x_lo, x_hi, y_lo, y_hi} (FP64, rounded
+// operation by operation), and the advance flags d2 <= r2.
+cudaError_t launch_window_d2(const Ctx &c, const double *d_box, double *d2, cudaStream_t s);
+cudaError_t launch_window_flags(const Ctx &c, const double *d2, double r2, uint8_t *adv,
+                                cudaStream_t s);
 cudaError_t launch_nodes_to_dense(const Ctx &c, const void *u, double *d_dense,
                                   cudaStream_t s);
 cudaError_t launch_dense_to_nodes(const Ctx &c, const double *d_dense, void *u,

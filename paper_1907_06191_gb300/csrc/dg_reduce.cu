@@ -436,6 +436,54 @@ __global__ void k_scale_rnorm(long long nvals, const double *__restrict__ in,
   out[t] = in[t] * res[1];
 }
 
+// ---- growing window ---------------------------------------------------------------
+// Squared distance from the centre (x0 + (ex + 1/2) h, y0 + (ey + 1/2) h) of
+// every mesh element to its geometry's start-point box; each operation is
+// rounded on its own (no fused multiply-add) so that the window takes the
+// same decisions as a plain FP64 evaluation of the same expression.
+// Padding elements get +inf (never advance).
+__global__ void k_window_d2(long long n_pad, const int2 *__restrict__ exy,
+                            const int2 *__restrict__ chunk_tab, const double4 *__restrict__ gpar,
+                            const double *__restrict__ box, double *__restrict__ d2) {
+  const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n_pad) return;
+  const int2 ci = chunk_tab[a / kBlock];
+  if ((int)(a % kBlock) >= ci.x) {
+    d2[a] = INFINITY;
+    return;
+  }
+  const double4 gp = gpar[ci.y];
+  const double *b = box + 4 * ci.y;
+  const int2 e = exy[a];
+  const double x = __dadd_rn(gp.x, __dmul_rn((double)e.x + 0.5, gp.z));
+  const double y = __dadd_rn(gp.y, __dmul_rn((double)e.y + 0.5, gp.z));
+  const double dx = fmax(fmax(__dsub_rn(b[0], x), __dsub_rn(x, b[1])), 0.0);
+  const double dy = fmax(fmax(__dsub_rn(b[2], y), __dsub_rn(y, b[3])), 0.0);
+  d2[a] = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+}
+
+__global__ void k_window_flags(long long n_pad, const double *__restrict__ d2, double r2,
+                               uint8_t *__restrict__ adv) {
+  const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a < n_pad) adv[a] = d2[a] <= r2 ? 1 : 0;
+}
+
+cudaError_t launch_window_d2(const Ctx &c, const double *d_box, double *d2, cudaStream_t s) {
+  const long long n = c.geo.n_pad;
+  if (n <= 0) return cudaSuccess;
+  k_window_d2<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, c.geo.d_exy, c.geo.d_chunk,
+                                                          c.geo.d_gpar, d_box, d2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_window_flags(const Ctx &c, const double *d2, double r2, uint8_t *adv,
+                                cudaStream_t s) {
+  const long long n = c.geo.n_pad;
+  if (n <= 0) return cudaSuccess;
+  k_window_flags<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, d2, r2, adv);
+  return cudaGetLastError();
+}
+
 // ---- launchers ----------------------------------------------------------------
 #define DG_P_SWITCH(p, CALL)          \
   switch (p) {                        \

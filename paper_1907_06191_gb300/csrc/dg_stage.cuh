@@ -267,7 +267,8 @@ __device__ __forceinline__ void face_record(const T (&u)[(P + 1) * (P + 1)], int
   for (int t = 0; t < P + 1; ++t) tr[t] = u[Faces<P>::own(f, t)];
 }
 
-// grid: (ceil(nA / kBlock), m); density s = blockIdx.y starts at s * stride
+// grid: (chunks launched, m): block x takes chunk chunk_list[x] (x itself
+// without a list); density s = blockIdx.y starts at s * stride
 // elements.  loc/halo tables come from the geometry (entries checked when
 // built).  out may alias u0 (the last stage updates u^n in place: a block
 // reads its whole u0 chunk into shared memory before it writes the same
@@ -287,6 +288,7 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
             const int4 *__restrict__ loc, const int2 *__restrict__ halo,
             const int *__restrict__ halo_cnt, const int2 *__restrict__ chunk_tab,
             const T *__restrict__ gscale, long long stride, int nrec,
+            const int *__restrict__ chunk_list, const uint8_t *__restrict__ adv,
             const StageTab<T, P> tb, const StageCoef<T> c) {
   constexpr int n = P + 1, NP = n * n;
   using St = Stage<T, NP>;
@@ -301,13 +303,16 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
                     rec_base + ((nrec * n * (int)sizeof(T) + 15) / 16) * 16 / (int)sizeof(T), nrec};
   const int zero_rec = nrec - 1;
 
-  const int chunk = blockIdx.x;
+  const int chunk = chunk_list ? __ldg(chunk_list + blockIdx.x) : (int)blockIdx.x;
   const long long a0 = (long long)chunk * kBlock;
   const int2 ci = __ldg(chunk_tab + chunk);  // {elements in the mesh, geometry}
   const int cnt = ci.x;
-  const T gam = c.gamma * __ldg(gscale + ci.y);  // beta dt D / J^2 of this geometry
   const int el = threadIdx.x;
   const bool live = el < cnt;
+  // beta dt D / J^2 of this geometry; 0 for an element held by the growing
+  // window (its value then passes through every stage unchanged)
+  T gam = c.gamma * __ldg(gscale + ci.y);
+  if (adv != nullptr && live && __ldg(adv + a0 + el) == 0) gam = (T)0;
   const size_t sbase = (size_t)blockIdx.y * (size_t)stride * NP;
   const T *U = uin + sbase;
 
@@ -471,8 +476,13 @@ StageTab<T, P> make_tab(const Gll &g) {
   StageTab<T, P> t;
   constexpr int n = P + 1;
   for (int k = 0; k < n * n; ++k) {
-    t.D[k] = (T)g.D[k];
-    t.D2[k] = (T)g.D2[k];
+    if constexpr (sizeof(T) == 4) {
+      t.D[k] = g.Df[k];
+      t.D2[k] = g.D2f[k];
+    } else {
+      t.D[k] = g.D[k];
+      t.D2[k] = g.D2[k];
+    }
   }
   t.inv_w = (T)(1.0 / g.w[0]);
   return t;
@@ -481,9 +491,11 @@ StageTab<T, P> make_tab(const Gll &g) {
 template <typename T, int P>
 cudaError_t launch_stage_p(const T *u, const T *u0, T *out, const Geometry &geo,
                            long long stride, int m, const Gll &g, const StageCoef<T> &c,
-                           cudaStream_t s) {
-  if (geo.n_pad <= 0 || m <= 0) return cudaSuccess;
-  const dim3 grid((unsigned)geo.n_chunks(), (unsigned)m);
+                           cudaStream_t s, const ChunkSel &sel) {
+  const long long nch = sel.list ? sel.count : geo.n_chunks();
+  if (geo.n_pad <= 0 || m <= 0 || nch <= 0) return cudaSuccess;
+  if (nch > geo.n_chunks()) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)nch, (unsigned)m);
   const T *gscale;
   if constexpr (sizeof(T) == 8) gscale = geo.d_gscale_d;
   else gscale = geo.d_gscale_f;
@@ -503,24 +515,24 @@ cudaError_t launch_stage_p(const T *u, const T *u0, T *out, const Geometry &geo,
   if (u0)
     k_stage<T, P, true><<<grid, kBlock, smem, s>>>(u, u0, out, geo.d_loc, geo.d_halo,
                                                    geo.d_halo_cnt, geo.d_chunk, gscale, stride,
-                                                   nrec, tb, c);
+                                                   nrec, sel.list, sel.adv, tb, c);
   else
     k_stage<T, P, false><<<grid, kBlock, smem, s>>>(u, u0, out, geo.d_loc, geo.d_halo,
                                                     geo.d_halo_cnt, geo.d_chunk, gscale, stride,
-                                                    nrec, tb, c);
+                                                    nrec, sel.list, sel.adv, tb, c);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_stage_any(int p, const T *u, const T *u0, T *out, const Geometry &geo,
                              long long stride, int m, const Gll &g, const StageCoef<T> &c,
-                             cudaStream_t s) {
+                             cudaStream_t s, const ChunkSel &sel) {
   switch (p) {
-    case 1: return launch_stage_p<T, 1>(u, u0, out, geo, stride, m, g, c, s);
-    case 2: return launch_stage_p<T, 2>(u, u0, out, geo, stride, m, g, c, s);
-    case 3: return launch_stage_p<T, 3>(u, u0, out, geo, stride, m, g, c, s);
-    case 4: return launch_stage_p<T, 4>(u, u0, out, geo, stride, m, g, c, s);
-    case 5: return launch_stage_p<T, 5>(u, u0, out, geo, stride, m, g, c, s);
+    case 1: return launch_stage_p<T, 1>(u, u0, out, geo, stride, m, g, c, s, sel);
+    case 2: return launch_stage_p<T, 2>(u, u0, out, geo, stride, m, g, c, s, sel);
+    case 3: return launch_stage_p<T, 3>(u, u0, out, geo, stride, m, g, c, s, sel);
+    case 4: return launch_stage_p<T, 4>(u, u0, out, geo, stride, m, g, c, s, sel);
+    case 5: return launch_stage_p<T, 5>(u, u0, out, geo, stride, m, g, c, s, sel);
     default: return cudaErrorInvalidValue;
   }
 }

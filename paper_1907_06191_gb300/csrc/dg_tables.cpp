@@ -20,6 +20,108 @@ static void legendre_pair(int p, double x, double *Pp, double *dPp, double *Pm,
   *Pp = P1; *dPp = d1; *Pm = P0; *dPm = d0;
 }
 
+namespace {
+
+// a + b with its rounding error (Knuth's TwoSum)
+inline double two_sum(double a, double b, double *err) {
+  const double s = a + b;
+  const double bb = s - a;
+  *err = (a - (s - bb)) + (b - bb);
+  return s;
+}
+
+// Exact sum of FP32 values, or false if FP64 cannot hold it exactly.
+bool exact_sum(const float *v, int n, int skip, double *out) {
+  double s = 0.0;
+  for (int k = 0; k < n; ++k) {
+    if (k == skip) continue;
+    double e;
+    s = two_sum(s, (double)v[k], &e);
+    if (e != 0.0) return false;
+  }
+  *out = s;
+  return true;
+}
+
+float step_ulp(float x, int k) {
+  for (; k > 0; --k) x = std::nextafter(x, INFINITY);
+  for (; k < 0; ++k) x = std::nextafter(x, -INFINITY);
+  return x;
+}
+
+double ulp_of(double t) {
+  const float f = (float)std::fabs(t);
+  return (double)std::nextafter(f, INFINITY) - (double)f;
+}
+
+// FP32 row g close to the FP64 row t (n entries) with an exactly zero sum.
+// Structural zeros of t stay zero.  mirror = 0: no constraint; +1 / -1: the
+// row must satisfy g[n-1-k] = mirror * g[k] (middle row of a centro-symmetric
+// / antisymmetric matrix).  One entry (the free one) takes minus the sum of
+// the others; at most one other entry (and its mirror partner) moves by one
+// ulp.  The candidate with the smallest largest error in ulps wins.
+bool zero_sum_row(const double *t_in, int n, int mirror, float *g_out) {
+  double t[kMaxN], tmax = 0.0;
+  for (int k = 0; k < n; ++k) tmax = std::fmax(tmax, std::fabs(t_in[k]));
+  for (int k = 0; k < n; ++k) t[k] = std::fabs(t_in[k]) < 1e-12 * tmax ? 0.0 : t_in[k];
+  float f[kMaxN];
+  for (int k = 0; k < n; ++k) f[k] = (float)t[k];
+  if (mirror != 0)
+    for (int k = 0; k < n; ++k) f[n - 1 - k] = (float)mirror * f[k];
+  double s0;
+  if (exact_sum(f, n, -1, &s0) && s0 == 0.0) {
+    for (int k = 0; k < n; ++k) g_out[k] = f[k];
+    return true;
+  }
+  double best = INFINITY;
+  for (int m = 0; m < n; ++m) {
+    if (t[m] == 0.0) continue;
+    if (mirror == 1 && 2 * m != n - 1) continue;  // palindrome: only the centre is free
+    if (mirror == -1) continue;                   // antisymmetric rows already sum to zero
+    for (int j = -1; j < n; ++j) {
+      for (int dir = -1; dir <= 1; dir += 2) {
+        if (j == m || (j < 0 && dir > 0)) continue;
+        if (j >= 0 && t[j] == 0.0) continue;
+        float g[kMaxN];
+        for (int k = 0; k < n; ++k) g[k] = f[k];
+        if (j >= 0) {
+          g[j] = step_ulp(g[j], dir);
+          if (mirror == 1) g[n - 1 - j] = g[j];
+          if (mirror == 1 && n - 1 - j == m) continue;
+        }
+        double s;
+        if (!exact_sum(g, n, m, &s)) continue;
+        if ((double)(float)s != s) continue;
+        g[m] = (float)(-s);
+        double cost = 0.0;
+        for (int k = 0; k < n; ++k)
+          if (t[k] != 0.0) cost = std::fmax(cost, std::fabs((double)g[k] - t[k]) / ulp_of(t[k]));
+        if (cost < best) {
+          best = cost;
+          for (int k = 0; k < n; ++k) g_out[k] = g[k];
+        }
+      }
+    }
+  }
+  return best < 8.0;
+}
+
+// mirror = -1: centro-antisymmetric (D), +1: centro-symmetric (D D).
+void zero_sum_matrix(const double *M, int n, int mirror, float *out) {
+  for (int a = 0; 2 * a < n; ++a) {
+    const bool mid = 2 * a == n - 1;
+    float g[kMaxN];
+    if (!zero_sum_row(M + a * n, n, mid ? mirror : 0, g))
+      for (int k = 0; k < n; ++k) g[k] = (float)M[a * n + k];  // plain rounding
+    for (int k = 0; k < n; ++k) {
+      out[a * n + k] = g[k];
+      out[(n - 1 - a) * n + (n - 1 - k)] = (float)mirror * g[k];
+    }
+  }
+}
+
+}  // namespace
+
 // Interior GLL nodes are the zeros of q(x) = P_{p-1}(x) - x P_p(x), which is
 // (1 - x^2) P_p'(x) / p; Newton with q' = P_{p-1}' - P_p - x P_p'.
 // Weights 2 / (p (p+1) P_p(x_i)^2).  D_ij = P_p(x_i) / (P_p(x_j) (x_i - x_j))
@@ -30,7 +132,10 @@ bool gll_tables(int p, Gll *g) {
   g->p = p;
   g->xi[0] = -1.0;
   g->xi[p] = 1.0;
-  for (int i = 1; i < p; ++i) {
+  // interior nodes of the left half by Newton; the right half mirrors them
+  // (x_{p-i} = -x_i exactly, and 0 in the middle for even p), so that the
+  // tables below are exactly centro-(anti)symmetric
+  for (int i = 1; 2 * i < p; ++i) {
     double x = -std::cos(M_PI * (double)i / (double)p);
     for (int it = 0; it < 60; ++it) {
       double Pp, dPp, Pm, dPm;
@@ -42,7 +147,9 @@ bool gll_tables(int p, Gll *g) {
       if (std::fabs(step) < 1e-17) break;
     }
     g->xi[i] = x;
+    g->xi[p - i] = -x;
   }
+  if (p % 2 == 0) g->xi[p / 2] = 0.0;
   double Pv[kMaxN];
   for (int i = 0; i < n; ++i) {
     double Pp, dPp, Pm, dPm;
@@ -64,8 +171,11 @@ bool gll_tables(int p, Gll *g) {
       for (int k = 0; k < n; ++k) s += g->D[i * n + k] * g->D[k * n + j];
       g->D2[i * n + j] = s;
     }
+  zero_sum_matrix(g->D, n, -1, g->Df);
+  zero_sum_matrix(g->D2, n, 1, g->D2f);
   return true;
 }
+
 
 // SSP-RK3 amplification on the real axis is 1 + z + z^2/2 + z^3/6; the step
 // stays stable for -x3 <= z <= 0 where the polynomial reaches -1 at z = -x3.

@@ -281,6 +281,75 @@ def test_mass_conservation_and_components(wall_mode):
     assert np.abs(u[act == 0]).max() == 0.0
 
 
+def test_frozen_component_keeps_values_and_the_other_evolves_alone():
+    """Held elements (the growing window's frozen region) keep their values
+    bit for bit, and a component that walls separate from them evolves
+    exactly as without the mask: no face couples the two components."""
+    act = np.ones((10, 10), np.uint8)
+    act[2:8, 2] = act[2:8, 7] = 0
+    act[2, 2:8] = act[7, 2:8] = 0
+    m = O.Mesh(p=2, active=act, h=0.5, k0=2.0, periodic=True)
+    u0 = O.init_gaussian(m, 1.3, 1.1, 0.4)
+    rho = O.power_rho(m)
+    n, dt = O.step_plan(rho, 0.5)
+    inside = np.zeros(act.shape, dtype=bool)
+    inside[3:7, 3:7] = True
+    full = O.rk3(m, u0, n, dt)
+    held = O.rk3(m, u0, n, dt, advance=inside)
+    assert np.array_equal(held[inside], full[inside])
+    assert np.array_equal(held[~inside], u0[~inside])
+    assert not np.array_equal(full[~inside], u0[~inside])
+    assert np.array_equal(O.rk3(m, u0, n, dt, advance=np.ones(act.shape, bool)), full)
+    assert np.array_equal(O.rk3(m, u0, n, dt, advance=np.zeros(act.shape, bool)), u0)
+
+
+def test_window_distance_closed_form():
+    m = O.Mesh(p=1, active=np.ones((4, 5), np.uint8), h=2.0, x0=-1.0, y0=3.0)
+    # element centres x = 0, 2, 4, 6, 8 and y = 4, 6, 8, 10
+    d2 = O.window_d2(m, (1.5, 4.5, 5.0, 7.0))
+    assert d2[1, 2] == 0.0                       # (4, 6) inside the box
+    assert d2[0, 0] == 1.5 ** 2 + 1.0 ** 2       # (0, 4): corner distance
+    assert d2[3, 4] == 3.5 ** 2 + 3.0 ** 2       # (8, 10)
+    assert d2[2, 1] == 1.0                       # (2, 8): above the box only
+
+
+def test_growing_window_free_diffusion():
+    """Sec. 4.2 free diffusion (2Tk = 32.4) on a window that grows with the
+    density: elements farther than 6 sqrt(sigma0^2 + 2kt) from the start
+    point hold their values.  Sigma moves from the fixed-window solve by about
+    70 exp(-r^2/2) relative (the Gaussian's weight at the held edge): 1e-6 at
+    r = 6, 1.5e-12 at r = 8, while the work drops; a radius that covers the
+    window from the start reproduces the fixed window bit for bit."""
+    g = _gold("paper_free_diffusion.json")
+    k, T = g["k0_um2_per_ms"], g["T_ms"]
+    nel, side, s0 = 60, 120.0, 4.0
+    h = side / nel
+    m = O.Mesh(p=2, active=np.ones((nel, nel), np.uint8), h=h,
+               x0=-side / 2, y0=-side / 2, k0=k)
+    xs, ys = 0.3 * h, -0.2 * h
+    u0 = O.init_gaussian(m, xs, ys, s0)
+    n, dt = O.step_plan(O.power_rho(m), T)
+    box = (xs, xs, ys, ys)
+    full = O.rk3(m, u0, n, dt)
+    assert np.array_equal(O.rk3_growing(m, u0, n, dt, box, 100.0, s0), full)
+    m0 = O.moments(m, u0, xs, ys)
+    sf = O.aggregate(np.array([O.moments(m, full, xs, ys)]), np.array([m0]))[0]
+    assert abs(sf[0] - g["sigma_analytic_diag"]) < 1e-9 * 32.4
+    for r, tol in ((6.0, 3e-6), (8.0, 1e-10)):
+        grow = O.rk3_growing(m, u0, n, dt, box, r, s0)
+        sg = O.aggregate(np.array([O.moments(m, grow, xs, ys)]), np.array([m0]))[0]
+        assert np.abs(sg - sf).max() < tol * 32.4
+    # elements advanced: well under the fixed window's
+    d2 = O.window_d2(m, box)
+    steps_done, work = 0, 0
+    while steps_done < n:
+        kk = min(64, n - steps_done)
+        t_end = (steps_done + kk) * dt
+        work += kk * int((d2 <= 36.0 * (s0 * s0 + 2.0 * k * t_end)).sum())
+        steps_done += kk
+    assert work < 0.6 * n * nel * nel
+
+
 def test_symmetry_transforms():
     """Mirroring geometry and start point in x flips Sigma_xy and keeps the
     diagonal; transposing swaps Sigma_xx and Sigma_yy."""
