@@ -394,6 +394,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--rounding", default="stochastic", choices=["stochastic", "nearest"],
+                    help="rounding of the FP32 state (library default: stochastic)")
     ap.add_argument("--rk", type=int, default=20, help="RK3 steps per bench step")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--densities", type=int, default=64,
@@ -451,7 +453,8 @@ def main():
         w.sources = sample_sources(args.seed + 7919 + 1000 * rank, w.disks, args.densities, lo, hi,
                                    margin=w.h)
     prec = dg.DG_FP32 if args.precision == "f32" else dg.DG_FP64
-    s = dg.DGSolver(p=w.p, precision=prec, D=w.D, sigma0=w.sigma0, device=dev)
+    rnd = dg.DG_ROUND_STOCHASTIC if args.rounding == "stochastic" else dg.DG_ROUND_NEAREST
+    s = dg.DGSolver(p=w.p, precision=prec, D=w.D, sigma0=w.sigma0, device=dev, rounding=rnd)
     s.set_geometry_disks(w.disks.cx, w.disks.cy, w.disks.r, w.L, w.n_cell, w.tiles)
     stream = torch.cuda.Stream(device=dev)
     s.set_stream(stream.cuda_stream)
@@ -545,7 +548,8 @@ def main():
         nd = 4
         res = {}
         for pr in (dg.DG_FP32, dg.DG_FP64):
-            with dg.DGSolver(p=w.p, precision=pr, D=w.D, sigma0=w.sigma0, device=dev) as c2:
+            with dg.DGSolver(p=w.p, precision=pr, D=w.D, sigma0=w.sigma0, device=dev,
+                             rounding=rnd) as c2:
                 c2.set_geometry_disks(w.disks.cx, w.disks.cy, w.disks.r, w.L, w.n_cell, w.tiles)
                 c2.set_sources(w.sources[:nd])
                 t0 = time.perf_counter()
@@ -616,7 +620,9 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.precision, "data": "synthetic",
-        "config": {"workload": w.name, "p": w.p, "window_elements": inf.nx * inf.ny,
+        "config": {"workload": w.name, "p": w.p,
+                   "rounding": args.rounding if args.precision == "f32" else "nearest",
+                   "window_elements": inf.nx * inf.ny,
                    "active_elements": inf.n_active, "densities_per_gpu": m,
                    "dof_per_density": inf.dof_per_source, "rk_steps_per_bench_step": R,
                    "dt_ms": dt, "rho_per_ms": rho, "packing": w.disks.packing,

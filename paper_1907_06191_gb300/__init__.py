@@ -20,7 +20,8 @@ from . import _build
 __all__ = [
     "DG_OK", "DG_EINVAL", "DG_ENOMEM", "DG_ECUDA", "DG_EUNSTABLE", "DG_ENONFINITE",
     "DG_ETIMEOUT", "DG_ESTATE", "DG_FP64", "DG_FP32", "DG_WALL_REMOVED",
-    "DG_WALL_PAPER", "DG_BC_ABSORBING", "DG_BC_PERIODIC", "DgError", "dg_config",
+    "DG_WALL_PAPER", "DG_BC_ABSORBING", "DG_BC_PERIODIC", "DG_ROUND_NEAREST",
+    "DG_ROUND_STOCHASTIC", "DgError", "dg_config",
     "dg_info", "lib", "library_path", "DGSolver", "EXPORTS",
 ]
 
@@ -29,6 +30,7 @@ DG_EUNSTABLE, DG_ENONFINITE, DG_ETIMEOUT, DG_ESTATE = 4, 5, 6, 7
 DG_FP64, DG_FP32 = 0, 1
 DG_WALL_REMOVED, DG_WALL_PAPER = 0, 1
 DG_BC_ABSORBING, DG_BC_PERIODIC = 0, 1
+DG_ROUND_NEAREST, DG_ROUND_STOCHASTIC = 0, 1
 
 
 class dg_config(ctypes.Structure):
@@ -36,7 +38,8 @@ class dg_config(ctypes.Structure):
                 ("D", ctypes.c_double), ("sigma0", ctypes.c_double),
                 ("eta", ctypes.c_double), ("cfl_safety", ctypes.c_double),
                 ("wall_mode", ctypes.c_int), ("boundary", ctypes.c_int),
-                ("power_iters", ctypes.c_int), ("device", ctypes.c_int)]
+                ("power_iters", ctypes.c_int), ("device", ctypes.c_int),
+                ("rounding", ctypes.c_int)]
 
 
 class dg_info(ctypes.Structure):

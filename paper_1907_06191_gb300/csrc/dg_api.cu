@@ -109,7 +109,7 @@ cudaError_t rk3_step(Ctx &c, double dt, cudaStream_t s, const ChunkSel &sel = Ch
                            (double *)outp[k], c.geo, st, c.m, c.gll, sc, s, sel);
     } else {
       StageCoef<float> sc{(float)co[k][0], (float)co[k][1], (float)co[k][2], (float)pen,
-                          wallA};
+                          wallA, c.cfg.rounding == DG_ROUND_STOCHASTIC};
       e = launch_stage_f32(c.cfg.p, (const float *)in[k], (const float *)base[k],
                            (float *)outp[k], c.geo, st, c.m, c.gll, sc, s, sel);
     }
@@ -307,6 +307,7 @@ int check_config(const dg_config *cfg, std::string &why) {
   if (cfg->wall_mode != DG_WALL_REMOVED && cfg->wall_mode != DG_WALL_PAPER) { why = "bad wall_mode"; return DG_EINVAL; }
   if (cfg->boundary != DG_BC_ABSORBING && cfg->boundary != DG_BC_PERIODIC) { why = "bad boundary"; return DG_EINVAL; }
   if (cfg->power_iters < 0) { why = "power_iters must be >= 0"; return DG_EINVAL; }
+  if (cfg->rounding != DG_ROUND_NEAREST && cfg->rounding != DG_ROUND_STOCHASTIC) { why = "bad rounding"; return DG_EINVAL; }
   return DG_OK;
 }
 
@@ -447,6 +448,7 @@ void dg_config_default(dg_config *cfg) {
   cfg->boundary = DG_BC_ABSORBING;
   cfg->power_iters = 200;
   cfg->device = -1;
+  cfg->rounding = DG_ROUND_STOCHASTIC;
 }
 
 const char *dg_strerror(int code) {

@@ -47,6 +47,7 @@ struct StageCoef {
   T alpha, beta, gamma;  // alpha = 1 - beta, kept for reference only
   T pen;     // eta (p+1)^2 / 2
   int wallA; // paper wall mode
+  int sround = 0;  // FP32: stochastic rounding of the stage result
 };
 
 // Tables by value in the kernel parameter space (constant bank).
@@ -54,6 +55,7 @@ template <typename T, int P>
 struct StageTab {
   T D[(P + 1) * (P + 1)];
   T D2[(P + 1) * (P + 1)];
+  T Dout[2 * (P + 1)];  // outward derivative rows: D[p][:] (east, north), -D[0][:] (west, south)
   T inv_w;  // 1 / w_0 = 1 / w_p
 };
 

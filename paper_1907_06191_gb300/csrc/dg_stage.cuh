@@ -185,20 +185,46 @@ struct Faces {
   __host__ __device__ static constexpr int row(int f) { return (f & 1) ? 0 : P; }  // D row of the face
 };
 
-// Outward normal derivative (reference units) at the nodes of face f.
+// murmur3's 32-bit finaliser (Appleby): avalanche mixing of one word.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
+// base + inc rounded to FP32 stochastically: s = fl(base + inc) moves one unit
+// in the last place toward the exact sum with probability |err| / ulp(s), err
+// the rounding error of s (exact by Fast2Sum when |base| >= |inc|), so the
+// expected result is base + inc.  The uniform number comes from h, a hash that
+// already depends on the element, and the bits of inc (multiplicative hashing
+// by the golden ratio; its high bits are used): reproducible, and different
+// from step to step because the operands change.  Zero, subnormal and
+// non-finite sums are returned as s.
+__device__ __forceinline__ float add_stochastic(float base, float inc, uint32_t h) {
+  const float s = base + inc;
+  const float err = inc - (s - base);
+  const float ulp = __uint_as_float(__float_as_uint(s) & 0x7f800000u) * 0x1p-23f;
+  const uint32_t hk = (h ^ __float_as_uint(inc)) * 0x9e3779b9u;
+  const float r = __uint_as_float(0x3f800000u | (hk >> 9)) - 1.0f;  // uniform in [0, 1)
+  return fabsf(err) > r * ulp ? s + copysignf(ulp, err) : s;
+}
+
+// Outward normal derivative (reference units) at the nodes of face f: the
+// face's signed row of D applied along the lines normal to the face.
 template <typename T, int P>
 __device__ __forceinline__ void outward_derivative(const T (&u)[(P + 1) * (P + 1)], int f,
                                                    const StageTab<T, P> &tb, T (&d)[P + 1]) {
   constexpr int n = P + 1;
-  const int r = Faces<P>::row(f);
-  const T sg = (T)Faces<P>::sgn(f);
+  const T *row = tb.Dout + (f & 1) * n;
 #pragma unroll
   for (int t = 0; t < n; ++t) {
     T s = 0;
 #pragma unroll
-    for (int m = 0; m < n; ++m)
-      s += tb.D[r * n + m] * (f < 2 ? u[t * n + m] : u[m * n + t]);
-    d[t] = sg * s;
+    for (int m = 0; m < n; ++m) s += row[m] * (f < 2 ? u[t * n + m] : u[m * n + t]);
+    d[t] = s;
   }
 }
 
@@ -282,12 +308,15 @@ constexpr int stage_min_blocks() {
   else return P <= 3 ? 2 : 1;
 }
 
-template <typename T, int P, bool HAS_U0>
+// FULL = false drops the flux terms in u^- and u^+ that vanish without a
+// penalty (eta = 0) and without paper walls (the default configuration).
+template <typename T, int P, bool HAS_U0, bool SROUND, bool FULL>
 __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
     k_stage(const T *__restrict__ uin, const T *u0, T *out,
             const int4 *__restrict__ loc, const int2 *__restrict__ halo,
             const int *__restrict__ halo_cnt, const int2 *__restrict__ chunk_tab,
-            const T *__restrict__ gscale, long long stride, int nrec,
+            const int2 *__restrict__ grange, const T *__restrict__ gscale, long long stride,
+            int nrec,
             const int *__restrict__ chunk_list, const uint8_t *__restrict__ adv,
             const StageTab<T, P> tb, const StageCoef<T> c) {
   constexpr int n = P + 1, NP = n * n;
@@ -396,43 +425,51 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
 
   if (live) {
     const int lq[4] = {l4.x, l4.y, l4.z, l4.w};
-    const T half = (T)0.5;
+    const T half = (T)0.5, iw = tb.inv_w;
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
       const int L = lq[f];
       const int fo = Fc::opp(f);
       // neighbour record: chunk element, halo entry, or the zero record
       const int rn = L >= kBlock ? 4 * kBlock + (L - kBlock) : (L >= 0 ? fo * kBlock + L : zero_rec);
-      // face-kind coefficients: g = cg_up u+ + cg_um u-,
-      // F = -(c_od d- + c_odn d+ + c_um u- + c_up u+) / w   (see file header)
+      // face-kind coefficients with 1/w (and, for the lifting, the face sign)
+      // folded in: gs = s_f g / w = cg_up u+ + cg_um u-, and the face term
+      // F / w = c_od d- + c_odn d+ (+ c_um u- + c_up u+)   (see file header)
       const bool in = L >= 0, wl = L == kWall, wa = wl && c.wallA, ed = L == kEdge;
-      const T cg_up = in ? half : (T)0;
-      const T cg_um = in ? -half : (wa ? -half : (ed ? (T)-1 : (T)0));
-      const T c_od = in ? half : (ed ? (T)0 : (T)1);
-      const T c_odn = in ? half : (T)0;
-      const T c_um = in ? c.pen : (wa ? -half * tb.inv_w : (ed ? c.pen : (T)0));
-      const T c_up = in ? -c.pen : (T)0;
+      const T sw = (f & 1) ? -iw : iw;
+      const T cg_up = in ? half * sw : (T)0;
+      const T cg_um = in ? -half * sw : (wa ? -half * sw : (ed ? -sw : (T)0));
+      const T c_od = in ? half * iw : (ed ? (T)0 : iw);
+      const T c_odn = in ? half * iw : (T)0;
       T up[n], odn[n], od[n];
       rec.get_tr(rn, up);
       rec.get_d(rn, odn);
       rec.get_d(f * kBlock + el, od);
-      T g[n];
+      T gs[n];
+      if constexpr (FULL) {
+        const T c_um = (in ? c.pen : (wa ? -half * iw : (ed ? c.pen : (T)0))) * iw;
+        const T c_up = in ? -c.pen * iw : (T)0;
 #pragma unroll
-      for (int t = 0; t < n; ++t) {
-        const T um = u[Fc::own(f, t)];
-        g[t] = cg_up * up[t] + cg_um * um;
-        R[Fc::own(f, t)] -= tb.inv_w * (c_od * od[t] + c_odn * odn[t] + c_um * um + c_up * up[t]);
+        for (int t = 0; t < n; ++t) {
+          const T um = u[Fc::own(f, t)];
+          gs[t] = cg_up * up[t] + cg_um * um;
+          R[Fc::own(f, t)] -= c_od * od[t] + c_odn * odn[t] + c_um * um + c_up * up[t];
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < n; ++t) {
+          gs[t] = cg_up * up[t] + cg_um * u[Fc::own(f, t)];
+          R[Fc::own(f, t)] -= c_od * od[t] + c_odn * odn[t];
+        }
       }
       // lifting of the u-flux jump: column (x-faces) or row (y-faces) of D
       const int r = Fc::row(f);
-      const T sg = (T)Fc::sgn(f);
 #pragma unroll
       for (int t = 0; t < n; ++t) {
-        const T gs = sg * tb.inv_w * g[t];
 #pragma unroll
         for (int q = 0; q < n; ++q) {
-          if (f < 2) R[t * n + q] += tb.D[q * n + r] * gs;
-          else R[q * n + t] += tb.D[q * n + r] * gs;
+          if (f < 2) R[t * n + q] += tb.D[q * n + r] * gs[t];
+          else R[q * n + t] += tb.D[q * n + r] * gs[t];
         }
       }
     }
@@ -444,7 +481,25 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
   }
   if (live) {
     T o[NP];
-    if constexpr (HAS_U0) {
+    if constexpr (SROUND) {
+      // increment first, then one stochastic rounding onto the state; the key
+      // is the node's place inside its own geometry and its density, so a
+      // geometry gives the same bits alone or in a batch
+      if constexpr (HAS_U0) St::read(so, el, o);
+      auto base = [&](int k) -> T { return HAS_U0 ? o[k] : c.beta * u[k]; };
+      auto inc = [&](int k) -> T {
+        return HAS_U0 ? fmaf(c.beta, u[k] - o[k], gam * R[k]) : gam * R[k];
+      };
+      // one avalanche hash per element: its place in its geometry, its
+      // density and the bits of its first two input values (they change
+      // every stage while the element is advancing)
+      const uint32_t h = fmix32(
+          ((uint32_t)(a0 + el - __ldg(grange + ci.y).x) * (uint32_t)NP) ^
+          ((uint32_t)blockIdx.y * 0x632be5abu) ^ __float_as_uint(u[0]) ^
+          (__float_as_uint(u[1]) * 0x85ebca77u));
+#pragma unroll
+      for (int k = 0; k < NP; ++k) o[k] = add_stochastic(base(k), inc(k), h + (uint32_t)k);
+    } else if constexpr (HAS_U0) {
       St::read(so, el, o);
 #pragma unroll
       for (int k = 0; k < NP; ++k) o[k] = o[k] + c.beta * (u[k] - o[k]) + gam * R[k];
@@ -484,6 +539,10 @@ StageTab<T, P> make_tab(const Gll &g) {
       t.D2[k] = g.D2[k];
     }
   }
+  for (int m = 0; m < n; ++m) {
+    t.Dout[m] = t.D[P * n + m];
+    t.Dout[n + m] = -t.D[m];
+  }
   t.inv_w = (T)(1.0 / g.w[0]);
   return t;
 }
@@ -503,23 +562,39 @@ cudaError_t launch_stage_p(const T *u, const T *u0, T *out, const Geometry &geo,
   const int nrec = 4 * kBlock + geo.halo_max + 1;
   const int smem = stage_smem_bytes<T, P>(geo.halo_max);
   static int attr_bytes = 0;  // per instantiation: largest size configured so far
+  constexpr bool kSR = sizeof(T) == 4;  // stochastic-rounding variants exist in FP32 only
   if (smem > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(k_stage<T, P, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_stage<T, P, false>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaSuccess;
+    auto set = [&](auto kern) {
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    };
+    set(k_stage<T, P, true, false, false>);
+    set(k_stage<T, P, false, false, false>);
+    set(k_stage<T, P, true, false, true>);
+    set(k_stage<T, P, false, false, true>);
+    if constexpr (kSR) {
+      set(k_stage<T, P, true, kSR, false>);
+      set(k_stage<T, P, false, kSR, false>);
+      set(k_stage<T, P, true, kSR, true>);
+      set(k_stage<T, P, false, kSR, true>);
+    }
     if (e != cudaSuccess) return e;
     attr_bytes = smem;
   }
-  if (u0)
-    k_stage<T, P, true><<<grid, kBlock, smem, s>>>(u, u0, out, geo.d_loc, geo.d_halo,
-                                                   geo.d_halo_cnt, geo.d_chunk, gscale, stride,
-                                                   nrec, sel.list, sel.adv, tb, c);
-  else
-    k_stage<T, P, false><<<grid, kBlock, smem, s>>>(u, u0, out, geo.d_loc, geo.d_halo,
-                                                    geo.d_halo_cnt, geo.d_chunk, gscale, stride,
-                                                    nrec, sel.list, sel.adv, tb, c);
+  const bool full = c.pen != (T)0 || c.wallA;
+  auto go = [&](auto kern) {
+    kern<<<grid, kBlock, smem, s>>>(u, u0, out, geo.d_loc, geo.d_halo, geo.d_halo_cnt,
+                                    geo.d_chunk, geo.d_grange, gscale, stride, nrec, sel.list,
+                                    sel.adv, tb, c);
+  };
+  if (kSR && c.sround) {
+    if (u0) full ? go(k_stage<T, P, true, kSR, true>) : go(k_stage<T, P, true, kSR, false>);
+    else full ? go(k_stage<T, P, false, kSR, true>) : go(k_stage<T, P, false, kSR, false>);
+  } else {
+    if (u0) full ? go(k_stage<T, P, true, false, true>) : go(k_stage<T, P, true, false, false>);
+    else full ? go(k_stage<T, P, false, false, true>) : go(k_stage<T, P, false, false, false>);
+  }
   return cudaGetLastError();
 }
 

@@ -48,6 +48,9 @@ def test_host_only_calls(L):
     h = ctypes.c_void_p()
     bad = dg.default_config(p=9)
     assert L.dg_create(ctypes.byref(bad), ctypes.byref(h)) == dg.DG_EINVAL
+    assert cfg.rounding == dg.DG_ROUND_STOCHASTIC
+    bad = dg.default_config(rounding=5)
+    assert L.dg_create(ctypes.byref(bad), ctypes.byref(h)) == dg.DG_EINVAL
     bad = dg.default_config(cfl_safety=1.5)
     assert L.dg_create(ctypes.byref(bad), ctypes.byref(h)) == dg.DG_EINVAL
     assert L.dg_create(None, ctypes.byref(h)) == dg.DG_EINVAL
