@@ -236,6 +236,14 @@ int dg_step(dg_ctx *ctx, int nsteps, double dt);
  * fixed-window path.  Errors: DG_EINVAL (negative or non-finite r_factor). */
 int dg_set_growing_window(dg_ctx *ctx, double r_factor);
 
+/* Test hook (no counterpart in the paper): the n-th device allocation of the
+ * library from now on (0 = the next one, in any context) fails as if the
+ * device were out of memory; -1 disarms.  Calls that hit it return
+ * DG_ENOMEM and leave their context as it was before the call (no geometry
+ * or no sources), so it can be used again or destroyed.  Errors: DG_EINVAL
+ * (n < -1). */
+int dg_debug_fail_alloc(int n);
+
 /* Advance from the current t to Delta in N = ceil((Delta - t)/dt_max) equal
  * steps, then check the moments: DG_ENONFINITE on NaN/Inf, DG_EUNSTABLE when
  * the L1 norm of any density grew above twice its start value.  Delta >= t. */

@@ -93,6 +93,7 @@ EXPORTS = {
     "dg_rasterize_disks": (_I, [_DP, _DP, _DP, _I, _D, _I, _P]),
     "dg_basis_tables": (_I, [_I, _I, _DP, _DP, _DP, _DP]),
     "dg_set_growing_window": (_I, [_P, _D]),
+    "dg_debug_fail_alloc": (_I, [_I]),
     # learned surrogate (include/dgsurrogate.h)
     "sg_create": (_I, [_I, ctypes.c_ulonglong, _I, ctypes.POINTER(_P)]),
     "sg_destroy": (None, [_P]),

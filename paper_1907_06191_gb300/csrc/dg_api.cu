@@ -11,9 +11,29 @@
 #include <string>
 #include <vector>
 
+#include <atomic>
+
 #include "dg_internal.h"
 
 using namespace dg;
+
+namespace dg {
+
+// countdown to an injected allocation failure; -1 = none armed
+static std::atomic<long long> g_fail_alloc{-1};
+
+cudaError_t dev_alloc(void **p, size_t bytes) {
+  long long n = g_fail_alloc.load();
+  while (n >= 0 && !g_fail_alloc.compare_exchange_weak(n, n - 1)) {
+  }
+  if (n == 0) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+}  // namespace dg
 
 struct dg_ctx {
   Ctx c;
@@ -31,7 +51,8 @@ int fail(dg_ctx *ctx, int code, const std::string &msg) {
 }
 
 int cuda_fail(dg_ctx *ctx, cudaError_t e, const char *what) {
-  return fail(ctx, DG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return fail(ctx, e == cudaErrorMemoryAllocation ? DG_ENOMEM : DG_ECUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
 }
 
 #define CK(expr, what)                                   \
@@ -119,6 +140,7 @@ cudaError_t rk3_step(Ctx &c, double dt, cudaStream_t s, const ChunkSel &sel = Ch
 
 int run_steps_fixed(dg_ctx *ctx, int nsteps, double dt) {
   Ctx &c = ctx->c;
+  TraceRange trace("RK3 steps");
   c.gw_synced = false;  // arrays 1 and 2 now hold stage values everywhere
   int left = nsteps;
   if (left >= kGraphChunk) {
@@ -155,6 +177,7 @@ int run_steps_fixed(dg_ctx *ctx, int nsteps, double dt) {
 // its geometry's start-point box, chunks ordered by their nearest element.
 int prepare_window(dg_ctx *ctx) {
   Ctx &c = ctx->c;
+  TraceRange trace("growing window tables");
   const int G = c.geo.G();
   const long long n = c.geo.n_pad, nch = c.geo.n_chunks();
   std::vector<double> box((size_t)4 * G);
@@ -168,13 +191,20 @@ int prepare_window(dg_ctx *ctx) {
       b[2] = std::min(b[2], y); b[3] = std::max(b[3], y);
     }
   }
-  if (!c.d_gw_d2) {
-    CK(cudaMalloc(&c.d_gw_d2, sizeof(double) * (size_t)n), "window allocation");
-    CK(cudaMalloc(&c.d_gw_adv, (size_t)n), "window allocation");
-    CK(cudaMalloc(&c.d_gw_order, sizeof(int) * (size_t)nch), "window allocation");
-  }
   double *d_box = nullptr;
-  CK(cudaMalloc(&d_box, sizeof(double) * box.size()), "window allocation");
+  {
+    cudaError_t e = cudaSuccess;
+    if (!c.d_gw_d2) {
+      e = dev_alloc(&c.d_gw_d2, sizeof(double) * (size_t)n);
+      if (e == cudaSuccess) e = dev_alloc(&c.d_gw_adv, (size_t)n);
+      if (e == cudaSuccess) e = dev_alloc(&c.d_gw_order, sizeof(int) * (size_t)nch);
+    }
+    if (e == cudaSuccess) e = dev_alloc(&d_box, sizeof(double) * box.size());
+    if (e != cudaSuccess) {
+      free_window(c);
+      return cuda_fail(ctx, e, "window allocation");
+    }
+  }
   std::vector<double> d2((size_t)n);
   cudaError_t e = cudaMemcpyAsync(d_box, box.data(), sizeof(double) * box.size(),
                                   cudaMemcpyHostToDevice, c.stream);
@@ -211,6 +241,7 @@ int prepare_window(dg_ctx *ctx) {
 // values in arrays 1 and 2, so launched chunks read their halos correctly.
 int run_steps_window(dg_ctx *ctx, int nsteps, double dt, double t0) {
   Ctx &c = ctx->c;
+  TraceRange trace("RK3 steps (growing window)");
   if (!c.gw_ready) {
     const int r = prepare_window(ctx);
     if (r != DG_OK) return r;
@@ -255,21 +286,23 @@ int run_steps(dg_ctx *ctx, int nsteps, double dt, double t0) {
 
 int compute_moments(dg_ctx *ctx, double *d_dst) {
   Ctx &c = ctx->c;
+  TraceRange trace("moments");
   CK(launch_moments(c, state_array(c, 0), c.d_part, d_dst, c.stream), "moments");
   return DG_OK;
 }
 
 int ensure_rho(dg_ctx *ctx) {
   Ctx &c = ctx->c;
+  TraceRange trace("spectral radius (power iteration)");
   if (c.have_rho) return DG_OK;
   if (!c.have_geo) return fail(ctx, DG_ESTATE, "no geometry");
   const size_t nv = (size_t)c.geo.n_pad * c.np();
   double *v = nullptr, *w = nullptr, *res = nullptr, *part = nullptr;
   auto cleanup = [&]() { cudaFree(v); cudaFree(w); cudaFree(res); cudaFree(part); };
   cudaError_t e;
-  if ((e = cudaMalloc(&v, nv * 8)) != cudaSuccess || (e = cudaMalloc(&w, nv * 8)) != cudaSuccess ||
-      (e = cudaMalloc(&res, 8 * kMomFields)) != cudaSuccess ||
-      (e = cudaMalloc(&part, 8 * kMomFields * (size_t)kMomBlocks)) != cudaSuccess) {
+  if ((e = dev_alloc(&v, nv * 8)) != cudaSuccess || (e = dev_alloc(&w, nv * 8)) != cudaSuccess ||
+      (e = dev_alloc(&res, 8 * kMomFields)) != cudaSuccess ||
+      (e = dev_alloc(&part, 8 * kMomFields * (size_t)kMomBlocks)) != cudaSuccess) {
     cleanup();
     return fail(ctx, DG_ENOMEM, std::string("power iteration buffers: ") + cudaGetErrorString(e));
   }
@@ -313,6 +346,7 @@ int check_config(const dg_config *cfg, std::string &why) {
 
 int set_parts(dg_ctx *ctx, const std::vector<PartSpec> &parts) {
   Ctx &c = ctx->c;
+  TraceRange trace("geometry upload");
   free_state(c);
   c.have_geo = false;
   c.have_rho = false;
@@ -357,6 +391,7 @@ PartSpec disk_part(const double *cx, const double *cy, const double *r, int nd, 
 // xy holds m start points for each geometry: [G][m][2].
 int set_sources_impl(dg_ctx *ctx, const double *xy, int m) {
   Ctx &c = ctx->c;
+  TraceRange trace("start densities");
   if (!c.have_geo) return fail(ctx, DG_ESTATE, "dg_set_sources before a geometry");
   if (!xy || m < 1 || m > 65535) return fail(ctx, DG_EINVAL, "need 1 <= m <= 65535 start points");
   const int G = c.geo.G();
@@ -382,22 +417,32 @@ int set_sources_impl(dg_ctx *ctx, const double *xy, int m) {
   if (!reuse) {
     free_state(c);
     const size_t need = state_bytes_for(c, m);
+    // a failed allocation leaves the context without sources, as before the call
+#define SK(expr, what)                            \
+  do {                                            \
+    const cudaError_t _e = (expr);                \
+    if (_e != cudaSuccess) {                      \
+      free_state(c);                              \
+      return cuda_fail(ctx, _e, what);            \
+    }                                             \
+  } while (0)
     if (c.bound_ptr) {
       if (c.bound_bytes < need) return fail(ctx, DG_EINVAL, "bound state buffer too small");
       c.d_state = c.bound_ptr;
       c.state_owned = false;
     } else {
-      CK(cudaMalloc(&c.d_state, need), "state allocation");
       c.state_owned = true;
+      SK(dev_alloc(&c.d_state, need), "state allocation");
     }
     c.state_bytes = need;
     c.m = m;
-    CK(cudaMalloc(&c.d_src, sizeof(double) * 2 * nd), "source allocation");
-    CK(cudaMalloc(&c.d_srel, sizeof(float4) * nd), "source allocation");
-    CK(cudaMalloc(&c.d_mom, sizeof(double) * kMomFields * nd), "moment allocation");
-    CK(cudaMalloc(&c.d_mom0, sizeof(double) * kMomFields * nd), "moment allocation");
-    CK(cudaMalloc(&c.d_part, sizeof(double) * kMomFields * moment_blocks(G) * nd), "partial allocation");
-    CK(cudaMalloc(&c.d_out, sizeof(double) * (kCovOut + 1) * G), "output allocation");
+    SK(dev_alloc(&c.d_src, sizeof(double) * 2 * nd), "source allocation");
+    SK(dev_alloc(&c.d_srel, sizeof(float4) * nd), "source allocation");
+    SK(dev_alloc(&c.d_mom, sizeof(double) * kMomFields * nd), "moment allocation");
+    SK(dev_alloc(&c.d_mom0, sizeof(double) * kMomFields * nd), "moment allocation");
+    SK(dev_alloc(&c.d_part, sizeof(double) * kMomFields * moment_blocks(G) * nd), "partial allocation");
+    SK(dev_alloc(&c.d_out, sizeof(double) * (kCovOut + 1) * G), "output allocation");
+#undef SK
   }
   c.src.assign(xy, xy + 2 * nd);
   c.gw_ready = false;
@@ -414,6 +459,7 @@ int set_sources_impl(dg_ctx *ctx, const double *xy, int m) {
 
 int check_growth(dg_ctx *ctx) {
   Ctx &c = ctx->c;
+  TraceRange trace("stability check");
   const int nd = c.m * c.geo.G();
   std::vector<double> mom((size_t)nd * kMomFields), mom0((size_t)nd * kMomFields);
   int r = compute_moments(ctx, c.d_mom);
@@ -583,8 +629,8 @@ int dg_rasterize_disks(const double *cx, const double *cy, const double *r, int 
   const int nd = ndisks > 0 ? ndisks : 1;
   double *d = nullptr;
   uint8_t *m = nullptr;
-  if (cudaMalloc(&d, sizeof(double) * 3 * nd) != cudaSuccess) return DG_ENOMEM;
-  if (cudaMalloc(&m, (size_t)npix * npix) != cudaSuccess) {
+  if (dev_alloc(&d, sizeof(double) * 3 * nd) != cudaSuccess) return DG_ENOMEM;
+  if (dev_alloc(&m, (size_t)npix * npix) != cudaSuccess) {
     cudaFree(d);
     return DG_ENOMEM;
   }
@@ -660,6 +706,12 @@ int dg_set_sources(dg_ctx *ctx, const double *xy, int m) {
   } catch (const std::bad_alloc &) {
     return fail(ctx, DG_ENOMEM, "host allocation");
   }
+}
+
+int dg_debug_fail_alloc(int n) {
+  if (n < -1) return DG_EINVAL;
+  g_fail_alloc.store(n);
+  return DG_OK;
 }
 
 int dg_set_growing_window(dg_ctx *ctx, double r_factor) {
@@ -770,7 +822,7 @@ int dg_ls_residual(dg_ctx *ctx, double *out) {
   const int G = c.geo.G();
   CK(launch_covariance(c.d_mom, c.d_mom0, c.m, G, c.d_out, c.stream), "covariance");
   double *d_res = nullptr;
-  CK(cudaMalloc(&d_res, sizeof(double) * kMomFields * (size_t)c.m * G), "residual buffer");
+  CK(dev_alloc(&d_res, sizeof(double) * kMomFields * (size_t)c.m * G), "residual buffer");
   double *d_ls = c.d_out + (size_t)kCovOut * G;  // G slots after the covariance outputs
   cudaError_t e = launch_ls_residual(c, state_array(c, 0), c.d_out, c.d_part, d_res, d_ls, c.stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_ls, sizeof(double) * G, cudaMemcpyDeviceToHost, c.stream);
@@ -798,7 +850,7 @@ int dg_mixture_covariance(dg_ctx *ctx, const double *mom, const double *mom0, in
       h[((size_t)m + s) * kMomFields + f] = mom0[s * 6 + f];
     }
   double *d = nullptr;
-  CK(cudaMalloc(&d, sizeof(double) * (h.size() + kCovOut)), "moment buffer");
+  CK(dev_alloc(&d, sizeof(double) * (h.size() + kCovOut)), "moment buffer");
   double out[5];
   cudaError_t e = cudaMemcpyAsync(d, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, c.stream);
   double *dout = d + h.size();
@@ -846,7 +898,7 @@ int dg_get_nodes(dg_ctx *ctx, double *host) {
   CK(cudaSetDevice(c.device), "set device");
   const size_t nd = (size_t)c.m * c.geo.nx * c.geo.ny * c.np();
   double *d = nullptr;
-  CK(cudaMalloc(&d, nd * 8), "dense buffer");
+  CK(dev_alloc(&d, nd * 8), "dense buffer");
   cudaError_t e = cudaMemsetAsync(d, 0, nd * 8, c.stream);
   if (e == cudaSuccess) e = launch_nodes_to_dense(c, state_array(c, 0), d, c.stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(host, d, nd * 8, cudaMemcpyDeviceToHost, c.stream);
@@ -865,7 +917,7 @@ int dg_set_nodes(dg_ctx *ctx, const double *host) {
   c.gw_synced = false;
   const size_t nd = (size_t)c.m * c.geo.nx * c.geo.ny * c.np();
   double *d = nullptr;
-  CK(cudaMalloc(&d, nd * 8), "dense buffer");
+  CK(dev_alloc(&d, nd * 8), "dense buffer");
   cudaError_t e = cudaMemcpyAsync(d, host, nd * 8, cudaMemcpyHostToDevice, c.stream);
   if (e == cudaSuccess) e = launch_dense_to_nodes(c, d, state_array(c, 0), c.stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);

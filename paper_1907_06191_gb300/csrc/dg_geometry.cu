@@ -260,7 +260,7 @@ struct Tmp {
   }
   template <typename X>
   cudaError_t alloc(X **p, size_t n) {
-    cudaError_t e = cudaMalloc(p, sizeof(X) * (n ? n : 1));
+    cudaError_t e = dev_alloc(p, sizeof(X) * (n ? n : 1));
     if (e == cudaSuccess) ptrs.push_back(*p);
     return e;
   }
@@ -301,8 +301,8 @@ int build_geometry(Geometry &geo, const std::vector<PartSpec> &specs, int period
     free_geometry(geo);
     return DG_EINVAL;
   }
-  GK(cudaMalloc(&geo.d_mask, (size_t)dense), "mask allocation", DG_ENOMEM);
-  GK(cudaMalloc(&geo.d_cidx, sizeof(int) * (size_t)dense), "index map allocation", DG_ENOMEM);
+  GK(dev_alloc(&geo.d_mask, (size_t)dense), "mask allocation", DG_ENOMEM);
+  GK(dev_alloc(&geo.d_cidx, sizeof(int) * (size_t)dense), "index map allocation", DG_ENOMEM);
   int max_nd = 1;
   for (const PartSpec &q : specs) max_nd = std::max(max_nd, q.nd);
   double *d_disk = nullptr;
@@ -361,8 +361,8 @@ int build_geometry(Geometry &geo, const std::vector<PartSpec> &specs, int period
   long long active = 0;
   for (const GeoPart &p : geo.parts) active += p.n_active;
   geo.n_active = active;
-  GK(cudaMalloc(&geo.d_nb, sizeof(int4) * (size_t)elems), "neighbour table allocation", DG_ENOMEM);
-  GK(cudaMalloc(&geo.d_exy, sizeof(int2) * (size_t)elems), "coordinate allocation", DG_ENOMEM);
+  GK(dev_alloc(&geo.d_nb, sizeof(int4) * (size_t)elems), "neighbour table allocation", DG_ENOMEM);
+  GK(dev_alloc(&geo.d_exy, sizeof(int2) * (size_t)elems), "coordinate allocation", DG_ENOMEM);
   const int4 pad = make_int4(kEdge, kEdge, kEdge, kEdge);
   k_fill_int4<<<(unsigned)((elems + 255) / 256), 256, 0, s>>>(geo.d_nb, elems, pad);
   cudaMemsetAsync(geo.d_exy, 0, sizeof(int2) * (size_t)elems, s);
@@ -406,11 +406,11 @@ int build_geometry(Geometry &geo, const std::vector<PartSpec> &specs, int period
     gsd[g] = 1.0 / (J * J);
     grange[g] = make_int2((int)p.off, (int)p.n_active);
   }
-  GK(cudaMalloc(&geo.d_chunk, sizeof(int2) * (size_t)nch), "chunk table allocation", DG_ENOMEM);
-  GK(cudaMalloc(&geo.d_gpar, sizeof(double4) * G), "parameter allocation", DG_ENOMEM);
-  GK(cudaMalloc(&geo.d_gscale_f, sizeof(float) * G), "parameter allocation", DG_ENOMEM);
-  GK(cudaMalloc(&geo.d_gscale_d, sizeof(double) * G), "parameter allocation", DG_ENOMEM);
-  GK(cudaMalloc(&geo.d_grange, sizeof(int2) * G), "parameter allocation", DG_ENOMEM);
+  GK(dev_alloc(&geo.d_chunk, sizeof(int2) * (size_t)nch), "chunk table allocation", DG_ENOMEM);
+  GK(dev_alloc(&geo.d_gpar, sizeof(double4) * G), "parameter allocation", DG_ENOMEM);
+  GK(dev_alloc(&geo.d_gscale_f, sizeof(float) * G), "parameter allocation", DG_ENOMEM);
+  GK(dev_alloc(&geo.d_gscale_d, sizeof(double) * G), "parameter allocation", DG_ENOMEM);
+  GK(dev_alloc(&geo.d_grange, sizeof(int2) * G), "parameter allocation", DG_ENOMEM);
   GK(cudaMemcpyAsync(geo.d_chunk, chunk.data(), sizeof(int2) * chunk.size(), cudaMemcpyHostToDevice, s), "copy", DG_ECUDA);
   GK(cudaMemcpyAsync(geo.d_gpar, gpar.data(), sizeof(double4) * G, cudaMemcpyHostToDevice, s), "copy", DG_ECUDA);
   GK(cudaMemcpyAsync(geo.d_gscale_f, gsf.data(), sizeof(float) * G, cudaMemcpyHostToDevice, s), "copy", DG_ECUDA);
@@ -418,9 +418,9 @@ int build_geometry(Geometry &geo, const std::vector<PartSpec> &specs, int period
   GK(cudaMemcpyAsync(geo.d_grange, grange.data(), sizeof(int2) * G, cudaMemcpyHostToDevice, s), "copy", DG_ECUDA);
   // halo lists of every chunk
   int hmax = 0;
-  GK(cudaMalloc(&geo.d_loc, sizeof(int4) * (size_t)elems), "halo table allocation", DG_ENOMEM);
-  GK(cudaMalloc(&geo.d_halo, sizeof(int2) * (size_t)nch * kHaloCap), "halo table allocation", DG_ENOMEM);
-  GK(cudaMalloc(&geo.d_halo_cnt, sizeof(int) * ((size_t)nch + 1)), "halo table allocation", DG_ENOMEM);
+  GK(dev_alloc(&geo.d_loc, sizeof(int4) * (size_t)elems), "halo table allocation", DG_ENOMEM);
+  GK(dev_alloc(&geo.d_halo, sizeof(int2) * (size_t)nch * kHaloCap), "halo table allocation", DG_ENOMEM);
+  GK(dev_alloc(&geo.d_halo_cnt, sizeof(int) * ((size_t)nch + 1)), "halo table allocation", DG_ENOMEM);
   k_halo<<<(unsigned)nch, kBlock, 0, s>>>(geo.d_nb, geo.d_chunk, geo.d_loc, geo.d_halo, geo.d_halo_cnt);
   k_max_int<<<1, 256, 0, s>>>(geo.d_halo_cnt, (int)nch, geo.d_halo_cnt + nch);
   GK(cudaMemcpyAsync(&hmax, geo.d_halo_cnt + nch, sizeof(int), cudaMemcpyDeviceToHost, s), "halo table", DG_ECUDA);

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -10,6 +11,36 @@
 #include "../../include/dgsigma.h"
 
 namespace dg {
+
+// NVTX range in the "dgsigma" domain for the lifetime of the object (a no-op
+// unless a profiler is attached): geometry upload, start densities, stepping,
+// moments.
+inline nvtxDomainHandle_t trace_domain() {
+  static const nvtxDomainHandle_t d = nvtxDomainCreateA("dgsigma");
+  return d;
+}
+struct TraceRange {
+  explicit TraceRange(const char *what) {
+    nvtxEventAttributes_t a = {};
+    a.version = NVTX_VERSION;
+    a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+    a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+    a.message.ascii = what;
+    nvtxDomainRangePushEx(trace_domain(), &a);
+  }
+  ~TraceRange() { nvtxDomainRangePop(trace_domain()); }
+  TraceRange(const TraceRange &) = delete;
+  TraceRange &operator=(const TraceRange &) = delete;
+};
+
+// Every device allocation of the library goes through dev_alloc.  A test can
+// make the n-th call from now fail as if the device were out of memory
+// (dg_debug_fail_alloc), to exercise the error paths without a GPU fault.
+cudaError_t dev_alloc(void **p, size_t bytes);
+template <typename X>
+cudaError_t dev_alloc(X **p, size_t bytes) {
+  return dev_alloc(reinterpret_cast<void **>(p), bytes);
+}
 
 constexpr int kMaxP = 5;
 constexpr int kMaxN = kMaxP + 1;

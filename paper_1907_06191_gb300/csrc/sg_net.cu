@@ -20,6 +20,10 @@
 
 #include "../../include/dgsigma.h"
 
+namespace dg {
+cudaError_t dev_alloc(void **p, size_t bytes);  // the library's allocator (dg_api.cu)
+}
+
 namespace sg {
 
 constexpr int kRes = 128;
@@ -444,7 +448,7 @@ int sg_create(int max_batch, unsigned long long seed, int device, sg_net **out) 
   fill(n.f2_w, kHidden);
   bool ok = true;
   auto al = [&](auto **ptr, size_t bytes) {
-    if (ok && cudaMalloc(ptr, bytes) != cudaSuccess) ok = false;
+    if (ok && dg::dev_alloc(reinterpret_cast<void **>(ptr), bytes) != cudaSuccess) ok = false;
   };
   al(&n.p, off * 4); al(&n.g, off * 4); al(&n.m, off * 4); al(&n.v, off * 4); al(&n.pbf, off * 2);
   for (int l = 0; l <= kLayers; ++l) al(&n.x[l], (size_t)max_batch * kCh[l] * res_of(l) * res_of(l) * 2);
