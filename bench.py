@@ -41,6 +41,19 @@ import dginputs  # noqa: E402
 
 METRIC = "DoF-steps/s"
 BYTES_PER_DOF_STEP = {"f32": 32, "f64": 64}   # 8 state accesses per RK step
+# pixel triangles: per stage the q pass reads u and writes q (2 values per DoF),
+# the divergence pass reads q, u (and u0 in stages 2, 3) and writes the result:
+# 3 + 4 + 3 + 5 + 3 + 5 = 23 accesses per RK step
+BYTES_PER_DOF_STEP_TRI = {"f32": 92, "f64": 184}
+
+
+def flops_per_dof_step_tri(p: int) -> float:
+    """Dense element matrices per pixel and stage: G (4 N^2 FMAs per pass),
+    the liftings (6 N (p+1) per pass) and the normal products (12 N), over
+    the 2 N DoF of a pixel, 2 flops per FMA, 3 stages."""
+    N = (p + 1) * (p + 2) // 2
+    fma_pixel = 8 * N * N + 12 * N * (p + 1) + 12 * N
+    return 3 * 2 * fma_pixel / (2 * N)
 
 
 def flops_per_dof_step(p: int) -> float:
@@ -394,6 +407,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--element", default="square", choices=["square", "triangle"],
+                    help="square GLL elements or the paper's pixel triangles (p <= 3)")
     ap.add_argument("--rounding", default="stochastic", choices=["stochastic", "nearest"],
                     help="rounding of the FP32 state (library default: stochastic)")
     ap.add_argument("--rk", type=int, default=20, help="RK3 steps per bench step")
@@ -454,7 +469,11 @@ def main():
                                    margin=w.h)
     prec = dg.DG_FP32 if args.precision == "f32" else dg.DG_FP64
     rnd = dg.DG_ROUND_STOCHASTIC if args.rounding == "stochastic" else dg.DG_ROUND_NEAREST
-    s = dg.DGSolver(p=w.p, precision=prec, D=w.D, sigma0=w.sigma0, device=dev, rounding=rnd)
+    tri = args.element == "triangle"
+    if tri:
+        w.p = min(w.p, 3)
+    s = dg.DGSolver(p=w.p, precision=prec, D=w.D, sigma0=w.sigma0, device=dev, rounding=rnd,
+                    element=dg.DG_ELEMENT_TRIANGLE if tri else dg.DG_ELEMENT_SQUARE)
     s.set_geometry_disks(w.disks.cx, w.disks.cy, w.disks.r, w.L, w.n_cell, w.tiles)
     stream = torch.cuda.Stream(device=dev)
     s.set_stream(stream.cuda_stream)
@@ -502,17 +521,18 @@ def main():
     e1.record(stream)
     e1.synchronize()
     stage_ms = e0.elapsed_time(e1) / (3 * R)
-    bytes_per_launch = BYTES_PER_DOF_STEP[args.precision] * dof / 3.0
+    bytes_per_launch = (BYTES_PER_DOF_STEP_TRI if tri else BYTES_PER_DOF_STEP)[args.precision] * dof / 3.0
     peaks, src = _peaks()
     achieved = bytes_per_launch / (stage_ms * 1e-3) / 1e9
     rec = _traffic_record(os.path.join(ROOT, "paper_1907_06191_gb300", "csrc", "dg_stage.cuh"))
     traffic = None
-    if rec and rec.get("precision") == args.precision and rec.get("p") == w.p:
+    if rec and rec.get("precision") == args.precision and rec.get("p") == w.p and not tri:
         traffic = rec["dram_bytes_per_launch_per_dof"] * dof
     if args.precision == "f64":
         # FP64 is bound by the FP64 pipe (2 FMA/clk/SM): 152 x 2 x 2 x 2.07 GHz
         peak_f64 = 152 * 2 * 2 * 2.07e9 / 1e12
-        roofline = {"bound": "alu", "achieved": flops_per_dof_step(w.p) * dof / 3.0
+        fl = flops_per_dof_step_tri(w.p) if tri else flops_per_dof_step(w.p)
+        roofline = {"bound": "alu", "achieved": fl * dof / 3.0
                     / (stage_ms * 1e-3) / 1e12, "peak": peak_f64, "unit": "TFLOP/s",
                     "traffic": traffic, "peak_source": "derived from unit counts and max clock"}
         roofline["frac"] = roofline["achieved"] / peak_f64
@@ -549,7 +569,7 @@ def main():
         res = {}
         for pr in (dg.DG_FP32, dg.DG_FP64):
             with dg.DGSolver(p=w.p, precision=pr, D=w.D, sigma0=w.sigma0, device=dev,
-                             rounding=rnd) as c2:
+                             rounding=rnd, element=s.cfg.element) as c2:
                 c2.set_geometry_disks(w.disks.cx, w.disks.cy, w.disks.r, w.L, w.n_cell, w.tiles)
                 c2.set_sources(w.sources[:nd])
                 t0 = time.perf_counter()
@@ -569,7 +589,8 @@ def main():
         s.step(R, dt)
         sig32 = s.covariance()[0]
         mom32 = s.moments()
-        with dg.DGSolver(p=w.p, precision=dg.DG_FP64, D=w.D, sigma0=w.sigma0, device=dev) as d64:
+        with dg.DGSolver(p=w.p, precision=dg.DG_FP64, D=w.D, sigma0=w.sigma0, device=dev,
+                         element=s.cfg.element) as d64:
             d64.set_geometry_disks(w.disks.cx, w.disks.cy, w.disks.r, w.L, w.n_cell, w.tiles)
             d64.set_sources(w.sources)
             d64.step(R, dt)
@@ -620,7 +641,8 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.precision, "data": "synthetic",
-        "config": {"workload": w.name, "p": w.p,
+        "config": {"workload": w.name + ("_triangles" if tri else ""), "p": w.p,
+                   "element": args.element,
                    "rounding": args.rounding if args.precision == "f32" else "nearest",
                    "window_elements": inf.nx * inf.ny,
                    "active_elements": inf.n_active, "densities_per_gpu": m,

@@ -80,6 +80,19 @@ extern "C" {
 #define DG_ROUND_NEAREST 0
 #define DG_ROUND_STOCHASTIC 1
 
+/* Element of the mesh of pixels.  DG_ELEMENT_SQUARE: one square element per
+ * pixel with the tensor-product GLL basis of order p (collocated, diagonal
+ * mass; p = 1..5).  DG_ELEMENT_TRIANGLE: the paper's own element (Sec. 3.3),
+ * each pixel split by its lower-left to upper-right diagonal into two
+ * triangles with the Lagrange basis of order p on equispaced nodes and
+ * exactly integrated (full) mass matrices (p = 1..3, eta = 0); node k of a
+ * triangle is the reference point (i/p, j/p) with k running over j = 0..p,
+ * then i = 0..p-j; a pixel holds the lower-right triangle's nodes, then the
+ * upper-left one's.  Both use the fluxes of Sec. 3.2 and the same walls,
+ * edges, stepping and moments (integrated exactly on the triangles). */
+#define DG_ELEMENT_SQUARE 0
+#define DG_ELEMENT_TRIANGLE 1
+
 typedef struct dg_config {
   int p;             /* polynomial order of the GLL basis, 1..5 (Eq. 8) */
   int precision;     /* DG_FP64 or DG_FP32 */
@@ -93,6 +106,7 @@ typedef struct dg_config {
   int power_iters;   /* power iterations for rho(L); 0 selects 200 */
   int device;        /* CUDA device ordinal; -1 = the calling thread's current */
   int rounding;      /* DG_ROUND_STOCHASTIC or DG_ROUND_NEAREST (FP32 state) */
+  int element;       /* DG_ELEMENT_SQUARE or DG_ELEMENT_TRIANGLE */
 } dg_config;
 
 typedef struct dg_ctx dg_ctx;
@@ -189,6 +203,18 @@ int dg_rasterize_disks(const double *cx, const double *cy, const double *r, int 
  * summing to exactly zero.  Any output pointer may be NULL.  Errors:
  * DG_EINVAL (p outside 1..5 or an unknown precision). */
 int dg_basis_tables(int p, int precision, double *xi, double *w, double *D, double *D2);
+
+/* The tables of the triangle elements (DG_ELEMENT_TRIANGLE, Sec. 3.3, Eq. 7
+ * integrated exactly) for order p = 1..3, N = (p+1)(p+2)/2.  Host only.
+ * r[N], s[N]: reference nodes.  G[2][2][N][N]: for triangle t (0 = lower
+ * right, 1 = upper left) and component c (x, y), h q_c = G[t][c] u +
+ * sum_e n_ec Lf[t][e] uhat_e, i.e. G = -M^-1 (d(r,s)/dx Sr^T + ...) with M,
+ * Sr, Ss the reference mass and derivative matrices.  Lf[2][3][N][p+1]: the
+ * lifting of edge values (edge length / h times M^-1 times the edge mass
+ * matrix on the edge's nodes).  mono[6][N]: integrals of r^a s^b N_j for
+ * (a, b) = (0,0), (1,0), (0,1), (2,0), (1,1), (0,2).  Any pointer may be
+ * NULL.  Errors: DG_EINVAL (p outside 1..3). */
+int dg_triangle_tables(int p, double *r, double *s, double *G, double *Lf, double *mono);
 
 /* Copy the element mask as built, [ny][nx] bytes (1 = in the mesh); the
  * first geometry of a batch. */

@@ -21,7 +21,7 @@ __all__ = [
     "DG_OK", "DG_EINVAL", "DG_ENOMEM", "DG_ECUDA", "DG_EUNSTABLE", "DG_ENONFINITE",
     "DG_ETIMEOUT", "DG_ESTATE", "DG_FP64", "DG_FP32", "DG_WALL_REMOVED",
     "DG_WALL_PAPER", "DG_BC_ABSORBING", "DG_BC_PERIODIC", "DG_ROUND_NEAREST",
-    "DG_ROUND_STOCHASTIC", "DgError", "dg_config",
+    "DG_ROUND_STOCHASTIC", "DG_ELEMENT_SQUARE", "DG_ELEMENT_TRIANGLE", "DgError", "dg_config",
     "dg_info", "lib", "library_path", "DGSolver", "EXPORTS",
 ]
 
@@ -31,6 +31,7 @@ DG_FP64, DG_FP32 = 0, 1
 DG_WALL_REMOVED, DG_WALL_PAPER = 0, 1
 DG_BC_ABSORBING, DG_BC_PERIODIC = 0, 1
 DG_ROUND_NEAREST, DG_ROUND_STOCHASTIC = 0, 1
+DG_ELEMENT_SQUARE, DG_ELEMENT_TRIANGLE = 0, 1
 
 
 class dg_config(ctypes.Structure):
@@ -39,7 +40,7 @@ class dg_config(ctypes.Structure):
                 ("eta", ctypes.c_double), ("cfl_safety", ctypes.c_double),
                 ("wall_mode", ctypes.c_int), ("boundary", ctypes.c_int),
                 ("power_iters", ctypes.c_int), ("device", ctypes.c_int),
-                ("rounding", ctypes.c_int)]
+                ("rounding", ctypes.c_int), ("element", ctypes.c_int)]
 
 
 class dg_info(ctypes.Structure):
@@ -94,6 +95,7 @@ EXPORTS = {
     "dg_basis_tables": (_I, [_I, _I, _DP, _DP, _DP, _DP]),
     "dg_set_growing_window": (_I, [_P, _D]),
     "dg_debug_fail_alloc": (_I, [_I]),
+    "dg_triangle_tables": (_I, [_I, _DP, _DP, _DP, _DP, _DP]),
     # learned surrogate (include/dgsurrogate.h)
     "sg_create": (_I, [_I, ctypes.c_ulonglong, _I, ctypes.POINTER(_P)]),
     "sg_destroy": (None, [_P]),
@@ -233,8 +235,7 @@ class DGSolver:
     def get_elements_batch(self, idx) -> np.ndarray:
         """Node values [k, n, n] of elements idx = [(geometry, source, ex, ey), ...]."""
         idx = np.ascontiguousarray(idx, dtype=np.int32).reshape(-1, 4)
-        n = self.info().p + 1
-        out = np.zeros((idx.shape[0], n, n))
+        out = np.zeros((idx.shape[0],) + self.node_shape())
         self._ck(self._L.dg_get_elements_batch(self.ctx, idx.ctypes.data, idx.shape[0], _dp(out)),
                  "dg_get_elements_batch")
         return out
@@ -297,24 +298,29 @@ class DGSolver:
     def apply_operator(self):
         self._ck(self._L.dg_apply_operator(self.ctx), "dg_apply_operator")
 
+    def node_shape(self):
+        """Nodes of one element: (p+1, p+1) for squares (j, i), (2, N) for the
+        two triangles of a pixel."""
+        inf = self.info()
+        if self.cfg.element == DG_ELEMENT_TRIANGLE:
+            return (2, inf.n_nodes // 2)
+        return (inf.p + 1, inf.p + 1)
+
     def get_nodes(self) -> np.ndarray:
         inf = self.info()
-        n = inf.p + 1
-        out = np.zeros((inf.m, inf.ny, inf.nx, n, n))
+        out = np.zeros((inf.m, inf.ny, inf.nx) + self.node_shape())
         self._ck(self._L.dg_get_nodes(self.ctx, _dp(out)), "dg_get_nodes")
         return out
 
     def set_nodes(self, u):
         inf = self.info()
-        n = inf.p + 1
-        u = _f64(u).reshape(inf.m, inf.ny, inf.nx, n, n)
+        u = _f64(u).reshape((inf.m, inf.ny, inf.nx) + self.node_shape())
         self._ck(self._L.dg_set_nodes(self.ctx, _dp(u)), "dg_set_nodes")
 
     def get_elements(self, idx) -> np.ndarray:
         """Node values [k, n, n] of elements idx = [(source, ex, ey), ...]."""
         idx = np.ascontiguousarray(idx, dtype=np.int32).reshape(-1, 3)
-        n = self.info().p + 1
-        out = np.zeros((idx.shape[0], n, n))
+        out = np.zeros((idx.shape[0],) + self.node_shape())
         self._ck(self._L.dg_get_elements(self.ctx, idx.ctypes.data, idx.shape[0], _dp(out)),
                  "dg_get_elements")
         return out
@@ -373,6 +379,17 @@ def basis_tables(p: int, precision: int = DG_FP64):
     if rc != DG_OK:
         raise DgError(rc, f"dg_basis_tables: {lib().dg_strerror(rc).decode()}")
     return xi, w, D, D2
+
+
+def triangle_tables(p: int):
+    """(r, s, G, Lf, mono) of the triangle elements as the kernels use them."""
+    n = (p + 1) * (p + 2) // 2
+    r, s_, G = np.zeros(n), np.zeros(n), np.zeros((2, 2, n, n))
+    Lf, mono = np.zeros((2, 3, n, p + 1)), np.zeros((6, n))
+    rc = lib().dg_triangle_tables(int(p), _dp(r), _dp(s_), _dp(G), _dp(Lf), _dp(mono))
+    if rc != DG_OK:
+        raise DgError(rc, f"dg_triangle_tables: {lib().dg_strerror(rc).decode()}")
+    return r, s_, G, Lf, mono
 
 
 class Surrogate:

@@ -90,6 +90,8 @@ void free_state(Ctx &c) {
   cudaFree(c.d_mom0);
   cudaFree(c.d_part);
   cudaFree(c.d_out);
+  cudaFree(c.d_q);
+  c.d_q = nullptr;
   c.d_src = c.d_mom = c.d_mom0 = c.d_part = c.d_out = nullptr;
   free_window(c);
   c.m = 0;
@@ -126,13 +128,23 @@ cudaError_t rk3_step(Ctx &c, double dt, cudaStream_t s, const ChunkSel &sel = Ch
   for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
     if (c.cfg.precision == DG_FP64) {
       StageCoef<double> sc{co[k][0], co[k][1], co[k][2], pen, wallA};
-      e = launch_stage_f64(c.cfg.p, (const double *)in[k], (const double *)base[k],
-                           (double *)outp[k], c.geo, st, c.m, c.gll, sc, s, sel);
+      if (c.triangles())
+        e = launch_tri_stage_f64(c.cfg.p, (const double *)in[k], (const double *)base[k],
+                                 (double *)outp[k], (double *)c.d_q, c.geo, st, c.m, c.tri, sc,
+                                 s, sel);
+      else
+        e = launch_stage_f64(c.cfg.p, (const double *)in[k], (const double *)base[k],
+                             (double *)outp[k], c.geo, st, c.m, c.gll, sc, s, sel);
     } else {
       StageCoef<float> sc{(float)co[k][0], (float)co[k][1], (float)co[k][2], (float)pen,
                           wallA, c.cfg.rounding == DG_ROUND_STOCHASTIC};
-      e = launch_stage_f32(c.cfg.p, (const float *)in[k], (const float *)base[k],
-                           (float *)outp[k], c.geo, st, c.m, c.gll, sc, s, sel);
+      if (c.triangles())
+        e = launch_tri_stage_f32(c.cfg.p, (const float *)in[k], (const float *)base[k],
+                                 (float *)outp[k], (float *)c.d_q, c.geo, st, c.m, c.tri, sc,
+                                 s, sel);
+      else
+        e = launch_stage_f32(c.cfg.p, (const float *)in[k], (const float *)base[k],
+                             (float *)outp[k], c.geo, st, c.m, c.gll, sc, s, sel);
     }
   }
   return e;
@@ -297,12 +309,13 @@ int ensure_rho(dg_ctx *ctx) {
   if (c.have_rho) return DG_OK;
   if (!c.have_geo) return fail(ctx, DG_ESTATE, "no geometry");
   const size_t nv = (size_t)c.geo.n_pad * c.np();
-  double *v = nullptr, *w = nullptr, *res = nullptr, *part = nullptr;
-  auto cleanup = [&]() { cudaFree(v); cudaFree(w); cudaFree(res); cudaFree(part); };
+  double *v = nullptr, *w = nullptr, *res = nullptr, *part = nullptr, *qb = nullptr;
+  auto cleanup = [&]() { cudaFree(v); cudaFree(w); cudaFree(res); cudaFree(part); cudaFree(qb); };
   cudaError_t e;
   if ((e = dev_alloc(&v, nv * 8)) != cudaSuccess || (e = dev_alloc(&w, nv * 8)) != cudaSuccess ||
       (e = dev_alloc(&res, 8 * kMomFields)) != cudaSuccess ||
-      (e = dev_alloc(&part, 8 * kMomFields * (size_t)kMomBlocks)) != cudaSuccess) {
+      (e = dev_alloc(&part, 8 * kMomFields * (size_t)kMomBlocks)) != cudaSuccess ||
+      (c.triangles() && (e = dev_alloc(&qb, nv * 2 * 8)) != cudaSuccess)) {
     cleanup();
     return fail(ctx, DG_ENOMEM, std::string("power iteration buffers: ") + cudaGetErrorString(e));
   }
@@ -314,7 +327,11 @@ int ensure_rho(dg_ctx *ctx) {
   if (e == cudaSuccess) e = launch_wnorm2(c, v, part, res, c.stream);
   if (e == cudaSuccess) e = launch_scale_by_rnorm(c, v, res, v, c.stream);
   for (int it = 0; it < iters && e == cudaSuccess; ++it) {
-    e = launch_stage_f64(c.cfg.p, v, nullptr, w, c.geo, c.geo.n_pad, 1, c.gll, sc, c.stream);
+    if (c.triangles())
+      e = launch_tri_stage_f64(c.cfg.p, v, nullptr, w, qb, c.geo, c.geo.n_pad, 1, c.tri, sc,
+                               c.stream);
+    else
+      e = launch_stage_f64(c.cfg.p, v, nullptr, w, c.geo, c.geo.n_pad, 1, c.gll, sc, c.stream);
     if (e == cudaSuccess) e = launch_wnorm2(c, w, part, res, c.stream);
     if (e == cudaSuccess && it + 1 < iters) e = launch_scale_by_rnorm(c, w, res, v, c.stream);
   }
@@ -341,6 +358,11 @@ int check_config(const dg_config *cfg, std::string &why) {
   if (cfg->boundary != DG_BC_ABSORBING && cfg->boundary != DG_BC_PERIODIC) { why = "bad boundary"; return DG_EINVAL; }
   if (cfg->power_iters < 0) { why = "power_iters must be >= 0"; return DG_EINVAL; }
   if (cfg->rounding != DG_ROUND_NEAREST && cfg->rounding != DG_ROUND_STOCHASTIC) { why = "bad rounding"; return DG_EINVAL; }
+  if (cfg->element != DG_ELEMENT_SQUARE && cfg->element != DG_ELEMENT_TRIANGLE) { why = "bad element"; return DG_EINVAL; }
+  if (cfg->element == DG_ELEMENT_TRIANGLE && (cfg->p > kTriMaxP || cfg->eta != 0.0)) {
+    why = "triangles take p = 1..3 and eta = 0";
+    return DG_EINVAL;
+  }
   return DG_OK;
 }
 
@@ -442,6 +464,8 @@ int set_sources_impl(dg_ctx *ctx, const double *xy, int m) {
     SK(dev_alloc(&c.d_mom0, sizeof(double) * kMomFields * nd), "moment allocation");
     SK(dev_alloc(&c.d_part, sizeof(double) * kMomFields * moment_blocks(G) * nd), "partial allocation");
     SK(dev_alloc(&c.d_out, sizeof(double) * (kCovOut + 1) * G), "output allocation");
+    if (c.triangles())
+      SK(dev_alloc(&c.d_q, (size_t)m * c.field_elems() * 2 * c.esize()), "q allocation");
 #undef SK
   }
   c.src.assign(xy, xy + 2 * nd);
@@ -495,6 +519,7 @@ void dg_config_default(dg_config *cfg) {
   cfg->power_iters = 200;
   cfg->device = -1;
   cfg->rounding = DG_ROUND_STOCHASTIC;
+  cfg->element = DG_ELEMENT_SQUARE;
 }
 
 const char *dg_strerror(int code) {
@@ -536,7 +561,7 @@ int dg_create(const dg_config *cfg, dg_ctx **out) {
     return DG_ECUDA;
   }
   c.stream = c.own_stream;
-  if (!gll_tables(c.cfg.p, &c.gll)) {
+  if (!gll_tables(c.cfg.p, &c.gll) || (c.triangles() && !tri_tables(c.cfg.p, &c.tri))) {
     cudaStreamDestroy(c.own_stream);
     delete ctx;
     return DG_EINVAL;
@@ -663,6 +688,28 @@ int dg_basis_tables(int p, int precision, double *xi, double *w, double *D, doub
     if (D) D[k] = precision == DG_FP32 ? (double)g.Df[k] : g.D[k];
     if (D2) D2[k] = precision == DG_FP32 ? (double)g.D2f[k] : g.D2[k];
   }
+  return DG_OK;
+}
+
+int dg_triangle_tables(int p, double *r, double *s, double *G, double *Lf, double *mono) {
+  TriRef t;
+  if (!tri_tables(p, &t)) return DG_EINVAL;
+  const int N = t.N, NE = p + 1;
+  for (int k = 0; k < N; ++k) {
+    if (r) r[k] = t.r[k];
+    if (s) s[k] = t.s[k];
+  }
+  for (int o = 0; o < 2; ++o) {
+    for (int c = 0; c < 2; ++c)
+      for (int k = 0; k < N * N; ++k)
+        if (G) G[((size_t)o * 2 + c) * N * N + k] = t.G[o][c][k];
+    for (int e = 0; e < 3; ++e)
+      for (int k = 0; k < N * NE; ++k)
+        if (Lf) Lf[((size_t)o * 3 + e) * N * NE + k] = t.Lf[o][e][k];
+  }
+  for (int q = 0; q < 6; ++q)
+    for (int k = 0; k < N; ++k)
+      if (mono) mono[q * N + k] = t.mono[q][k];
   return DG_OK;
 }
 
@@ -816,6 +863,7 @@ int dg_ls_residual(dg_ctx *ctx, double *out) {
   if (!ctx || !out) return DG_EINVAL;
   Ctx &c = ctx->c;
   if (c.m < 1) return fail(ctx, DG_ESTATE, "no sources");
+  if (c.triangles()) return fail(ctx, DG_EINVAL, "the least-squares residual is defined on the square elements");
   CK(cudaSetDevice(c.device), "set device");
   int r = compute_moments(ctx, c.d_mom);
   if (r != DG_OK) return r;
@@ -875,7 +923,17 @@ int dg_apply_operator(dg_ctx *ctx) {
   void *U0 = state_array(c, 0), *U1 = state_array(c, 1);
   c.gw_synced = false;
   cudaError_t e;
-  if (c.cfg.precision == DG_FP64) {
+  if (c.triangles()) {
+    if (c.cfg.precision == DG_FP64) {
+      StageCoef<double> sc{0.0, 0.0, kc, pen, wallA};
+      e = launch_tri_stage_f64(c.cfg.p, (const double *)U0, nullptr, (double *)U1, (double *)c.d_q,
+                               c.geo, c.geo.n_pad, c.m, c.tri, sc, c.stream);
+    } else {
+      StageCoef<float> sc{0.0f, 0.0f, (float)kc, (float)pen, wallA};
+      e = launch_tri_stage_f32(c.cfg.p, (const float *)U0, nullptr, (float *)U1, (float *)c.d_q,
+                               c.geo, c.geo.n_pad, c.m, c.tri, sc, c.stream);
+    }
+  } else if (c.cfg.precision == DG_FP64) {
     StageCoef<double> sc{0.0, 0.0, kc, pen, wallA};
     e = launch_stage_f64(c.cfg.p, (const double *)U0, nullptr, (double *)U1, c.geo, c.geo.n_pad, c.m,
                          c.gll, sc, c.stream);

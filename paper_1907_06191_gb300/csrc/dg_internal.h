@@ -68,6 +68,32 @@ struct Gll {
   float Df[kMaxN * kMaxN], D2f[kMaxN * kMaxN];
 };
 bool gll_tables(int p, Gll *g);
+
+// Triangles of the pixel split (Sec. 3.3): each pixel of side h is cut by its
+// lower-left to upper-right diagonal into A (vertices (x0,y0), (x1,y0),
+// (x1,y1)) and B ((x0,y0), (x1,y1), (x0,y1)), both affine images of the
+// reference triangle (0,0), (1,0), (0,1) with Jacobian determinant h^2.  The
+// basis is the Lagrange P_p basis on the equispaced nodes (i/p, j/p), node
+// index k running over j = 0..p, then i = 0..p - j; edges e0 (0,0)->(1,0),
+// e1 (1,0)->(0,1), e2 (0,1)->(0,0).  A pixel's four faces are A e1 (east),
+// B e2 (west), B e1 (north) and A e0 (south); A e2 and B e0 are the diagonal.
+constexpr int kTriMaxP = 3;
+constexpr int kTriN = (kTriMaxP + 1) * (kTriMaxP + 2) / 2;
+struct TriRef {
+  int p = 0, N = 0;
+  double r[kTriN], s[kTriN];                  // reference nodes
+  // q = (1/h) [G_t u + sum_e n_te Lf_te uhat_e] on triangle t (0 = A, 1 = B):
+  // G_t,x = -M^-1 (rx Sr^T + sx Ss^T), (rx, ry, sx, sy) the inverse Jacobian
+  // times h; Lf_te = (|e|/h) M^-1 E_e, E_e the edge mass matrix placed on the
+  // edge's nodes.  The divergence uses the same matrices.
+  double G[2][2][kTriN * kTriN];
+  double Lf[2][3][kTriN * (kTriMaxP + 1)];
+  double nrm[2][3][2];                         // outward unit normals
+  // int over the reference triangle of r^a s^b N_j for
+  // (a, b) = (0,0), (1,0), (0,1), (2,0), (1,1), (0,2)
+  double mono[6][kTriN];
+};
+bool tri_tables(int p, TriRef *t);
 double rk3_real_axis_limit();
 
 // Operator scalars of one stage launch: out = u0 + beta (u - u0) + gamma s_g R
@@ -150,6 +176,7 @@ struct Ctx {
   cudaStream_t stream = nullptr;
   std::string last_error;
   Gll gll;
+  TriRef tri;                     // element == DG_ELEMENT_TRIANGLE
   Geometry geo;
   bool have_geo = false;
 
@@ -173,6 +200,7 @@ struct Ctx {
   double *d_mom0 = nullptr;       // [m][7] start moments
   double *d_part = nullptr;       // [m][kMomBlocks][7] partial sums
   double *d_out = nullptr;        // [G][kCovOut] covariance results
+  void *d_q = nullptr;            // triangles: q of one stage, [m][n_pad][4 N]
   size_t part_elems = 0;
 
   // Growing window (off while gw_r <= 0): in each group of up to 64 steps an
@@ -194,7 +222,11 @@ struct Ctx {
   int graph_steps = 0;
   cudaStream_t graph_stream = nullptr;
 
-  int np() const { return (cfg.p + 1) * (cfg.p + 1); }
+  bool triangles() const { return cfg.element == DG_ELEMENT_TRIANGLE; }
+  // nodes per pixel element
+  int np() const {
+    return triangles() ? (cfg.p + 1) * (cfg.p + 2) : (cfg.p + 1) * (cfg.p + 1);
+  }
   size_t esize() const { return cfg.precision == DG_FP64 ? 8 : 4; }
   size_t field_elems() const { return (size_t)geo.n_pad * np(); }  // one density slot
 };
@@ -218,6 +250,16 @@ cudaError_t launch_stage_f32(int p, const float *u, const float *u0, float *out,
                              const Geometry &geo, long long stride, int m,
                              const Gll &g, const StageCoef<float> &c, cudaStream_t s,
                              const ChunkSel &sel = ChunkSel{});
+
+// One stage on the pixel triangles (two passes through qbuf, [m][n_pad][4 N]).
+cudaError_t launch_tri_stage_f64(int p, const double *u, const double *u0, double *out,
+                                 double *qbuf, const Geometry &geo, long long stride, int m,
+                                 const TriRef &ref, const StageCoef<double> &c, cudaStream_t s,
+                                 const ChunkSel &sel = ChunkSel{});
+cudaError_t launch_tri_stage_f32(int p, const float *u, const float *u0, float *out,
+                                 float *qbuf, const Geometry &geo, long long stride, int m,
+                                 const TriRef &ref, const StageCoef<float> &c, cudaStream_t s,
+                                 const ChunkSel &sel = ChunkSel{});
 
 cudaError_t build_mask_disks(const double *d_cx, const double *d_cy, const double *d_r,
                              int nd, double L, int n_cell, int tiles, uint8_t *d_mask,

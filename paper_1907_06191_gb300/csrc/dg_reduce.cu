@@ -356,10 +356,9 @@ __global__ void k_ls_mean(const double *__restrict__ res, int m, int G, double *
 }
 
 // ---- node layout conversion ------------------------------------------------
-template <typename T, int P>
+template <typename T, int NP>
 __global__ void k_to_dense(const int2 *__restrict__ exy, long long nA, long long stride,
                            int nx, int ny, const T *__restrict__ u, double *__restrict__ d) {
-  constexpr int NP = (P + 1) * (P + 1);
   const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= nA) return;
   const int s = blockIdx.y;
@@ -370,10 +369,9 @@ __global__ void k_to_dense(const int2 *__restrict__ exy, long long nA, long long
   for (int k = 0; k < NP; ++k) dst[k] = (double)src[k];
 }
 
-template <typename T, int P>
+template <typename T, int NP>
 __global__ void k_from_dense(const int2 *__restrict__ exy, long long nA, long long stride,
                              int nx, int ny, const double *__restrict__ d, T *__restrict__ u) {
-  constexpr int NP = (P + 1) * (P + 1);
   const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= nA) return;
   const int s = blockIdx.y;
@@ -436,6 +434,140 @@ __global__ void k_scale_rnorm(long long nvals, const double *__restrict__ in,
   out[t] = in[t] * res[1];
 }
 
+// ---- pixel triangles (Sec. 3.3) ----------------------------------------------------
+// Node (r, s) of the reference triangle sits at (x0 + h (ex + r + s), y0 + h (ey + s))
+// in triangle A and at (x0 + h (ex + r), y0 + h (ey + r + s)) in triangle B.
+struct TriGeo {
+  double r[kTriN], s[kTriN];
+  double mono[6][kTriN];  // int r^a s^b N_j over the reference triangle
+  int N;
+};
+
+static TriGeo tri_geo(const Ctx &c) {
+  TriGeo g;
+  g.N = c.tri.N;
+  for (int j = 0; j < c.tri.N; ++j) {
+    g.r[j] = c.tri.r[j];
+    g.s[j] = c.tri.s[j];
+    for (int q = 0; q < 6; ++q) g.mono[q][j] = c.tri.mono[q][j];
+  }
+  return g;
+}
+
+// Gaussian start densities at the triangle nodes (FP64 per node; pixels whose
+// nearest point lies beyond 40 sigma0 are set to zero without evaluating).
+template <typename T, int NPX>
+__global__ void k_init_tri(const int2 *__restrict__ exy, const int2 *__restrict__ chunk_tab,
+                           const double4 *__restrict__ gpar, long long stride, int m,
+                           const double *__restrict__ src, double cnorm, double inv2s2,
+                           double cut2, const TriGeo g, T *__restrict__ u) {
+  const long long a = (long long)blockIdx.x * kBlock + threadIdx.x;
+  const int s = blockIdx.y;
+  const int2 ci = chunk_tab[blockIdx.x];
+  T *dst = u + ((size_t)s * stride + a) * NPX;
+  if ((int)threadIdx.x >= ci.x) {
+#pragma unroll
+    for (int k = 0; k < NPX; ++k) dst[k] = (T)0;
+    return;
+  }
+  const double4 gp = gpar[ci.y];
+  const double xs = src[2 * ((size_t)ci.y * m + s)], ys = src[2 * ((size_t)ci.y * m + s) + 1];
+  const int2 e = exy[a];
+  const double px = gp.x + e.x * gp.z, py = gp.y + e.y * gp.z;  // pixel corner
+  const double dx = fmax(fmax(px - xs, xs - (px + gp.z)), 0.0);
+  const double dy = fmax(fmax(py - ys, ys - (py + gp.z)), 0.0);
+  const bool far = dx * dx + dy * dy > cut2;
+  constexpr int N = NPX / 2;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const double ra = g.r[k], sa = g.s[k];
+    const double xa = px + gp.z * (ra + sa) - xs, ya = py + gp.z * sa - ys;
+    const double xb = px + gp.z * ra - xs, yb = py + gp.z * (ra + sa) - ys;
+    dst[k] = far ? (T)0 : (T)(cnorm * exp(-(xa * xa + ya * ya) * inv2s2));
+    dst[N + k] = far ? (T)0 : (T)(cnorm * exp(-(xb * xb + yb * yb) * inv2s2));
+  }
+}
+
+// Exact moments of the piecewise polynomial density: per pixel the integrals
+// of r^a s^b u over each reference triangle, mapped to the pixel's local
+// coordinates (x - x0, y - y0) = h (r + s, s) in A and h (r, r + s) in B and
+// shifted to the start point in FP64.  Field 6 is the mass of |u| at the
+// nodes weighted by the integrals of the basis functions.
+template <typename T, int NPX>
+__global__ void __launch_bounds__(256)
+    k_moments_tri(const int2 *__restrict__ exy, const int2 *__restrict__ grange,
+                  const double4 *__restrict__ gpar, long long stride, int m,
+                  const double *__restrict__ src, const TriGeo g, const T *__restrict__ u,
+                  double *__restrict__ part) {
+  constexpr int N = NPX / 2;
+  const int s = blockIdx.y, gi = blockIdx.z;
+  const int2 rg = grange[gi];
+  const double4 gp = gpar[gi];
+  const double h = gp.z, J = h * h;
+  const double xs = src[2 * ((size_t)gi * m + s)], ys = src[2 * ((size_t)gi * m + s) + 1];
+  double acc[kMomFields] = {0, 0, 0, 0, 0, 0, 0};
+  const T *U = u + (size_t)s * stride * NPX;
+  for (long long k = (long long)blockIdx.x * 256 + threadIdx.x; k < rg.y;
+       k += (long long)gridDim.x * 256) {
+    const long long a = rg.x + k;
+    const int2 e = exy[a];
+    const T *ue = U + (size_t)a * NPX;
+    const double cx = gp.x + e.x * h - xs, cy = gp.y + e.y * h - ys;
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+      double I[6] = {0, 0, 0, 0, 0, 0}, l1 = 0.0;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const double v = (double)ue[o * N + j];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) I[q] += g.mono[q][j] * v;
+        l1 += g.mono[0][j] * fabs(v);
+      }
+      // I: (0,0), (1,0) = r, (0,1) = s, (2,0), (1,1), (0,2)
+      double lx, ly, lxx, lxy, lyy;
+      if (o == 0) {
+        lx = I[1] + I[2]; ly = I[2];
+        lxx = I[3] + 2.0 * I[4] + I[5]; lxy = I[4] + I[5]; lyy = I[5];
+      } else {
+        lx = I[1]; ly = I[1] + I[2];
+        lxx = I[3]; lxy = I[3] + I[4]; lyy = I[3] + 2.0 * I[4] + I[5];
+      }
+      const double m0 = J * I[0], mx = J * h * lx, my = J * h * ly;
+      acc[0] += m0;
+      acc[1] += cx * m0 + mx;
+      acc[2] += cy * m0 + my;
+      acc[3] += cx * cx * m0 + 2.0 * cx * mx + J * h * h * lxx;
+      acc[4] += cx * cy * m0 + cx * my + cy * mx + J * h * h * lxy;
+      acc[5] += cy * cy * m0 + 2.0 * cy * my + J * h * h * lyy;
+      acc[6] += J * l1;
+    }
+  }
+  block_sum7(acc);
+  if (threadIdx.x == 0) {
+    double *o = part + (((size_t)gi * m + s) * gridDim.x + blockIdx.x) * kMomFields;
+#pragma unroll
+    for (int f = 0; f < kMomFields; ++f) o[f] = acc[f];
+  }
+}
+
+// Euclidean norm^2 of an FP64 field (power iteration on triangles).
+__global__ void __launch_bounds__(256)
+    k_norm2(long long nvals, int np, const int2 *__restrict__ chunk_tab,
+            const double *__restrict__ v, double *__restrict__ part) {
+  double acc[kMomFields] = {0, 0, 0, 0, 0, 0, 0};
+  for (long long t = (long long)blockIdx.x * 256 + threadIdx.x; t < nvals;
+       t += (long long)gridDim.x * 256) {
+    const long long a = t / np;
+    if ((int)(a % kBlock) < chunk_tab[a / kBlock].x) acc[0] += v[t] * v[t];
+  }
+  block_sum7(acc);
+  if (threadIdx.x == 0) {
+    double *o = part + (size_t)blockIdx.x * kMomFields;
+#pragma unroll
+    for (int f = 0; f < kMomFields; ++f) o[f] = acc[f];
+  }
+}
+
 // ---- growing window ---------------------------------------------------------------
 // Squared distance from the centre (x0 + (ex + 1/2) h, y0 + (ey + 1/2) h) of
 // every mesh element to its geometry's start-point box; each operation is
@@ -495,11 +627,50 @@ cudaError_t launch_window_flags(const Ctx &c, const double *d2, double r2, uint8
     default: return cudaErrorInvalidValue;         \
   }
 
+// nodes per element: (p+1)^2 for squares, 2 (p+1)(p+2)/2 for pixel triangles
+#define DG_NP_SWITCH(np, CALL)                                     \
+  switch (np) {                                                    \
+    case 4: { constexpr int NN = 4; CALL; } break;                 \
+    case 9: { constexpr int NN = 9; CALL; } break;                 \
+    case 16: { constexpr int NN = 16; CALL; } break;               \
+    case 25: { constexpr int NN = 25; CALL; } break;               \
+    case 36: { constexpr int NN = 36; CALL; } break;               \
+    case 6: { constexpr int NN = 6; CALL; } break;                 \
+    case 12: { constexpr int NN = 12; CALL; } break;               \
+    case 20: { constexpr int NN = 20; CALL; } break;               \
+    default: return cudaErrorInvalidValue;                         \
+  }
+
+// nodes per pixel of the triangle elements, p = 1..3
+#define DG_TRI_SWITCH(np, CALL)                                    \
+  switch (np) {                                                    \
+    case 6: { constexpr int NN = 6; CALL; } break;                 \
+    case 12: { constexpr int NN = 12; CALL; } break;               \
+    case 20: { constexpr int NN = 20; CALL; } break;               \
+    default: return cudaErrorInvalidValue;                         \
+  }
+
 cudaError_t launch_init_sources(const Ctx &c, void *u, cudaStream_t s) {
   const int G = c.geo.G();
   k_src_rel<<<(G * c.m + 127) / 128, 128, 0, s>>>(c.d_src, c.geo.d_grange, c.geo.d_gpar, c.m, G,
                                                    c.d_srel);
   const dim3 grid((unsigned)c.geo.n_chunks(), (unsigned)c.m);
+  if (c.cfg.element == DG_ELEMENT_TRIANGLE) {
+    const TriGeo g = tri_geo(c);
+    const double s2 = c.cfg.sigma0 * c.cfg.sigma0;
+    const double cnorm = 1.0 / (2.0 * M_PI * s2), inv2s2 = 1.0 / (2.0 * s2);
+    const double cut2 = 1600.0 * s2;
+    if (c.cfg.precision == DG_FP64) {
+      DG_TRI_SWITCH(c.np(), (k_init_tri<double, NN><<<grid, kBlock, 0, s>>>(
+                               c.geo.d_exy, c.geo.d_chunk, c.geo.d_gpar, c.geo.n_pad, c.m,
+                               c.d_src, cnorm, inv2s2, cut2, g, (double *)u)));
+    } else {
+      DG_TRI_SWITCH(c.np(), (k_init_tri<float, NN><<<grid, kBlock, 0, s>>>(
+                               c.geo.d_exy, c.geo.d_chunk, c.geo.d_gpar, c.geo.n_pad, c.m,
+                               c.d_src, cnorm, inv2s2, cut2, g, (float *)u)));
+    }
+    return cudaGetLastError();
+  }
   const NodeGeo g = node_geo(c);
   const double s2 = c.cfg.sigma0 * c.cfg.sigma0;
   const double cnorm = 1.0 / (2.0 * M_PI * s2), inv2s2 = 1.0 / (2.0 * s2);
@@ -522,6 +693,20 @@ cudaError_t launch_moments(const Ctx &c, const void *u, double *d_part, double *
   const int G = c.geo.G();
   const int B = moment_blocks(G);
   const dim3 grid((unsigned)B, (unsigned)c.m, (unsigned)G);
+  if (c.cfg.element == DG_ELEMENT_TRIANGLE) {
+    const TriGeo tg = tri_geo(c);
+    if (c.cfg.precision == DG_FP64) {
+      DG_TRI_SWITCH(c.np(), (k_moments_tri<double, NN><<<grid, 256, 0, s>>>(
+                               c.geo.d_exy, c.geo.d_grange, c.geo.d_gpar, c.geo.n_pad, c.m,
+                               c.d_src, tg, (const double *)u, d_part)));
+    } else {
+      DG_TRI_SWITCH(c.np(), (k_moments_tri<float, NN><<<grid, 256, 0, s>>>(
+                               c.geo.d_exy, c.geo.d_grange, c.geo.d_gpar, c.geo.n_pad, c.m,
+                               c.d_src, tg, (const float *)u, d_part)));
+    }
+    k_moments_final<<<(unsigned)(c.m * G), 256, 0, s>>>(d_part, B, d_mom);
+    return cudaGetLastError();
+  }
   const NodeGeo g = node_geo(c);
   if (c.cfg.precision == DG_FP64) {
     DG_P_SWITCH(c.cfg.p, (k_moments<double, PP><<<grid, 256, 0, s>>>(
@@ -568,33 +753,31 @@ cudaError_t launch_nodes_to_dense(const Ctx &c, const void *u, double *d_dense,
   const long long nA = c.geo.parts[0].n_active;
   const dim3 grid((unsigned)((nA + 255) / 256), (unsigned)c.m);
   if (c.cfg.precision == DG_FP64) {
-    DG_P_SWITCH(c.cfg.p, (k_to_dense<double, PP><<<grid, 256, 0, s>>>(
+    DG_NP_SWITCH(c.np(), (k_to_dense<double, NN><<<grid, 256, 0, s>>>(
                              c.geo.d_exy, nA, c.geo.n_pad, c.geo.nx, c.geo.ny,
                              (const double *)u, d_dense)));
   } else {
-    DG_P_SWITCH(c.cfg.p, (k_to_dense<float, PP><<<grid, 256, 0, s>>>(
+    DG_NP_SWITCH(c.np(), (k_to_dense<float, NN><<<grid, 256, 0, s>>>(
                              c.geo.d_exy, nA, c.geo.n_pad, c.geo.nx, c.geo.ny,
                              (const float *)u, d_dense)));
   }
   return cudaGetLastError();
 }
-
 cudaError_t launch_dense_to_nodes(const Ctx &c, const double *d_dense, void *u,
                                   cudaStream_t s) {
   const long long nA = c.geo.parts[0].n_active;
   const dim3 grid((unsigned)((nA + 255) / 256), (unsigned)c.m);
   if (c.cfg.precision == DG_FP64) {
-    DG_P_SWITCH(c.cfg.p, (k_from_dense<double, PP><<<grid, 256, 0, s>>>(
+    DG_NP_SWITCH(c.np(), (k_from_dense<double, NN><<<grid, 256, 0, s>>>(
                              c.geo.d_exy, nA, c.geo.n_pad, c.geo.nx, c.geo.ny, d_dense,
                              (double *)u)));
   } else {
-    DG_P_SWITCH(c.cfg.p, (k_from_dense<float, PP><<<grid, 256, 0, s>>>(
+    DG_NP_SWITCH(c.np(), (k_from_dense<float, NN><<<grid, 256, 0, s>>>(
                              c.geo.d_exy, nA, c.geo.n_pad, c.geo.nx, c.geo.ny, d_dense,
                              (float *)u)));
   }
   return cudaGetLastError();
 }
-
 cudaError_t launch_random_field(const Ctx &c, double *v, unsigned long long seed,
                                 cudaStream_t s) {
   const long long nv = c.geo.n_pad * c.np();
@@ -604,6 +787,11 @@ cudaError_t launch_random_field(const Ctx &c, double *v, unsigned long long seed
 
 cudaError_t launch_wnorm2(const Ctx &c, const double *v, double *d_part, double *d_res,
                           cudaStream_t s) {
+  if (c.cfg.element == DG_ELEMENT_TRIANGLE) {
+    k_norm2<<<kMomBlocks, 256, 0, s>>>(c.geo.n_pad * c.np(), c.np(), c.geo.d_chunk, v, d_part);
+    k_moments_final<<<1, 256, 0, s>>>(d_part, kMomBlocks, d_res);
+    return cudaGetLastError();
+  }
   const NodeGeo g = node_geo(c);
   DG_P_SWITCH(c.cfg.p, (k_wnorm2<PP><<<kMomBlocks, 256, 0, s>>>(c.geo.n_pad, c.geo.d_chunk, v, g,
                                                                  d_part)));

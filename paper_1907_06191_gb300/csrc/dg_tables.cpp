@@ -1,5 +1,6 @@
 // dg_tables.cpp -- GLL nodal basis of order p (Eq. 8 on a tensor-product
 // grid) and the real-axis stability limit of SSP-RK3, in FP64 on the host.
+#include <algorithm>
 #include <cmath>
 
 #include "dg_internal.h"
@@ -176,6 +177,152 @@ bool gll_tables(int p, Gll *g) {
   return true;
 }
 
+
+namespace {
+
+double factorial(int n) {
+  double f = 1.0;
+  for (int k = 2; k <= n; ++k) f *= k;
+  return f;
+}
+
+// integral of r^a s^b over the reference triangle (0,0), (1,0), (0,1)
+double tri_mono(int a, int b) { return factorial(a) * factorial(b) / factorial(a + b + 2); }
+
+// in-place inverse of an n x n row-major matrix (Gauss-Jordan, partial
+// pivoting); false if singular
+bool invert(double *A, int n) {
+  double B[kTriN * kTriN * 2];
+  const int w = 2 * n;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < w; ++j) B[i * w + j] = j < n ? A[i * n + j] : (j - n == i ? 1.0 : 0.0);
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int i = c + 1; i < n; ++i)
+      if (std::fabs(B[i * w + c]) > std::fabs(B[piv * w + c])) piv = i;
+    if (B[piv * w + c] == 0.0) return false;
+    if (piv != c)
+      for (int j = 0; j < w; ++j) std::swap(B[c * w + j], B[piv * w + j]);
+    const double d = B[c * w + c];
+    for (int j = 0; j < w; ++j) B[c * w + j] /= d;
+    for (int i = 0; i < n; ++i) {
+      if (i == c) continue;
+      const double f = B[i * w + c];
+      if (f == 0.0) continue;
+      for (int j = 0; j < w; ++j) B[i * w + j] -= f * B[c * w + j];
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) A[i * n + j] = B[i * w + n + j];
+  return true;
+}
+
+int tri_index(int p, int i, int j) { return j * (p + 1) - j * (j - 1) / 2 + i; }
+
+int tri_edge_node(int p, int e, int t) {
+  if (e == 0) return tri_index(p, t, 0);
+  if (e == 1) return tri_index(p, p - t, t);
+  return tri_index(p, 0, p - t);
+}
+
+}  // namespace
+
+bool tri_tables(int p, TriRef *T) {
+  if (p < 1 || p > kTriMaxP) return false;
+  const int N = (p + 1) * (p + 2) / 2, NE = p + 1;
+  T->p = p;
+  T->N = N;
+  // nodes and monomials r^ea s^eb (a + b <= p)
+  int ea[kTriN], eb[kTriN];
+  {
+    int k = 0;
+    for (int j = 0; j <= p; ++j)
+      for (int i = 0; i + j <= p; ++i, ++k) {
+        T->r[k] = (double)i / p;
+        T->s[k] = (double)j / p;
+      }
+    k = 0;
+    for (int a = 0; a <= p; ++a)
+      for (int b = 0; a + b <= p; ++b, ++k) {
+        ea[k] = a;
+        eb[k] = b;
+      }
+  }
+  // C = V^-1, V[k][m] = r_k^a_m s_k^b_m: basis function j = sum_m C[m][j] mono_m
+  double C[kTriN * kTriN];
+  for (int k = 0; k < N; ++k)
+    for (int m = 0; m < N; ++m) C[k * N + m] = std::pow(T->r[k], ea[m]) * std::pow(T->s[k], eb[m]);
+  if (!invert(C, N)) return false;
+  // exact integrals of products of basis functions and their derivatives
+  double M[kTriN * kTriN], Sr[kTriN * kTriN], Ss[kTriN * kTriN];
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
+      double m = 0.0, sr = 0.0, ss = 0.0;
+      for (int a = 0; a < N; ++a)
+        for (int b = 0; b < N; ++b) {
+          const double cc = C[a * N + i] * C[b * N + j];
+          if (cc == 0.0) continue;
+          m += cc * tri_mono(ea[a] + ea[b], eb[a] + eb[b]);
+          if (ea[b] > 0) sr += cc * ea[b] * tri_mono(ea[a] + ea[b] - 1, eb[a] + eb[b]);
+          if (eb[b] > 0) ss += cc * eb[b] * tri_mono(ea[a] + ea[b], eb[a] + eb[b] - 1);
+        }
+      M[i * N + j] = m;       // int N_i N_j
+      Sr[i * N + j] = sr;     // int N_i dN_j/dr
+      Ss[i * N + j] = ss;
+    }
+  double Mi[kTriN * kTriN];
+  for (int k = 0; k < N * N; ++k) Mi[k] = M[k];
+  if (!invert(Mi, N)) return false;
+  // 1D mass matrix of the equispaced Lagrange basis on [0, 1]
+  double C1[(kTriMaxP + 1) * (kTriMaxP + 1)], E1[(kTriMaxP + 1) * (kTriMaxP + 1)];
+  for (int t = 0; t < NE; ++t)
+    for (int a = 0; a < NE; ++a) C1[t * NE + a] = std::pow((double)t / p, a);
+  if (!invert(C1, NE)) return false;
+  for (int t = 0; t < NE; ++t)
+    for (int u = 0; u < NE; ++u) {
+      double v = 0.0;
+      for (int a = 0; a < NE; ++a)
+        for (int b = 0; b < NE; ++b) v += C1[a * NE + t] * C1[b * NE + u] / (a + b + 1.0);
+      E1[t * NE + u] = v;
+    }
+  // the two triangles of a pixel
+  const double ij[2][4] = {{1.0, -1.0, 0.0, 1.0}, {1.0, 0.0, -1.0, 1.0}};  // rx ry sx sy (x h)
+  const double q = std::sqrt(0.5);
+  const double nr[2][3][2] = {{{0.0, -1.0}, {1.0, 0.0}, {-q, q}}, {{q, -q}, {0.0, 1.0}, {-1.0, 0.0}}};
+  const double len[2][3] = {{1.0, 1.0, std::sqrt(2.0)}, {std::sqrt(2.0), 1.0, 1.0}};
+  for (int t = 0; t < 2; ++t) {
+    const double rx = ij[t][0], ry = ij[t][1], sx = ij[t][2], sy = ij[t][3];
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) {
+        double gx = 0.0, gy = 0.0;
+        for (int k = 0; k < N; ++k) {
+          // (rx Sr^T + sx Ss^T)[k][j] = rx Sr[j][k] + sx Ss[j][k]
+          gx += Mi[i * N + k] * (rx * Sr[j * N + k] + sx * Ss[j * N + k]);
+          gy += Mi[i * N + k] * (ry * Sr[j * N + k] + sy * Ss[j * N + k]);
+        }
+        T->G[t][0][i * N + j] = -gx;
+        T->G[t][1][i * N + j] = -gy;
+      }
+    for (int e = 0; e < 3; ++e) {
+      T->nrm[t][e][0] = nr[t][e][0];
+      T->nrm[t][e][1] = nr[t][e][1];
+      for (int i = 0; i < N; ++i)
+        for (int u = 0; u < NE; ++u) {
+          double v = 0.0;
+          for (int tt = 0; tt < NE; ++tt) v += Mi[i * N + tri_edge_node(p, e, tt)] * E1[tt * NE + u];
+          T->Lf[t][e][i * NE + u] = len[t][e] * v;
+        }
+    }
+  }
+  const int mab[6][2] = {{0, 0}, {1, 0}, {0, 1}, {2, 0}, {1, 1}, {0, 2}};
+  for (int q6 = 0; q6 < 6; ++q6)
+    for (int j = 0; j < N; ++j) {
+      double v = 0.0;
+      for (int m = 0; m < N; ++m) v += C[m * N + j] * tri_mono(mab[q6][0] + ea[m], mab[q6][1] + eb[m]);
+      T->mono[q6][j] = v;
+    }
+  return true;
+}
 
 // SSP-RK3 amplification on the real axis is 1 + z + z^2/2 + z^3/6; the step
 // stays stable for -x3 <= z <= 0 where the polynomial reaches -1 at z = -x3.

@@ -1,0 +1,385 @@
+// dg_tri.cu -- SSP-RK3 stage on the paper's pixel triangles (Sec. 3.3).
+//
+// One thread owns one pixel (its two triangles A and B, 2 N nodal values,
+// N = (p+1)(p+2)/2) of one density.  With a full (non-diagonal) mass matrix
+// the lifted gradient of a neighbour depends on that neighbour's other faces,
+// so the stage runs in two passes:
+//   pass Q: q = grad u with the central flux u_hat = (u^- + u^+)/2 (Eq. 7,
+//           first line), written to a q buffer (4 N values per pixel);
+//   pass R: R = div q with the harmonic-mean flux of Sec. 3.2 (second line),
+//           then out = u0 + beta (u - u0) + gamma R as for the square elements.
+// Both passes use the pixel neighbour tables of the square mesh: a pixel's
+// east / west / north / south faces are the edges A e1 / B e2 / B e1 / A e0,
+// and the diagonal joins A e2 and B e0 inside the pixel.  Matching edges run
+// in opposite directions, so node t of an edge meets node p - t across it.
+// Face records in shared memory carry, per pixel face, the trace of u (pass Q)
+// or of q . n (pass R) at the p + 1 edge nodes.
+#include "dg_internal.h"
+#include "dg_stage.cuh"
+
+namespace dg {
+
+template <int P>
+struct TriShape {
+  static constexpr int N = (P + 1) * (P + 2) / 2, NE = P + 1, NPX = 2 * N;
+  __host__ __device__ static constexpr int idx(int i, int j) { return j * (P + 1) - j * (j - 1) / 2 + i; }
+  __host__ __device__ static constexpr int en(int e, int t) {
+    return e == 0 ? idx(t, 0) : (e == 1 ? idx(P - t, t) : idx(0, P - t));
+  }
+  // pixel face f -> (triangle, edge)
+  __host__ __device__ static constexpr int ftri(int f) { return (f == 0 || f == 3) ? 0 : 1; }
+  __host__ __device__ static constexpr int fedge(int f) { return f == 0 ? 1 : (f == 1 ? 2 : (f == 2 ? 1 : 0)); }
+};
+
+template <typename T, int P>
+struct TriTab {
+  static constexpr int N = TriShape<P>::N, NE = TriShape<P>::NE;
+  T G[2][2][N * N];
+  T Lf[2][3][N * NE];
+  T nrm[2][3][2];
+};
+
+template <typename T, int P>
+TriTab<T, P> make_tri_tab(const TriRef &r) {
+  TriTab<T, P> t;
+  constexpr int N = TriShape<P>::N, NE = TriShape<P>::NE;
+  for (int o = 0; o < 2; ++o) {
+    for (int c = 0; c < 2; ++c)
+      for (int k = 0; k < N * N; ++k) t.G[o][c][k] = (T)r.G[o][c][k];
+    for (int e = 0; e < 3; ++e) {
+      for (int k = 0; k < N * NE; ++k) t.Lf[o][e][k] = (T)r.Lf[o][e][k];
+      t.nrm[o][e][0] = (T)r.nrm[o][e][0];
+      t.nrm[o][e][1] = (T)r.nrm[o][e][1];
+    }
+  }
+  return t;
+}
+
+// y[i] += sum_t L[i*NE + t] v[t]
+template <typename T, int N, int NE>
+__device__ __forceinline__ void lift_add(const T *L, const T (&v)[NE], T s, T (&y)[N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    T a = 0;
+#pragma unroll
+    for (int t = 0; t < NE; ++t) a += L[i * NE + t] * v[t];
+    y[i] += s * a;
+  }
+}
+
+// Shared set-up of both passes: chunk, element, record slots.
+struct TriBlock {
+  int chunk, el, cnt, hcnt, geo;
+  long long a0;
+  bool live;
+  int4 l4;
+};
+
+__device__ __forceinline__ TriBlock tri_block(const int *chunk_list, const int2 *chunk_tab,
+                                              const int4 *loc, const int *halo_cnt) {
+  TriBlock b;
+  b.chunk = chunk_list ? __ldg(chunk_list + blockIdx.x) : (int)blockIdx.x;
+  b.a0 = (long long)b.chunk * kBlock;
+  const int2 ci = __ldg(chunk_tab + b.chunk);
+  b.cnt = ci.x;
+  b.geo = ci.y;
+  b.el = threadIdx.x;
+  b.live = b.el < b.cnt;
+  b.l4 = b.live ? __ldg(loc + b.a0 + b.el) : make_int4(kEdge, kEdge, kEdge, kEdge);
+  b.hcnt = __ldg(halo_cnt + b.chunk);
+  return b;
+}
+
+__device__ __forceinline__ int tri_rec_index(int L, int f, int el, int zero_rec) {
+  return L >= kBlock ? 4 * kBlock + (L - kBlock) : (L >= 0 ? (f ^ 1) * kBlock + L : zero_rec);
+}
+
+// ---- pass Q -------------------------------------------------------------------
+template <typename T, int P>
+__global__ void __launch_bounds__(kBlock, 2)
+    k_tri_q(const T *__restrict__ uin, T *__restrict__ qout, const int4 *__restrict__ loc,
+            const int2 *__restrict__ halo, const int *__restrict__ halo_cnt,
+            const int2 *__restrict__ chunk_tab, long long stride, int nrec,
+            const int *__restrict__ chunk_list, const TriTab<T, P> tb, int wallA) {
+  using S = TriShape<P>;
+  constexpr int N = S::N, NE = S::NE, NPX = S::NPX;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *rec = reinterpret_cast<T *>(smem_raw);
+  const int zero_rec = nrec - 1;
+  const TriBlock b = tri_block(chunk_list, chunk_tab, loc, halo_cnt);
+  const size_t sbase = (size_t)blockIdx.y * (size_t)stride;
+  const T *U = uin + sbase * NPX;
+
+  T u[NPX];
+  if (b.live) {
+    load_elem<T, NPX>(U + (size_t)(b.a0 + b.el) * NPX, u);
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+      for (int t = 0; t < NE; ++t)
+        rec[(f * kBlock + b.el) * NE + t] = u[S::ftri(f) * N + S::en(S::fedge(f), t)];
+  }
+  if (b.el == 0)
+    for (int t = 0; t < NE; ++t) rec[zero_rec * NE + t] = (T)0;
+  for (int h = b.el; h < b.hcnt; h += kBlock) {
+    const int2 q = __ldg(halo + (size_t)b.chunk * kHaloCap + h);
+    T v[NPX];
+    load_elem<T, NPX>(U + (size_t)q.x * NPX, v);
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+      if (q.y == f)
+#pragma unroll
+        for (int t = 0; t < NE; ++t) rec[(4 * kBlock + h) * NE + t] = v[S::ftri(f) * N + S::en(S::fedge(f), t)];
+  }
+  __syncthreads();
+  if (!b.live) return;
+
+  const int lq[4] = {b.l4.x, b.l4.y, b.l4.z, b.l4.w};
+  const T half = (T)0.5;
+  T *Q = qout + (sbase + (size_t)(b.a0 + b.el)) * (4 * N);
+#pragma unroll
+  for (int o = 0; o < 2; ++o) {
+    T qx[N], qy[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      T ax = 0, ay = 0;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        ax += tb.G[o][0][i * N + j] * u[o * N + j];
+        ay += tb.G[o][1][i * N + j] * u[o * N + j];
+      }
+      qx[i] = ax;
+      qy[i] = ay;
+    }
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      T uh[NE];
+      const bool diag = (o == 0 && e == 2) || (o == 1 && e == 0);
+      if (diag) {
+        const int oe = o == 0 ? 0 : 2;  // the other triangle's diagonal edge
+#pragma unroll
+        for (int t = 0; t < NE; ++t)
+          uh[t] = half * (u[o * N + S::en(e, t)] + u[(1 - o) * N + S::en(oe, P - t)]);
+      } else {
+        // the pixel face of this edge
+        const int f = o == 0 ? (e == 1 ? 0 : 3) : (e == 2 ? 1 : 2);
+        const int L = lq[f];
+        const int rn = tri_rec_index(L, f, b.el, zero_rec);
+        const T cp = L >= 0 ? half : (T)0;                                  // weight of u+
+        const T cm = L >= 0 ? half : (L == kWall ? (wallA ? half : (T)1) : (T)0);  // of u-
+#pragma unroll
+        for (int t = 0; t < NE; ++t)
+          uh[t] = cm * u[o * N + S::en(e, t)] + cp * rec[rn * NE + (P - t)];
+      }
+      T lift[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) lift[i] = 0;
+      lift_add<T, N, NE>(tb.Lf[o][e], uh, (T)1, lift);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        qx[i] += tb.nrm[o][e][0] * lift[i];
+        qy[i] += tb.nrm[o][e][1] * lift[i];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      Q[(2 * o) * N + i] = qx[i];
+      Q[(2 * o + 1) * N + i] = qy[i];
+    }
+  }
+}
+
+// ---- pass R + stage update ------------------------------------------------------
+template <typename T, int P, bool HAS_U0, bool SROUND>
+__global__ void __launch_bounds__(kBlock, 2)
+    k_tri_r(const T *__restrict__ qin, const T *__restrict__ uin, const T *u0, T *out,
+            const int4 *__restrict__ loc, const int2 *__restrict__ halo,
+            const int *__restrict__ halo_cnt, const int2 *__restrict__ chunk_tab,
+            const int2 *__restrict__ grange, const T *__restrict__ gscale, long long stride,
+            int nrec, const int *__restrict__ chunk_list, const uint8_t *__restrict__ adv,
+            const TriTab<T, P> tb, const StageCoef<T> c) {
+  using S = TriShape<P>;
+  constexpr int N = S::N, NE = S::NE, NPX = S::NPX;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *rec = reinterpret_cast<T *>(smem_raw);
+  const int zero_rec = nrec - 1;
+  const TriBlock b = tri_block(chunk_list, chunk_tab, loc, halo_cnt);
+  const size_t sbase = (size_t)blockIdx.y * (size_t)stride;
+  const T *Qb = qin + sbase * (4 * N);
+
+  // q . n (own outward normal) at the edge nodes of pixel face f
+  auto qn_face = [&](const T *q, int f, int t) -> T {
+    const int o = S::ftri(f), e = S::fedge(f), k = S::en(e, t);
+    return q[(2 * o) * N + k] * tb.nrm[o][e][0] + q[(2 * o + 1) * N + k] * tb.nrm[o][e][1];
+  };
+  T q[4 * N];
+  if (b.live) {
+    load_elem<T, 4 * N>(Qb + (size_t)(b.a0 + b.el) * (4 * N), q);
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+      for (int t = 0; t < NE; ++t) rec[(f * kBlock + b.el) * NE + t] = qn_face(q, f, t);
+  }
+  if (b.el == 0)
+    for (int t = 0; t < NE; ++t) rec[zero_rec * NE + t] = (T)0;
+  for (int h = b.el; h < b.hcnt; h += kBlock) {
+    const int2 hq = __ldg(halo + (size_t)b.chunk * kHaloCap + h);
+    T v[4 * N];
+    load_elem<T, 4 * N>(Qb + (size_t)hq.x * (4 * N), v);
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+      if (hq.y == f)
+#pragma unroll
+        for (int t = 0; t < NE; ++t) rec[(4 * kBlock + h) * NE + t] = qn_face(v, f, t);
+  }
+  __syncthreads();
+  if (!b.live) return;
+
+  const int lq[4] = {b.l4.x, b.l4.y, b.l4.z, b.l4.w};
+  const T half = (T)0.5;
+  T R[NPX];
+#pragma unroll
+  for (int o = 0; o < 2; ++o) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      T a = 0;
+#pragma unroll
+      for (int j = 0; j < N; ++j)
+        a += tb.G[o][0][i * N + j] * q[(2 * o) * N + j] + tb.G[o][1][i * N + j] * q[(2 * o + 1) * N + j];
+      R[o * N + i] = a;
+    }
+    T r[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) r[i] = R[o * N + i];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      T hn[NE];  // the normal flux h_q . n / k at the edge nodes
+      const bool diag = (o == 0 && e == 2) || (o == 1 && e == 0);
+      if (diag) {
+        const int oe = o == 0 ? 0 : 2;
+#pragma unroll
+        for (int t = 0; t < NE; ++t) {
+          const int k = S::en(e, t), kn = S::en(oe, P - t);
+          const T own = q[(2 * o) * N + k] * tb.nrm[o][e][0] + q[(2 * o + 1) * N + k] * tb.nrm[o][e][1];
+          const T nb = q[(2 * (1 - o)) * N + kn] * tb.nrm[1 - o][oe][0] +
+                       q[(2 * (1 - o) + 1) * N + kn] * tb.nrm[1 - o][oe][1];
+          hn[t] = half * (own - nb);
+        }
+      } else {
+        const int f = o == 0 ? (e == 1 ? 0 : 3) : (e == 2 ? 1 : 2);
+        const int L = lq[f];
+        const int rn = tri_rec_index(L, f, b.el, zero_rec);
+        // interior: (q- . n - q+ . n+) / 2; wall: 0; absorbing edge: q- . n
+        const T cm = L >= 0 ? half : (L == kEdge ? (T)1 : (T)0);
+        const T cp = L >= 0 ? -half : (T)0;
+#pragma unroll
+        for (int t = 0; t < NE; ++t) hn[t] = cm * rec[(f * kBlock + b.el) * NE + t] + cp * rec[rn * NE + (P - t)];
+      }
+      lift_add<T, N, NE>(tb.Lf[o][e], hn, (T)1, r);
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) R[o * N + i] = r[i];
+  }
+
+  // gamma is beta dt D / J^2 with J = h/2 of the square elements: 1/h^2 = gscale / 4
+  T gam = c.gamma * (T)0.25 * __ldg(gscale + b.geo);
+  if (adv != nullptr && __ldg(adv + b.a0 + b.el) == 0) gam = (T)0;
+  const size_t off = (sbase + (size_t)(b.a0 + b.el)) * NPX;
+  T u[NPX], o[NPX];
+  load_elem<T, NPX>(uin + off, u);
+  if constexpr (HAS_U0) load_elem<T, NPX, false>(u0 + off, o);
+  if constexpr (SROUND) {
+    const uint32_t h = fmix32(((uint32_t)(b.a0 + b.el - __ldg(grange + b.geo).x) * (uint32_t)NPX) ^
+                              ((uint32_t)blockIdx.y * 0x632be5abu) ^ __float_as_uint(u[0]) ^
+                              (__float_as_uint(u[1]) * 0x85ebca77u));
+#pragma unroll
+    for (int k = 0; k < NPX; ++k) {
+      const T base = HAS_U0 ? o[k] : c.beta * u[k];
+      const T inc = HAS_U0 ? fmaf(c.beta, u[k] - o[k], gam * R[k]) : gam * R[k];
+      o[k] = add_stochastic(base, inc, h + (uint32_t)k);
+    }
+  } else if constexpr (HAS_U0) {
+#pragma unroll
+    for (int k = 0; k < NPX; ++k) o[k] = o[k] + c.beta * (u[k] - o[k]) + gam * R[k];
+  } else {
+#pragma unroll
+    for (int k = 0; k < NPX; ++k) o[k] = c.beta * u[k] + gam * R[k];
+  }
+  store_elem<T, NPX>(out + off, o);
+}
+
+template <typename T, int P>
+cudaError_t launch_tri_p(const T *u, const T *u0, T *out, T *qbuf, const Geometry &geo,
+                         long long stride, int m, const TriRef &ref, const StageCoef<T> &c,
+                         cudaStream_t s, const ChunkSel &sel) {
+  const long long nch = sel.list ? sel.count : geo.n_chunks();
+  if (geo.n_pad <= 0 || m <= 0 || nch <= 0) return cudaSuccess;
+  if (nch > geo.n_chunks()) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)nch, (unsigned)m);
+  const T *gscale;
+  if constexpr (sizeof(T) == 8) gscale = geo.d_gscale_d;
+  else gscale = geo.d_gscale_f;
+  const TriTab<T, P> tb = make_tri_tab<T, P>(ref);
+  const int nrec = 4 * kBlock + geo.halo_max + 1;
+  const int smem = nrec * TriShape<P>::NE * (int)sizeof(T);
+  static int attr_bytes = 0;
+  constexpr bool kSR = sizeof(T) == 4;
+  if (smem > attr_bytes) {
+    cudaError_t e = cudaSuccess;
+    auto set = [&](auto kern) {
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    };
+    set(k_tri_q<T, P>);
+    set(k_tri_r<T, P, true, false>);
+    set(k_tri_r<T, P, false, false>);
+    if constexpr (kSR) {
+      set(k_tri_r<T, P, true, kSR>);
+      set(k_tri_r<T, P, false, kSR>);
+    }
+    if (e != cudaSuccess) return e;
+    attr_bytes = smem;
+  }
+  k_tri_q<T, P><<<grid, kBlock, smem, s>>>(u, qbuf, geo.d_loc, geo.d_halo, geo.d_halo_cnt,
+                                           geo.d_chunk, stride, nrec, sel.list, tb, c.wallA);
+  auto go = [&](auto kern) {
+    kern<<<grid, kBlock, smem, s>>>(qbuf, u, u0, out, geo.d_loc, geo.d_halo, geo.d_halo_cnt,
+                                    geo.d_chunk, geo.d_grange, gscale, stride, nrec, sel.list,
+                                    sel.adv, tb, c);
+  };
+  if (kSR && c.sround) {
+    if (u0) go(k_tri_r<T, P, true, kSR>);
+    else go(k_tri_r<T, P, false, kSR>);
+  } else {
+    if (u0) go(k_tri_r<T, P, true, false>);
+    else go(k_tri_r<T, P, false, false>);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_tri_any(int p, const T *u, const T *u0, T *out, T *qbuf, const Geometry &geo,
+                           long long stride, int m, const TriRef &ref, const StageCoef<T> &c,
+                           cudaStream_t s, const ChunkSel &sel) {
+  switch (p) {
+    case 1: return launch_tri_p<T, 1>(u, u0, out, qbuf, geo, stride, m, ref, c, s, sel);
+    case 2: return launch_tri_p<T, 2>(u, u0, out, qbuf, geo, stride, m, ref, c, s, sel);
+    case 3: return launch_tri_p<T, 3>(u, u0, out, qbuf, geo, stride, m, ref, c, s, sel);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_tri_stage_f64(int p, const double *u, const double *u0, double *out,
+                                 double *qbuf, const Geometry &geo, long long stride, int m,
+                                 const TriRef &ref, const StageCoef<double> &c, cudaStream_t s,
+                                 const ChunkSel &sel) {
+  return launch_tri_any<double>(p, u, u0, out, qbuf, geo, stride, m, ref, c, s, sel);
+}
+cudaError_t launch_tri_stage_f32(int p, const float *u, const float *u0, float *out,
+                                 float *qbuf, const Geometry &geo, long long stride, int m,
+                                 const TriRef &ref, const StageCoef<float> &c, cudaStream_t s,
+                                 const ChunkSel &sel) {
+  return launch_tri_any<float>(p, u, u0, out, qbuf, geo, stride, m, ref, c, s, sel);
+}
+
+}  // namespace dg

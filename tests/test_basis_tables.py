@@ -84,3 +84,38 @@ def test_bad_arguments(dg):
     assert L.dg_basis_tables(6, dg.DG_FP64, None, None, None, None) == dg.DG_EINVAL
     assert L.dg_basis_tables(3, 7, None, None, None, None) == dg.DG_EINVAL
     assert L.dg_basis_tables(3, dg.DG_FP32, None, None, None, None) == dg.DG_OK
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_triangle_tables_match_the_oracle(dg, p):
+    """The library builds its triangle tables on its own (Gauss-Jordan on the
+    monomial Vandermonde matrix, exact monomial integrals); they must equal
+    the oracle's independently assembled matrices."""
+    from oracle import triangles as T
+    r, s, G, Lf, mono = dg.triangle_tables(p)
+    R = T.ref_matrices(p)
+    Minv = np.linalg.inv(R["M"])
+    X = T.ref_nodes(p)
+    assert np.abs(r - X[:, 0]).max() < 1e-15 and np.abs(s - X[:, 1]).max() < 1e-15
+    EN = T.edge_nodes(p)
+    for t in (0, 1):
+        rx, ry, sx, sy = T._INVJ[t]
+        assert np.abs(G[t, 0] + Minv @ (rx * R["Sr"].T + sx * R["Ss"].T)).max() < 1e-10
+        assert np.abs(G[t, 1] + Minv @ (ry * R["Sr"].T + sy * R["Ss"].T)).max() < 1e-10
+        for e in range(3):
+            ln = T._EDGE[t][e][1]
+            assert np.abs(Lf[t, e] - ln * Minv[:, EN[e]] @ R["E1"]).max() < 1e-10
+    for q, ab in enumerate([(0, 0), (1, 0), (0, 1), (2, 0), (1, 1), (0, 2)]):
+        assert np.abs(mono[q] - R["mono_w"][ab]).max() < 1e-14
+    # exactness the kernels rely on: with u_hat = u on every edge, the weak
+    # gradient G u + sum_e n_e Lf_e u_e is the gradient of u in P_p (h = 1)
+    for t, (x, y) in enumerate(((r + s, s), (r, r + s))):
+        for u, gx, gy in ((x, 1.0, 0.0), (y, 0.0, 1.0), (x * y if p > 1 else x, None, None)):
+            qx, qy = G[t, 0] @ u, G[t, 1] @ u
+            for e in range(3):
+                (nx_, ny_), _ = T._EDGE[t][e]
+                lift = Lf[t, e] @ u[EN[e]]
+                qx, qy = qx + nx_ * lift, qy + ny_ * lift
+            if gx is None:
+                gx, gy = (y, x) if p > 1 else (1.0, 0.0)
+            assert np.abs(qx - gx).max() < 1e-10 and np.abs(qy - gy).max() < 1e-10
