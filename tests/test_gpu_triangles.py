@@ -176,3 +176,33 @@ def test_triangle_arguments():
         s.set_sources(np.array([[1.5, 1.5]]))
         with pytest.raises(dg.DgError):
             s.ls_residual()
+
+
+def test_growing_window_on_triangles():
+    """The growing window works on the triangle path too: a radius that
+    covers the window is the fixed window bit for bit, and with a small
+    radius the held pixels keep their start values bit for bit."""
+    d = dginputs.gamma_disks(3, 4.0, 2.0, 0.15, n=8, min_gap=0.05)
+    src = dginputs.sample_sources(4, d, 2, 0.0, 4.0, margin=0.25)
+    kw = dict(D=1.0, sigma0=0.3)
+    out = []
+    for r in (0.0, 1e3, 2.0):
+        with _solver(2, "f64", **kw) as s:
+            s.set_geometry_disks(d.cx, d.cy, d.r, 4.0, 16, 3)
+            s.set_growing_window(r)
+            s.set_sources(src)
+            init = s.get_nodes()
+            dt, _ = s.query_dt()
+            s.step(90, dt)
+            out.append((init, s.get_nodes(), dt))
+    assert np.array_equal(out[0][1], out[1][1])
+    init, grown, dt = out[2]
+    box = (src[:, 0].min(), src[:, 0].max(), src[:, 1].min(), src[:, 1].max())
+    L, nc, tiles = 4.0, 16, 3
+    mesh = O.Mesh(p=1, active=np.ones((nc * tiles, nc * tiles), np.uint8), h=L / nc,
+                  x0=-(tiles // 2) * L, y0=-(tiles // 2) * L)
+    d2 = O.window_d2(mesh, box)
+    held = d2 > 4.0 * (0.09 + 2.0 * 90 * dt)
+    assert held.sum() > 100
+    assert np.array_equal(grown[:, held], init[:, held])
+    assert not np.array_equal(grown, out[0][1])
