@@ -94,9 +94,15 @@ __device__ __forceinline__ int tri_rec_index(int L, int f, int el, int zero_rec)
   return L >= kBlock ? 4 * kBlock + (L - kBlock) : (L >= 0 ? (f ^ 1) * kBlock + L : zero_rec);
 }
 
+// Blocks of 256 threads per SM the register budget is sized for.
+template <typename T>
+constexpr int tri_min_blocks() { return sizeof(T) == 4 ? 4 : 2; }
+
 // ---- pass Q -------------------------------------------------------------------
+// One triangle at a time: only its N values, its q and the diagonal traces of
+// both triangles are live, which keeps the FP32 kernel within 64 registers.
 template <typename T, int P>
-__global__ void __launch_bounds__(kBlock, 2)
+__global__ void __launch_bounds__(kBlock, tri_min_blocks<T>())
     k_tri_q(const T *__restrict__ uin, T *__restrict__ qout, const int4 *__restrict__ loc,
             const int2 *__restrict__ halo, const int *__restrict__ halo_cnt,
             const int2 *__restrict__ chunk_tab, long long stride, int nrec,
@@ -109,27 +115,35 @@ __global__ void __launch_bounds__(kBlock, 2)
   const TriBlock b = tri_block(chunk_list, chunk_tab, loc, halo_cnt);
   const size_t sbase = (size_t)blockIdx.y * (size_t)stride;
   const T *U = uin + sbase * NPX;
+  const T *Ue = U + (size_t)(b.a0 + b.el) * NPX;
 
-  T u[NPX];
+  T dg[2][NE];  // diagonal traces: A e2 and B e0, each in its own edge order
   if (b.live) {
-    load_elem<T, NPX>(U + (size_t)(b.a0 + b.el) * NPX, u);
 #pragma unroll
-    for (int f = 0; f < 4; ++f)
+    for (int o = 0; o < 2; ++o) {
+      T uo[N];
+      load_elem<T, N>(Ue + o * N, uo);
 #pragma unroll
-      for (int t = 0; t < NE; ++t)
-        rec[(f * kBlock + b.el) * NE + t] = u[S::ftri(f) * N + S::en(S::fedge(f), t)];
+      for (int f = 0; f < 4; ++f)
+        if (S::ftri(f) == o)
+#pragma unroll
+          for (int t = 0; t < NE; ++t) rec[(f * kBlock + b.el) * NE + t] = uo[S::en(S::fedge(f), t)];
+#pragma unroll
+      for (int t = 0; t < NE; ++t) dg[o][t] = uo[S::en(o == 0 ? 2 : 0, t)];
+    }
   }
   if (b.el == 0)
     for (int t = 0; t < NE; ++t) rec[zero_rec * NE + t] = (T)0;
   for (int h = b.el; h < b.hcnt; h += kBlock) {
     const int2 q = __ldg(halo + (size_t)b.chunk * kHaloCap + h);
-    T v[NPX];
-    load_elem<T, NPX>(U + (size_t)q.x * NPX, v);
+    const int o = (q.y == 0 || q.y == 3) ? 0 : 1;  // the triangle that owns the face
+    T v[N];
+    load_elem<T, N>(U + (size_t)q.x * NPX + o * N, v);
 #pragma unroll
     for (int f = 0; f < 4; ++f)
       if (q.y == f)
 #pragma unroll
-        for (int t = 0; t < NE; ++t) rec[(4 * kBlock + h) * NE + t] = v[S::ftri(f) * N + S::en(S::fedge(f), t)];
+        for (int t = 0; t < NE; ++t) rec[(4 * kBlock + h) * NE + t] = v[S::en(S::fedge(f), t)];
   }
   __syncthreads();
   if (!b.live) return;
@@ -137,16 +151,18 @@ __global__ void __launch_bounds__(kBlock, 2)
   const int lq[4] = {b.l4.x, b.l4.y, b.l4.z, b.l4.w};
   const T half = (T)0.5;
   T *Q = qout + (sbase + (size_t)(b.a0 + b.el)) * (4 * N);
-#pragma unroll
+#pragma unroll 1
   for (int o = 0; o < 2; ++o) {
+    T uo[N];
+    load_elem<T, N>(Ue + o * N, uo);
     T qx[N], qy[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       T ax = 0, ay = 0;
 #pragma unroll
       for (int j = 0; j < N; ++j) {
-        ax += tb.G[o][0][i * N + j] * u[o * N + j];
-        ay += tb.G[o][1][i * N + j] * u[o * N + j];
+        ax += tb.G[o][0][i * N + j] * uo[j];
+        ay += tb.G[o][1][i * N + j] * uo[j];
       }
       qx[i] = ax;
       qy[i] = ay;
@@ -156,42 +172,35 @@ __global__ void __launch_bounds__(kBlock, 2)
       T uh[NE];
       const bool diag = (o == 0 && e == 2) || (o == 1 && e == 0);
       if (diag) {
-        const int oe = o == 0 ? 0 : 2;  // the other triangle's diagonal edge
 #pragma unroll
-        for (int t = 0; t < NE; ++t)
-          uh[t] = half * (u[o * N + S::en(e, t)] + u[(1 - o) * N + S::en(oe, P - t)]);
+        for (int t = 0; t < NE; ++t) uh[t] = half * (dg[o][t] + dg[1 - o][P - t]);
       } else {
-        // the pixel face of this edge
         const int f = o == 0 ? (e == 1 ? 0 : 3) : (e == 2 ? 1 : 2);
         const int L = lq[f];
         const int rn = tri_rec_index(L, f, b.el, zero_rec);
-        const T cp = L >= 0 ? half : (T)0;                                  // weight of u+
+        const T cp = L >= 0 ? half : (T)0;                                         // weight of u+
         const T cm = L >= 0 ? half : (L == kWall ? (wallA ? half : (T)1) : (T)0);  // of u-
 #pragma unroll
         for (int t = 0; t < NE; ++t)
-          uh[t] = cm * u[o * N + S::en(e, t)] + cp * rec[rn * NE + (P - t)];
+          uh[t] = cm * uo[S::en(e, t)] + cp * rec[rn * NE + (P - t)];
       }
-      T lift[N];
-#pragma unroll
-      for (int i = 0; i < N; ++i) lift[i] = 0;
-      lift_add<T, N, NE>(tb.Lf[o][e], uh, (T)1, lift);
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        qx[i] += tb.nrm[o][e][0] * lift[i];
-        qy[i] += tb.nrm[o][e][1] * lift[i];
+        T a = 0;
+#pragma unroll
+        for (int t = 0; t < NE; ++t) a += tb.Lf[o][e][i * NE + t] * uh[t];
+        qx[i] += tb.nrm[o][e][0] * a;
+        qy[i] += tb.nrm[o][e][1] * a;
       }
     }
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      Q[(2 * o) * N + i] = qx[i];
-      Q[(2 * o + 1) * N + i] = qy[i];
-    }
+    store_elem<T, N>(Q + (2 * o) * N, qx);
+    store_elem<T, N>(Q + (2 * o + 1) * N, qy);
   }
 }
 
 // ---- pass R + stage update ------------------------------------------------------
 template <typename T, int P, bool HAS_U0, bool SROUND>
-__global__ void __launch_bounds__(kBlock, 2)
+__global__ void __launch_bounds__(kBlock, tri_min_blocks<T>())
     k_tri_r(const T *__restrict__ qin, const T *__restrict__ uin, const T *u0, T *out,
             const int4 *__restrict__ loc, const int2 *__restrict__ halo,
             const int *__restrict__ halo_cnt, const int2 *__restrict__ chunk_tab,
@@ -206,65 +215,75 @@ __global__ void __launch_bounds__(kBlock, 2)
   const TriBlock b = tri_block(chunk_list, chunk_tab, loc, halo_cnt);
   const size_t sbase = (size_t)blockIdx.y * (size_t)stride;
   const T *Qb = qin + sbase * (4 * N);
+  const T *Qe = Qb + (size_t)(b.a0 + b.el) * (4 * N);
 
-  // q . n (own outward normal) at the edge nodes of pixel face f
-  auto qn_face = [&](const T *q, int f, int t) -> T {
-    const int o = S::ftri(f), e = S::fedge(f), k = S::en(e, t);
-    return q[(2 * o) * N + k] * tb.nrm[o][e][0] + q[(2 * o + 1) * N + k] * tb.nrm[o][e][1];
+  // q . n (outward normal of triangle o, edge e) at the edge's node t
+  auto qn = [&](const T (&qx)[N], const T (&qy)[N], int o, int e, int t) -> T {
+    const int k = S::en(e, t);
+    return qx[k] * tb.nrm[o][e][0] + qy[k] * tb.nrm[o][e][1];
   };
-  T q[4 * N];
+  T dg[2][NE];  // q . n on the diagonal of A (e2) and of B (e0)
   if (b.live) {
-    load_elem<T, 4 * N>(Qb + (size_t)(b.a0 + b.el) * (4 * N), q);
 #pragma unroll
-    for (int f = 0; f < 4; ++f)
+    for (int o = 0; o < 2; ++o) {
+      T qx[N], qy[N];
+      load_elem<T, N>(Qe + (2 * o) * N, qx);
+      load_elem<T, N>(Qe + (2 * o + 1) * N, qy);
 #pragma unroll
-      for (int t = 0; t < NE; ++t) rec[(f * kBlock + b.el) * NE + t] = qn_face(q, f, t);
+      for (int f = 0; f < 4; ++f)
+        if (S::ftri(f) == o)
+#pragma unroll
+          for (int t = 0; t < NE; ++t) rec[(f * kBlock + b.el) * NE + t] = qn(qx, qy, o, S::fedge(f), t);
+#pragma unroll
+      for (int t = 0; t < NE; ++t) dg[o][t] = qn(qx, qy, o, o == 0 ? 2 : 0, t);
+    }
   }
   if (b.el == 0)
     for (int t = 0; t < NE; ++t) rec[zero_rec * NE + t] = (T)0;
   for (int h = b.el; h < b.hcnt; h += kBlock) {
     const int2 hq = __ldg(halo + (size_t)b.chunk * kHaloCap + h);
-    T v[4 * N];
-    load_elem<T, 4 * N>(Qb + (size_t)hq.x * (4 * N), v);
+    const int o = (hq.y == 0 || hq.y == 3) ? 0 : 1;
+    T qx[N], qy[N];
+    load_elem<T, N>(Qb + (size_t)hq.x * (4 * N) + (2 * o) * N, qx);
+    load_elem<T, N>(Qb + (size_t)hq.x * (4 * N) + (2 * o + 1) * N, qy);
 #pragma unroll
     for (int f = 0; f < 4; ++f)
       if (hq.y == f)
 #pragma unroll
-        for (int t = 0; t < NE; ++t) rec[(4 * kBlock + h) * NE + t] = qn_face(v, f, t);
+        for (int t = 0; t < NE; ++t) rec[(4 * kBlock + h) * NE + t] = qn(qx, qy, o, S::fedge(f), t);
   }
   __syncthreads();
   if (!b.live) return;
 
   const int lq[4] = {b.l4.x, b.l4.y, b.l4.z, b.l4.w};
   const T half = (T)0.5;
-  T R[NPX];
-#pragma unroll
+  // gamma is beta dt D / J^2 with J = h/2 of the square elements: 1/h^2 = gscale / 4
+  T gam = c.gamma * (T)0.25 * __ldg(gscale + b.geo);
+  if (adv != nullptr && __ldg(adv + b.a0 + b.el) == 0) gam = (T)0;
+  const size_t off = (sbase + (size_t)(b.a0 + b.el)) * NPX;
+  uint32_t hkey = 0;
+#pragma unroll 1
   for (int o = 0; o < 2; ++o) {
+    T R[N];
+    {
+      T qx[N], qy[N];
+      load_elem<T, N>(Qe + (2 * o) * N, qx);
+      load_elem<T, N>(Qe + (2 * o + 1) * N, qy);
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-      T a = 0;
+      for (int i = 0; i < N; ++i) {
+        T a = 0;
 #pragma unroll
-      for (int j = 0; j < N; ++j)
-        a += tb.G[o][0][i * N + j] * q[(2 * o) * N + j] + tb.G[o][1][i * N + j] * q[(2 * o + 1) * N + j];
-      R[o * N + i] = a;
+        for (int j = 0; j < N; ++j) a += tb.G[o][0][i * N + j] * qx[j] + tb.G[o][1][i * N + j] * qy[j];
+        R[i] = a;
+      }
     }
-    T r[N];
-#pragma unroll
-    for (int i = 0; i < N; ++i) r[i] = R[o * N + i];
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
       T hn[NE];  // the normal flux h_q . n / k at the edge nodes
       const bool diag = (o == 0 && e == 2) || (o == 1 && e == 0);
       if (diag) {
-        const int oe = o == 0 ? 0 : 2;
 #pragma unroll
-        for (int t = 0; t < NE; ++t) {
-          const int k = S::en(e, t), kn = S::en(oe, P - t);
-          const T own = q[(2 * o) * N + k] * tb.nrm[o][e][0] + q[(2 * o + 1) * N + k] * tb.nrm[o][e][1];
-          const T nb = q[(2 * (1 - o)) * N + kn] * tb.nrm[1 - o][oe][0] +
-                       q[(2 * (1 - o) + 1) * N + kn] * tb.nrm[1 - o][oe][1];
-          hn[t] = half * (own - nb);
-        }
+        for (int t = 0; t < NE; ++t) hn[t] = half * (dg[o][t] - dg[1 - o][P - t]);
       } else {
         const int f = o == 0 ? (e == 1 ? 0 : 3) : (e == 2 ? 1 : 2);
         const int L = lq[f];
@@ -275,37 +294,37 @@ __global__ void __launch_bounds__(kBlock, 2)
 #pragma unroll
         for (int t = 0; t < NE; ++t) hn[t] = cm * rec[(f * kBlock + b.el) * NE + t] + cp * rec[rn * NE + (P - t)];
       }
-      lift_add<T, N, NE>(tb.Lf[o][e], hn, (T)1, r);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        T a = 0;
+#pragma unroll
+        for (int t = 0; t < NE; ++t) a += tb.Lf[o][e][i * NE + t] * hn[t];
+        R[i] += a;
+      }
     }
+    T u[N], w[N];
+    load_elem<T, N>(uin + off + o * N, u);
+    if constexpr (HAS_U0) load_elem<T, N, false>(u0 + off + o * N, w);
+    if constexpr (SROUND) {
+      if (o == 0)
+        hkey = fmix32(((uint32_t)(b.a0 + b.el - __ldg(grange + b.geo).x) * (uint32_t)NPX) ^
+                      ((uint32_t)blockIdx.y * 0x632be5abu) ^ __float_as_uint(u[0]) ^
+                      (__float_as_uint(u[1]) * 0x85ebca77u));
 #pragma unroll
-    for (int i = 0; i < N; ++i) R[o * N + i] = r[i];
-  }
-
-  // gamma is beta dt D / J^2 with J = h/2 of the square elements: 1/h^2 = gscale / 4
-  T gam = c.gamma * (T)0.25 * __ldg(gscale + b.geo);
-  if (adv != nullptr && __ldg(adv + b.a0 + b.el) == 0) gam = (T)0;
-  const size_t off = (sbase + (size_t)(b.a0 + b.el)) * NPX;
-  T u[NPX], o[NPX];
-  load_elem<T, NPX>(uin + off, u);
-  if constexpr (HAS_U0) load_elem<T, NPX, false>(u0 + off, o);
-  if constexpr (SROUND) {
-    const uint32_t h = fmix32(((uint32_t)(b.a0 + b.el - __ldg(grange + b.geo).x) * (uint32_t)NPX) ^
-                              ((uint32_t)blockIdx.y * 0x632be5abu) ^ __float_as_uint(u[0]) ^
-                              (__float_as_uint(u[1]) * 0x85ebca77u));
+      for (int k = 0; k < N; ++k) {
+        const T base = HAS_U0 ? w[k] : c.beta * u[k];
+        const T inc = HAS_U0 ? fmaf(c.beta, u[k] - w[k], gam * R[k]) : gam * R[k];
+        w[k] = add_stochastic(base, inc, hkey + (uint32_t)(o * N + k));
+      }
+    } else if constexpr (HAS_U0) {
 #pragma unroll
-    for (int k = 0; k < NPX; ++k) {
-      const T base = HAS_U0 ? o[k] : c.beta * u[k];
-      const T inc = HAS_U0 ? fmaf(c.beta, u[k] - o[k], gam * R[k]) : gam * R[k];
-      o[k] = add_stochastic(base, inc, h + (uint32_t)k);
+      for (int k = 0; k < N; ++k) w[k] = w[k] + c.beta * (u[k] - w[k]) + gam * R[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < N; ++k) w[k] = c.beta * u[k] + gam * R[k];
     }
-  } else if constexpr (HAS_U0) {
-#pragma unroll
-    for (int k = 0; k < NPX; ++k) o[k] = o[k] + c.beta * (u[k] - o[k]) + gam * R[k];
-  } else {
-#pragma unroll
-    for (int k = 0; k < NPX; ++k) o[k] = c.beta * u[k] + gam * R[k];
+    store_elem<T, N>(out + off + o * N, w);
   }
-  store_elem<T, NPX>(out + off, o);
 }
 
 template <typename T, int P>
