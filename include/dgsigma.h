@@ -262,6 +262,19 @@ int dg_step(dg_ctx *ctx, int nsteps, double dt);
  * fixed-window path.  Errors: DG_EINVAL (negative or non-finite r_factor). */
 int dg_set_growing_window(dg_ctx *ctx, double r_factor);
 
+/* Test hook (no counterpart in the paper) for the shared-memory copies of the
+ * stage kernel.  By default a chunk of square elements whose node values fill
+ * whole 16-byte slots (p = 1, 3, 5) arrives by one tensor copy (TMA) per
+ * chunk, waited for on an mbarrier at most ~4M polls; a wait that runs out
+ * makes the block give up and the next dg_moments, dg_covariance or
+ * dg_propagate_to return DG_ETIMEOUT (the state is then undefined and the
+ * context usable again after dg_set_sources).  mode 0: that default; 1:
+ * per-thread cp.async copies only; 2: the barriers also wait for 16 bytes no
+ * copy delivers, so every wait runs out (after ~4k polls).  Returns in
+ * *tensor_copies (may be NULL) the chunk copies made by the tensor path since
+ * the last call.  Errors: DG_EINVAL (mode outside 0..2). */
+int dg_debug_copies(dg_ctx *ctx, int mode, unsigned long long *tensor_copies);
+
 /* Test hook (no counterpart in the paper): the n-th device allocation of the
  * library from now on (0 = the next one, in any context) fails as if the
  * device were out of memory; -1 disarms.  Calls that hit it return

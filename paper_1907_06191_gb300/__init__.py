@@ -95,6 +95,7 @@ EXPORTS = {
     "dg_basis_tables": (_I, [_I, _I, _DP, _DP, _DP, _DP]),
     "dg_set_growing_window": (_I, [_P, _D]),
     "dg_debug_fail_alloc": (_I, [_I]),
+    "dg_debug_copies": (_I, [_P, _I, ctypes.POINTER(ctypes.c_ulonglong)]),
     "dg_triangle_tables": (_I, [_I, _DP, _DP, _DP, _DP, _DP]),
     # learned surrogate (include/dgsurrogate.h)
     "sg_create": (_I, [_I, ctypes.c_ulonglong, _I, ctypes.POINTER(_P)]),
@@ -264,6 +265,14 @@ class DGSolver:
         dt, rho = ctypes.c_double(), ctypes.c_double()
         self._ck(self._L.dg_query_dt(self.ctx, ctypes.byref(dt), ctypes.byref(rho)), "dg_query_dt")
         return dt.value, rho.value
+
+    def debug_copies(self, mode: int) -> int:
+        """Set the stage kernel's copy mode (0 tensor copies, 1 cp.async, 2
+        test hook: waits that run out); returns the tensor copies made since
+        the last call."""
+        n = ctypes.c_ulonglong(0)
+        self._ck(self._L.dg_debug_copies(self.ctx, int(mode), ctypes.byref(n)), "dg_debug_copies")
+        return n.value
 
     def set_growing_window(self, r_factor: float):
         """Advance only elements within r_factor sqrt(sigma0^2 + 2 D t) of the

@@ -11,7 +11,10 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include <atomic>
+#include <mutex>
 
 #include "dg_internal.h"
 
@@ -92,6 +95,7 @@ void free_state(Ctx &c) {
   cudaFree(c.d_out);
   cudaFree(c.d_q);
   c.d_q = nullptr;
+  c.tmap_ok = false;
   c.d_src = c.d_mom = c.d_mom0 = c.d_part = c.d_out = nullptr;
   free_window(c);
   c.m = 0;
@@ -108,6 +112,78 @@ void *state_array(Ctx &c, int k) {
 size_t state_bytes_for(const Ctx &c, int m) {
   size_t b = 3 * (size_t)m * c.field_elems() * c.esize();
   return (b + 255) / 256 * 256;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// Tensor maps of the three state arrays: rows of np values, boxes of kBlock
+// rows, the hardware swizzle that matches Stage's layout (32, 64 or 128 bytes
+// per row; none otherwise).  Left unset (cp.async copies) when the rows are
+// not whole 16-byte slots or the encoder is unavailable.
+void make_tensor_maps(Ctx &c) {
+  c.tmap_ok = false;
+  if (c.triangles() || !c.d_state) return;
+  const size_t row_bytes = (size_t)c.np() * c.esize();
+  if (row_bytes % 16 != 0) return;
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return;
+  const CUtensorMapSwizzle sw = row_bytes == 32    ? CU_TENSOR_MAP_SWIZZLE_32B
+                                : row_bytes == 64  ? CU_TENSOR_MAP_SWIZZLE_64B
+                                : row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                                   : CU_TENSOR_MAP_SWIZZLE_NONE;
+  const cuuint64_t dims[2] = {(cuuint64_t)c.np(), (cuuint64_t)c.m * (cuuint64_t)c.geo.n_pad};
+  const cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
+  const cuuint32_t box[2] = {(cuuint32_t)c.np(), (cuuint32_t)kBlock};
+  const cuuint32_t estr[2] = {1, 1};
+  for (int k = 0; k < 3; ++k) {
+    const CUresult r = enc(&c.tmap[k],
+                           c.cfg.precision == DG_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                           2, state_array(c, k), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return;
+  }
+  c.tmap_ok = true;
+}
+
+// DG_ETIMEOUT if a bounded wait of a stage kernel gave up since the last
+// check (the flag is cleared); synchronises the stream.
+int take_device_error(dg_ctx *ctx) {
+  Ctx &c = ctx->c;
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, c.d_err, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "error flag");
+  CK(cudaStreamSynchronize(c.stream), "error flag");
+  if (flag) {
+    CK(cudaMemsetAsync(c.d_err, 0, sizeof(int), c.stream), "error flag");
+    return fail(ctx, DG_ETIMEOUT, "a stage kernel gave up waiting for its shared-memory copies");
+  }
+  return DG_OK;
+}
+
+StageCopies stage_copies(Ctx &c, int in_array, bool with_u0) {
+  StageCopies cp;
+  if (!c.tmap_ok || c.copy_mode == 1) return cp;
+  cp.map_u = &c.tmap[in_array];
+  cp.map_u0 = with_u0 ? &c.tmap[0] : nullptr;
+  cp.use_tma = 1;
+  cp.extra_tx = c.copy_mode == 2 ? 16 : 0;
+  cp.limit = c.copy_mode == 2 ? (1 << 12) : (1 << 22);
+  cp.err = c.d_err;
+  cp.counter = c.d_tma;
+  return cp;
 }
 
 // One SSP-RK3 step: U1 = U + dt L U; U2 = 3/4 U + 1/4 (U1 + dt L U1);
@@ -134,7 +210,8 @@ cudaError_t rk3_step(Ctx &c, double dt, cudaStream_t s, const ChunkSel &sel = Ch
                                  s, sel);
       else
         e = launch_stage_f64(c.cfg.p, (const double *)in[k], (const double *)base[k],
-                             (double *)outp[k], c.geo, st, c.m, c.gll, sc, s, sel);
+                             (double *)outp[k], c.geo, st, c.m, c.gll, sc, s, sel,
+                             stage_copies(c, k, base[k] != nullptr));
     } else {
       StageCoef<float> sc{(float)co[k][0], (float)co[k][1], (float)co[k][2], (float)pen,
                           wallA, c.cfg.rounding == DG_ROUND_STOCHASTIC};
@@ -144,7 +221,8 @@ cudaError_t rk3_step(Ctx &c, double dt, cudaStream_t s, const ChunkSel &sel = Ch
                                  s, sel);
       else
         e = launch_stage_f32(c.cfg.p, (const float *)in[k], (const float *)base[k],
-                             (float *)outp[k], c.geo, st, c.m, c.gll, sc, s, sel);
+                             (float *)outp[k], c.geo, st, c.m, c.gll, sc, s, sel,
+                             stage_copies(c, k, base[k] != nullptr));
     }
   }
   return e;
@@ -471,6 +549,7 @@ int set_sources_impl(dg_ctx *ctx, const double *xy, int m) {
   c.src.assign(xy, xy + 2 * nd);
   c.gw_ready = false;
   c.gw_synced = false;
+  make_tensor_maps(c);
   CK(cudaMemcpyAsync(c.d_src, c.src.data(), sizeof(double) * 2 * nd, cudaMemcpyHostToDevice, c.stream), "source copy");
   CK(launch_init_sources(c, state_array(c, 0), c.stream), "init sources");
   int r = compute_moments(ctx, c.d_mom0);
@@ -484,6 +563,7 @@ int set_sources_impl(dg_ctx *ctx, const double *xy, int m) {
 int check_growth(dg_ctx *ctx) {
   Ctx &c = ctx->c;
   TraceRange trace("stability check");
+  if (const int r = take_device_error(ctx); r != DG_OK) return r;
   const int nd = c.m * c.geo.G();
   std::vector<double> mom((size_t)nd * kMomFields), mom0((size_t)nd * kMomFields);
   int r = compute_moments(ctx, c.d_mom);
@@ -566,6 +646,15 @@ int dg_create(const dg_config *cfg, dg_ctx **out) {
     delete ctx;
     return DG_EINVAL;
   }
+  void *flags = nullptr;
+  if (dev_alloc(&flags, 16) != cudaSuccess || cudaMemset(flags, 0, 16) != cudaSuccess) {
+    cudaFree(flags);
+    cudaStreamDestroy(c.own_stream);
+    delete ctx;
+    return DG_ENOMEM;
+  }
+  c.d_err = static_cast<int *>(flags);
+  c.d_tma = reinterpret_cast<unsigned long long *>(static_cast<char *>(flags) + 8);
   *out = ctx;
   return DG_OK;
 }
@@ -577,6 +666,7 @@ void dg_destroy(dg_ctx *ctx) {
   if (c.stream) cudaStreamSynchronize(c.stream);
   free_state(c);
   free_geometry(c.geo);
+  cudaFree(c.d_err);
   if (c.own_stream) cudaStreamDestroy(c.own_stream);
   delete ctx;
 }
@@ -755,6 +845,22 @@ int dg_set_sources(dg_ctx *ctx, const double *xy, int m) {
   }
 }
 
+int dg_debug_copies(dg_ctx *ctx, int mode, unsigned long long *tensor_copies) {
+  if (!ctx || mode < 0 || mode > 2) return DG_EINVAL;
+  Ctx &c = ctx->c;
+  CK(cudaSetDevice(c.device), "set device");
+  unsigned long long n = 0;
+  CK(cudaMemcpyAsync(&n, c.d_tma, sizeof(n), cudaMemcpyDeviceToHost, c.stream), "copy counter");
+  CK(cudaMemsetAsync(c.d_tma, 0, sizeof(n), c.stream), "copy counter");
+  CK(cudaStreamSynchronize(c.stream), "copy counter");
+  if (tensor_copies) *tensor_copies = n;
+  if (mode != c.copy_mode) {
+    c.copy_mode = mode;
+    drop_graph(c);  // captured launches carry the old settings
+  }
+  return DG_OK;
+}
+
 int dg_debug_fail_alloc(int n) {
   if (n < -1) return DG_EINVAL;
   g_fail_alloc.store(n);
@@ -830,6 +936,7 @@ int dg_moments(dg_ctx *ctx, double *out) {
   std::vector<double> tmp((size_t)nd * kMomFields);
   CK(cudaMemcpyAsync(tmp.data(), c.d_mom, tmp.size() * 8, cudaMemcpyDeviceToHost, c.stream), "moment copy");
   CK(cudaStreamSynchronize(c.stream), "moments");
+  if (const int e = take_device_error(ctx); e != DG_OK) return e;
   for (int s = 0; s < nd; ++s)
     for (int f = 0; f < 6; ++f) out[(size_t)s * 6 + f] = tmp[(size_t)s * kMomFields + f];
   return DG_OK;
@@ -851,6 +958,7 @@ int dg_covariance_batch(dg_ctx *ctx, double *sigma3, double *mu2, double *mass) 
     CK(cudaMemcpy2DAsync(mass, sizeof(double), c.d_mom, sizeof(double) * kMomFields, sizeof(double),
                          (size_t)c.m * G, cudaMemcpyDeviceToHost, c.stream), "mass copy");
   CK(cudaStreamSynchronize(c.stream), "covariance");
+  if (const int e = take_device_error(ctx); e != DG_OK) return e;
   for (int g = 0; g < G; ++g) {
     const double *o = &out[(size_t)kCovOut * g];
     sigma3[3 * g] = o[0]; sigma3[3 * g + 1] = o[1]; sigma3[3 * g + 2] = o[2];

@@ -1,6 +1,7 @@
 // dg_internal.h -- internal types of the dgsigma library (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
@@ -201,6 +202,15 @@ struct Ctx {
   double *d_part = nullptr;       // [m][kMomBlocks][7] partial sums
   double *d_out = nullptr;        // [G][kCovOut] covariance results
   void *d_q = nullptr;            // triangles: q of one stage, [m][n_pad][4 N]
+  // state arrays 0..2 as 2D tensors [m n_pad rows][np values] for the tensor
+  // copies of the stage kernel (square elements whose rows are whole 16-byte
+  // slots)
+  CUtensorMap tmap[3];
+  bool tmap_ok = false;
+  int copy_mode = 0;              // 0 tensor copies where possible, 1 cp.async only,
+                                  // 2 test hook: barriers that never complete
+  int *d_err = nullptr;           // a bounded device wait gave up (and the copy counter)
+  unsigned long long *d_tma = nullptr;
   size_t part_elems = 0;
 
   // Growing window (off while gw_r <= 0): in each group of up to 64 steps an
@@ -241,15 +251,32 @@ struct ChunkSel {
   long long count = -1;
   const uint8_t *adv = nullptr;
 };
+// How a stage launch moves its chunks into shared memory.  Device side:
+struct CopyArgs {
+  int use_tma = 0;                         // tensor copies (else per-thread cp.async)
+  int extra_tx = 0;                        // test hook: bytes awaited beyond the copy
+  int limit = 1 << 22;                     // polls of a barrier before giving up
+  int *err = nullptr;                      // set to 1 when a wait gave up
+  unsigned long long *counter = nullptr;   // chunk copies made by the tensor path
+};
+// Host side: the tensor maps of the input and u0 arrays and the settings above.
+struct StageCopies {
+  const CUtensorMap *map_u = nullptr, *map_u0 = nullptr;
+  int use_tma = 0, extra_tx = 0, limit = 1 << 22;
+  int *err = nullptr;
+  unsigned long long *counter = nullptr;
+};
 // One stage over all m densities: out = u0 + beta (u - u0) + gamma R(u).
 cudaError_t launch_stage_f64(int p, const double *u, const double *u0, double *out,
                              const Geometry &geo, long long stride, int m,
                              const Gll &g, const StageCoef<double> &c, cudaStream_t s,
-                             const ChunkSel &sel = ChunkSel{});
+                             const ChunkSel &sel = ChunkSel{},
+                             const StageCopies &cp = StageCopies{});
 cudaError_t launch_stage_f32(int p, const float *u, const float *u0, float *out,
                              const Geometry &geo, long long stride, int m,
                              const Gll &g, const StageCoef<float> &c, cudaStream_t s,
-                             const ChunkSel &sel = ChunkSel{});
+                             const ChunkSel &sel = ChunkSel{},
+                             const StageCopies &cp = StageCopies{});
 
 // One stage on the pixel triangles (two passes through qbuf, [m][n_pad][4 N]).
 cudaError_t launch_tri_stage_f64(int p, const double *u, const double *u0, double *out,

@@ -25,6 +25,8 @@
 // faces the lifting parts of q^- and q^+ cancel in q_hat - k q^-.
 #pragma once
 
+#include <cuda.h>
+
 #include <algorithm>
 
 #include "dg_internal.h"
@@ -171,6 +173,51 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// Tensor-memory-accelerator copies of a whole chunk.  The state array is a 2D
+// tensor [rows = densities x padded elements][NP values]; one elected thread
+// arms an mbarrier with the expected bytes and issues one tiled copy of 256
+// rows.  With 32, 64 or 128 bytes per element the copy uses the hardware
+// swizzle of that width, which XORs the 16-byte slot index with bits of the
+// row exactly as Stage::swz does, so the shared-memory layout is the same as
+// with the per-thread cp.async copies.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_rows(uint32_t dst, const CUtensorMap *map, int row,
+                                              uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(row), "r"(bar)
+      : "memory");
+}
+// Poll phase `parity` of the barrier at most `limit` times (with a short
+// sleep in between); false if it did not complete.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit) {
+  for (int i = 0; i < limit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    __nanosleep(64);
+  }
+  return false;
+}
+
 // Face f of an element: 0 east (x = +1), 1 west, 2 north (y = +1), 3 south.
 // Node t runs along the face.  own(f, t): node index on face f; the matching
 // node of the neighbour across f is own(opposite(f), t).
@@ -310,6 +357,16 @@ constexpr int stage_min_blocks() {
 
 // FULL = false drops the flux terms in u^- and u^+ that vanish without a
 // penalty (eta = 0) and without paper walls (the default configuration).
+// Bytes of the front shared-memory buffer (u chunk, then face records),
+// rounded to 1024 so that the u0 chunk behind it starts on that boundary.
+template <typename T, int P>
+__host__ __device__ constexpr int stage_front_bytes(int nrec) {
+  return ((Stage<T, (P + 1) * (P + 1)>::CHUNK_BYTES > Records<T, P>::bytes(nrec)
+               ? Stage<T, (P + 1) * (P + 1)>::CHUNK_BYTES
+               : Records<T, P>::bytes(nrec)) +
+          1023) / 1024 * 1024;
+}
+
 template <typename T, int P, bool HAS_U0, bool SROUND, bool FULL>
 __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
     k_stage(const T *__restrict__ uin, const T *u0, T *out,
@@ -318,13 +375,18 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
             const int2 *__restrict__ grange, const T *__restrict__ gscale, long long stride,
             int nrec,
             const int *__restrict__ chunk_list, const uint8_t *__restrict__ adv,
-            const StageTab<T, P> tb, const StageCoef<T> c) {
+            const StageTab<T, P> tb, const StageCoef<T> c,
+            const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_u0,
+            const CopyArgs ca) {
   constexpr int n = P + 1, NP = n * n;
   using St = Stage<T, NP>;
   using Fc = Faces<P>;
-  // shared memory: [u chunk, later the face records][u0 chunk, later the result]
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int front = max(St::CHUNK_BYTES, Records<T, P>::bytes(nrec));
+  // shared memory: [u chunk, later the face records][u0 chunk, later the
+  // result][two mbarriers]; the first two start on 1024-byte boundaries so
+  // that the swizzled tensor copies land in the Stage layout
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const int front = stage_front_bytes<T, P>(nrec);
+  const int bar_off = front + ((St::CHUNK_BYTES + 15) / 16) * 16;
   T *su = reinterpret_cast<T *>(smem_raw);
   T *so = reinterpret_cast<T *>(smem_raw + front);
   T *rec_base = reinterpret_cast<T *>(smem_raw);
@@ -345,7 +407,27 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
   const size_t sbase = (size_t)blockIdx.y * (size_t)stride * NP;
   const T *U = uin + sbase;
 
-  {  // async copies of the u chunk (group 0) and the u0 chunk (group 1)
+  // tensor copies where the element is a whole number of 16-byte slots and the
+  // buffers sit on their alignment (the same for every thread of the block)
+  const bool tma = St::SLOT && ca.use_tma && (smem_u32(smem_raw) & 1023u) == 0;
+  const uint32_t bar0 = smem_u32(smem_raw + bar_off), bar1 = bar0 + 8;
+  if (tma) {
+    if (el == 0) {
+      mbar_init(bar0, 1);
+      if constexpr (HAS_U0) mbar_init(bar1, 1);
+      mbar_fence_init();
+      const uint32_t bytes = (uint32_t)(kBlock * NP * sizeof(T)) + (uint32_t)ca.extra_tx;
+      const int row = (int)((long long)blockIdx.y * stride + a0);
+      mbar_expect_tx(bar0, bytes);
+      tma_load_rows(smem_u32(su), &tm_u, row, bar0);
+      if constexpr (HAS_U0) {
+        mbar_expect_tx(bar1, bytes);
+        tma_load_rows(smem_u32(so), &tm_u0, row, bar1);
+      }
+      if (ca.counter) atomicAdd(ca.counter, 1ull);
+    }
+    __syncthreads();  // the barriers exist before anyone polls them
+  } else {  // async copies of the u chunk (group 0) and the u0 chunk (group 1)
     const char *gu = reinterpret_cast<const char *>(U + (size_t)a0 * NP);
     const int np16 = St::pieces(cnt);
     for (int j = el; j < np16; j += kBlock)
@@ -368,9 +450,20 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
     hk = __ldg(halo + (size_t)chunk * kHaloCap + el);
     load_elem<T, NP>(U + (size_t)hk.x * NP, hv);
   }
-  if constexpr (HAS_U0) cp_async_wait<1>();
-  else cp_async_wait<0>();
-  __syncthreads();
+  if (tma) {
+    // bounded wait; on a time-out the whole block records it and leaves
+    // (after waiting, also bounded, for the u0 copy it issued)
+    const bool ok = mbar_wait(bar0, 0, ca.limit);
+    if (__syncthreads_or(!ok)) {
+      if constexpr (HAS_U0) mbar_wait(bar1, 0, ca.limit);
+      if (el == 0) atomicExch(ca.err, 1);
+      return;
+    }
+  } else {
+    if constexpr (HAS_U0) cp_async_wait<1>();
+    else cp_async_wait<0>();
+    __syncthreads();
+  }
 
   T u[NP], R[NP];
   if (live) St::read(su, el, u);
@@ -476,8 +569,16 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
   }
 
   if constexpr (HAS_U0) {
-    cp_async_wait<0>();
-    __syncthreads();
+    if (tma) {
+      const bool ok = mbar_wait(bar1, 0, ca.limit);
+      if (__syncthreads_or(!ok)) {
+        if (el == 0) atomicExch(ca.err, 1);
+        return;
+      }
+    } else {
+      cp_async_wait<0>();
+      __syncthreads();
+    }
   }
   if (live) {
     T o[NP];
@@ -523,7 +624,7 @@ template <typename T, int P>
 int stage_smem_bytes(int halo_max) {
   const int nrec = 4 * kBlock + halo_max + 1;
   const int chunk = Stage<T, (P + 1) * (P + 1)>::CHUNK_BYTES;
-  return std::max(chunk, Records<T, P>::bytes(nrec)) + chunk;
+  return stage_front_bytes<T, P>(nrec) + ((chunk + 15) / 16) * 16 + 16;
 }
 
 template <typename T, int P>
@@ -550,7 +651,7 @@ StageTab<T, P> make_tab(const Gll &g) {
 template <typename T, int P>
 cudaError_t launch_stage_p(const T *u, const T *u0, T *out, const Geometry &geo,
                            long long stride, int m, const Gll &g, const StageCoef<T> &c,
-                           cudaStream_t s, const ChunkSel &sel) {
+                           cudaStream_t s, const ChunkSel &sel, const StageCopies &cp) {
   const long long nch = sel.list ? sel.count : geo.n_chunks();
   if (geo.n_pad <= 0 || m <= 0 || nch <= 0) return cudaSuccess;
   if (nch > geo.n_chunks()) return cudaErrorInvalidValue;
@@ -583,10 +684,20 @@ cudaError_t launch_stage_p(const T *u, const T *u0, T *out, const Geometry &geo,
     attr_bytes = smem;
   }
   const bool full = c.pen != (T)0 || c.wallA;
+  CopyArgs ca;
+  ca.use_tma = cp.map_u != nullptr && (u0 == nullptr || cp.map_u0 != nullptr) ? cp.use_tma : 0;
+  ca.extra_tx = cp.extra_tx;
+  ca.limit = cp.limit;
+  ca.err = cp.err;
+  ca.counter = cp.counter;
+  if (ca.use_tma && ca.err == nullptr) ca.use_tma = 0;
+  const CUtensorMap zero_map{};
+  const CUtensorMap &mu = ca.use_tma ? *cp.map_u : zero_map;
+  const CUtensorMap &mu0 = ca.use_tma && u0 ? *cp.map_u0 : zero_map;
   auto go = [&](auto kern) {
     kern<<<grid, kBlock, smem, s>>>(u, u0, out, geo.d_loc, geo.d_halo, geo.d_halo_cnt,
                                     geo.d_chunk, geo.d_grange, gscale, stride, nrec, sel.list,
-                                    sel.adv, tb, c);
+                                    sel.adv, tb, c, mu, mu0, ca);
   };
   if (kSR && c.sround) {
     if (u0) full ? go(k_stage<T, P, true, kSR, true>) : go(k_stage<T, P, true, kSR, false>);
@@ -601,13 +712,13 @@ cudaError_t launch_stage_p(const T *u, const T *u0, T *out, const Geometry &geo,
 template <typename T>
 cudaError_t launch_stage_any(int p, const T *u, const T *u0, T *out, const Geometry &geo,
                              long long stride, int m, const Gll &g, const StageCoef<T> &c,
-                             cudaStream_t s, const ChunkSel &sel) {
+                             cudaStream_t s, const ChunkSel &sel, const StageCopies &cp) {
   switch (p) {
-    case 1: return launch_stage_p<T, 1>(u, u0, out, geo, stride, m, g, c, s, sel);
-    case 2: return launch_stage_p<T, 2>(u, u0, out, geo, stride, m, g, c, s, sel);
-    case 3: return launch_stage_p<T, 3>(u, u0, out, geo, stride, m, g, c, s, sel);
-    case 4: return launch_stage_p<T, 4>(u, u0, out, geo, stride, m, g, c, s, sel);
-    case 5: return launch_stage_p<T, 5>(u, u0, out, geo, stride, m, g, c, s, sel);
+    case 1: return launch_stage_p<T, 1>(u, u0, out, geo, stride, m, g, c, s, sel, cp);
+    case 2: return launch_stage_p<T, 2>(u, u0, out, geo, stride, m, g, c, s, sel, cp);
+    case 3: return launch_stage_p<T, 3>(u, u0, out, geo, stride, m, g, c, s, sel, cp);
+    case 4: return launch_stage_p<T, 4>(u, u0, out, geo, stride, m, g, c, s, sel, cp);
+    case 5: return launch_stage_p<T, 5>(u, u0, out, geo, stride, m, g, c, s, sel, cp);
     default: return cudaErrorInvalidValue;
   }
 }
