@@ -31,6 +31,51 @@ struct TriShape {
   __host__ __device__ static constexpr int fedge(int f) { return f == 0 ? 1 : (f == 1 ? 2 : (f == 2 ? 1 : 0)); }
 };
 
+// FP32 staging of a chunk's q (4 N values per pixel = N 16-byte slots) in
+// shared memory, so that the q pass stores and the divergence pass loads it
+// with coalesced 16-byte pieces.  A pixel takes SP slots (N rounded up to an
+// odd count, so that 16-byte accesses of 8 consecutive threads hit 8 bank
+// groups); triangle o's q_x, q_y are its slots o N/2 .. o N/2 + N/2 - 1.
+// Needs N even (p = 2, 3).
+template <typename T, int P>
+struct TriQStage {
+  static constexpr int N = TriShape<P>::N;
+  static constexpr bool ON = sizeof(T) == 4 && N % 2 == 0;
+  static constexpr int S = N, SP = (N % 2 == 0) ? N + 1 : N, HALF = N / 2;
+  static constexpr int BYTES = ON ? kBlock * SP * 16 : 0;
+  __device__ static __forceinline__ void put(float4 *sq, int el, int o, const T (&qx)[N],
+                                             const T (&qy)[N]) {
+#pragma unroll
+    for (int k = 0; k < HALF; ++k) {
+      float v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int w = 4 * k + q;
+        v[q] = w < N ? qx[w] : qy[w - N];
+      }
+      sq[el * SP + o * HALF + k] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+  }
+  __device__ static __forceinline__ void get(const float4 *sq, int el, int o, T (&qx)[N],
+                                             T (&qy)[N]) {
+#pragma unroll
+    for (int k = 0; k < HALF; ++k) {
+      const float4 f = sq[el * SP + o * HALF + k];
+      const float v[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int w = 4 * k + q;
+        if (w < N) qx[w] = v[q];
+        else qy[w - N] = v[q];
+      }
+    }
+  }
+};
+
+__host__ __device__ constexpr int tri_rec_bytes(int nrec, int ne, int tsize) {
+  return (nrec * ne * tsize + 15) / 16 * 16;
+}
+
 template <typename T, int P>
 struct TriTab {
   static constexpr int N = TriShape<P>::N, NE = TriShape<P>::NE;
@@ -146,13 +191,15 @@ __global__ void __launch_bounds__(kBlock, tri_min_blocks<T>())
         for (int t = 0; t < NE; ++t) rec[(4 * kBlock + h) * NE + t] = v[S::en(S::fedge(f), t)];
   }
   __syncthreads();
-  if (!b.live) return;
+  using QS = TriQStage<T, P>;
+  if (!QS::ON && !b.live) return;
+  float4 *sq = reinterpret_cast<float4 *>(smem_raw + tri_rec_bytes(nrec, NE, (int)sizeof(T)));
 
   const int lq[4] = {b.l4.x, b.l4.y, b.l4.z, b.l4.w};
   const T half = (T)0.5;
   T *Q = qout + (sbase + (size_t)(b.a0 + b.el)) * (4 * N);
 #pragma unroll 1
-  for (int o = 0; o < 2; ++o) {
+  for (int o = 0; o < 2 && b.live; ++o) {
     T uo[N];
     load_elem<T, N>(Ue + o * N, uo);
     T qx[N], qy[N];
@@ -193,8 +240,18 @@ __global__ void __launch_bounds__(kBlock, tri_min_blocks<T>())
         qy[i] += tb.nrm[o][e][1] * a;
       }
     }
-    store_elem<T, N>(Q + (2 * o) * N, qx);
-    store_elem<T, N>(Q + (2 * o + 1) * N, qy);
+    if constexpr (QS::ON) {
+      QS::put(sq, b.el, o, qx, qy);
+    } else {
+      store_elem<T, N>(Q + (2 * o) * N, qx);
+      store_elem<T, N>(Q + (2 * o + 1) * N, qy);
+    }
+  }
+  if constexpr (QS::ON) {  // coalesced 16-byte stores of the chunk's q
+    __syncthreads();
+    float4 *gq = reinterpret_cast<float4 *>(qout + (sbase + (size_t)b.a0) * (4 * N));
+    for (int j = b.el; j < b.cnt * QS::S; j += kBlock)
+      gq[j] = sq[(j / QS::S) * QS::SP + j % QS::S];
   }
 }
 
@@ -216,6 +273,24 @@ __global__ void __launch_bounds__(kBlock, tri_min_blocks<T>())
   const size_t sbase = (size_t)blockIdx.y * (size_t)stride;
   const T *Qb = qin + sbase * (4 * N);
   const T *Qe = Qb + (size_t)(b.a0 + b.el) * (4 * N);
+  using QS = TriQStage<T, P>;
+  float4 *sq = reinterpret_cast<float4 *>(smem_raw + tri_rec_bytes(nrec, NE, (int)sizeof(T)));
+  if constexpr (QS::ON) {  // coalesced 16-byte copies of the chunk's q
+    const char *gq = reinterpret_cast<const char *>(Qb + (size_t)b.a0 * (4 * N));
+    for (int j = b.el; j < b.cnt * QS::S; j += kBlock)
+      cp_async16(sq + (j / QS::S) * QS::SP + j % QS::S, gq + 16 * (size_t)j);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+  }
+  auto load_q = [&](int o, T (&qx)[N], T (&qy)[N]) {
+    if constexpr (QS::ON) {
+      QS::get(sq, b.el, o, qx, qy);
+    } else {
+      load_elem<T, N>(Qe + (2 * o) * N, qx);
+      load_elem<T, N>(Qe + (2 * o + 1) * N, qy);
+    }
+  };
 
   // q . n (outward normal of triangle o, edge e) at the edge's node t
   auto qn = [&](const T (&qx)[N], const T (&qy)[N], int o, int e, int t) -> T {
@@ -227,8 +302,7 @@ __global__ void __launch_bounds__(kBlock, tri_min_blocks<T>())
 #pragma unroll
     for (int o = 0; o < 2; ++o) {
       T qx[N], qy[N];
-      load_elem<T, N>(Qe + (2 * o) * N, qx);
-      load_elem<T, N>(Qe + (2 * o + 1) * N, qy);
+      load_q(o, qx, qy);
 #pragma unroll
       for (int f = 0; f < 4; ++f)
         if (S::ftri(f) == o)
@@ -267,8 +341,7 @@ __global__ void __launch_bounds__(kBlock, tri_min_blocks<T>())
     T R[N];
     {
       T qx[N], qy[N];
-      load_elem<T, N>(Qe + (2 * o) * N, qx);
-      load_elem<T, N>(Qe + (2 * o + 1) * N, qy);
+      load_q(o, qx, qy);
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         T a = 0;
@@ -340,7 +413,7 @@ cudaError_t launch_tri_p(const T *u, const T *u0, T *out, T *qbuf, const Geometr
   else gscale = geo.d_gscale_f;
   const TriTab<T, P> tb = make_tri_tab<T, P>(ref);
   const int nrec = 4 * kBlock + geo.halo_max + 1;
-  const int smem = nrec * TriShape<P>::NE * (int)sizeof(T);
+  const int smem = tri_rec_bytes(nrec, TriShape<P>::NE, (int)sizeof(T)) + TriQStage<T, P>::BYTES;
   static int attr_bytes = 0;
   constexpr bool kSR = sizeof(T) == 4;
   if (smem > attr_bytes) {
