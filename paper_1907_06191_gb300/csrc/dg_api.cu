@@ -173,11 +173,14 @@ int take_device_error(dg_ctx *ctx) {
   return DG_OK;
 }
 
+// Copy settings of RK stage k (input array k; u0 = array 0; output array
+// k + 1 mod 3: U1, U2, then U in place).
 StageCopies stage_copies(Ctx &c, int in_array, bool with_u0) {
   StageCopies cp;
   if (!c.tmap_ok || c.copy_mode == 1) return cp;
   cp.map_u = &c.tmap[in_array];
   cp.map_u0 = with_u0 ? &c.tmap[0] : nullptr;
+  cp.map_out = &c.tmap[(in_array + 1) % 3];
   cp.use_tma = 1;
   cp.extra_tx = c.copy_mode == 2 ? 16 : 0;
   cp.limit = c.copy_mode == 2 ? (1 << 12) : (1 << 22);

@@ -254,6 +254,7 @@ struct ChunkSel {
 // How a stage launch moves its chunks into shared memory.  Device side:
 struct CopyArgs {
   int use_tma = 0;                         // tensor copies (else per-thread cp.async)
+  int store_tma = 0;                       // tensor stores of full result chunks
   int extra_tx = 0;                        // test hook: bytes awaited beyond the copy
   int limit = 1 << 22;                     // polls of a barrier before giving up
   int *err = nullptr;                      // set to 1 when a wait gave up
@@ -261,7 +262,7 @@ struct CopyArgs {
 };
 // Host side: the tensor maps of the input and u0 arrays and the settings above.
 struct StageCopies {
-  const CUtensorMap *map_u = nullptr, *map_u0 = nullptr;
+  const CUtensorMap *map_u = nullptr, *map_u0 = nullptr, *map_out = nullptr;
   int use_tma = 0, extra_tx = 0, limit = 1 << 22;
   int *err = nullptr;
   unsigned long long *counter = nullptr;

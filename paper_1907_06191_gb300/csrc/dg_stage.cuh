@@ -201,6 +201,23 @@ __device__ __forceinline__ void tma_load_rows(uint32_t dst, const CUtensorMap *m
       "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(row), "r"(bar)
       : "memory");
 }
+// Tiled store of 256 rows from shared memory; the issuing thread waits until
+// the shared-memory source has been read (the block's other threads may have
+// left: shared memory lives until the last thread of the block exits).
+__device__ __forceinline__ void tma_store_rows(const CUtensorMap *map, int row, uint32_t src) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(0), "r"(row), "r"(src)
+      : "memory");
+  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+// Make this thread's shared-memory writes visible to the tensor copies.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
 // Poll phase `parity` of the barrier at most `limit` times (with a short
 // sleep in between); false if it did not complete.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit) {
@@ -377,7 +394,7 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
             const int *__restrict__ chunk_list, const uint8_t *__restrict__ adv,
             const StageTab<T, P> tb, const StageCoef<T> c,
             const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_u0,
-            const CopyArgs ca) {
+            const __grid_constant__ CUtensorMap tm_out, const CopyArgs ca) {
   constexpr int n = P + 1, NP = n * n;
   using St = Stage<T, NP>;
   using Fc = Faces<P>;
@@ -610,6 +627,12 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
     }
     St::write(so, el, o);
   }
+  if (tma && ca.store_tma && cnt == kBlock) {  // a full chunk: one tiled store
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (el == 0) tma_store_rows(&tm_out, (int)((long long)blockIdx.y * stride + a0), smem_u32(so));
+    return;
+  }
   __syncthreads();
   {  // coalesced 16-byte stores of the result chunk
     char *go = reinterpret_cast<char *>(out + sbase + (size_t)a0 * NP);
@@ -691,13 +714,15 @@ cudaError_t launch_stage_p(const T *u, const T *u0, T *out, const Geometry &geo,
   ca.err = cp.err;
   ca.counter = cp.counter;
   if (ca.use_tma && ca.err == nullptr) ca.use_tma = 0;
+  ca.store_tma = ca.use_tma && cp.map_out != nullptr ? 1 : 0;
   const CUtensorMap zero_map{};
   const CUtensorMap &mu = ca.use_tma ? *cp.map_u : zero_map;
   const CUtensorMap &mu0 = ca.use_tma && u0 ? *cp.map_u0 : zero_map;
+  const CUtensorMap &mo = ca.store_tma ? *cp.map_out : zero_map;
   auto go = [&](auto kern) {
     kern<<<grid, kBlock, smem, s>>>(u, u0, out, geo.d_loc, geo.d_halo, geo.d_halo_cnt,
                                     geo.d_chunk, geo.d_grange, gscale, stride, nrec, sel.list,
-                                    sel.adv, tb, c, mu, mu0, ca);
+                                    sel.adv, tb, c, mu, mu0, mo, ca);
   };
   if (kSR && c.sround) {
     if (u0) full ? go(k_stage<T, P, true, kSR, true>) : go(k_stage<T, P, true, kSR, false>);
