@@ -108,13 +108,23 @@ struct StageCoef {
   int sround = 0;  // FP32: stochastic rounding of the stage result
 };
 
-// Tables by value in the kernel parameter space (constant bank).
+template <typename T> struct Vec2;  // two lanes of T
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+// Tables by value in the kernel parameter space (constant bank).  The paired
+// forms of D2 feed the packed two-lane FP32 instructions of the volume term
+// (two nodes per instruction; n = P + 1 even):
+//   D2x[ip n + m] = (D2[2ip][m], D2[2ip+1][m]),  D2y[j n + m] = (D2[j][m], D2[j][m]).
 template <typename T, int P>
 struct StageTab {
+  using T2 = typename Vec2<T>::type;
   T D[(P + 1) * (P + 1)];
   T D2[(P + 1) * (P + 1)];
   T Dout[2 * (P + 1)];  // outward derivative rows: D[p][:] (east, north), -D[0][:] (west, south)
   T inv_w;  // 1 / w_0 = 1 / w_p
+  T2 D2x[((P + 1) / 2) * (P + 1)];
+  T2 D2y[(P + 1) * (P + 1)];
 };
 
 // One geometry (domain) of a context.  A context holds G >= 1 of them; their

@@ -276,6 +276,34 @@ __device__ __forceinline__ float add_stochastic(float base, float inc, uint32_t 
   return fabsf(err) > r * ulp ? s + copysignf(ulp, err) : s;
 }
 
+// Two lanes of add_stochastic with packed FP32 instructions: lane by lane the
+// same operations and roundings (s - base and inc - (s - base) as fused
+// multiply-adds by -1, which round like the subtractions).
+__device__ __forceinline__ float2 add_stochastic2(float2 base, float2 inc, uint32_t h0,
+                                                  uint32_t h1) {
+  const float2 m1 = make_float2(-1.0f, -1.0f);
+  const float2 s = __fadd2_rn(base, inc);
+  const float2 err = __ffma2_rn(__ffma2_rn(base, m1, s), m1, inc);
+  const float2 ulp = __fmul2_rn(
+      make_float2(__uint_as_float(__float_as_uint(s.x) & 0x7f800000u),
+                  __uint_as_float(__float_as_uint(s.y) & 0x7f800000u)),
+      make_float2(0x1p-23f, 0x1p-23f));
+  const uint32_t k0 = (h0 ^ __float_as_uint(inc.x)) * 0x9e3779b9u;
+  const uint32_t k1 = (h1 ^ __float_as_uint(inc.y)) * 0x9e3779b9u;
+  const float2 thr = __fmul2_rn(__fadd2_rn(make_float2(__uint_as_float(0x3f800000u | (k0 >> 9)),
+                                                       __uint_as_float(0x3f800000u | (k1 >> 9))),
+                                           m1),
+                                ulp);
+  const float2 up = __fadd2_rn(s, make_float2(copysignf(ulp.x, err.x), copysignf(ulp.y, err.y)));
+  return make_float2(fabsf(err.x) > thr.x ? up.x : s.x, fabsf(err.y) > thr.y ? up.y : s.y);
+}
+
+// FP32 with an even number of nodes per line: pairs of nodes go through the
+// packed two-lane instructions (fma.rn.f32x2 and friends; each lane rounds
+// like the scalar instruction).
+template <typename T, int P>
+constexpr bool kPacked = sizeof(T) == 4 && (P + 1) % 2 == 0;
+
 // Outward normal derivative (reference units) at the nodes of face f: the
 // face's signed row of D applied along the lines normal to the face.
 template <typename T, int P>
@@ -498,16 +526,35 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
       face_record<T, P>(u, f, tb, tr, d);
       rec.put(f * kBlock + el, tr, d);
     }
+    if constexpr (kPacked<T, P>) {
+      // nodes (j, i) and (j, i + 1) together: the x part pairs a column of
+      // D2 with u_jm, the y part a value of D2 with u_m,i..i+1
 #pragma unroll
-    for (int j = 0; j < n; ++j)
+      for (int j = 0; j < n; ++j)
 #pragma unroll
-      for (int i = 0; i < n; ++i) {
-        T s = 0;
+        for (int ip = 0; ip < n / 2; ++ip) {
+          float2 s = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int m = 0; m < n; ++m)
-          s += tb.D2[i * n + m] * u[j * n + m] + tb.D2[j * n + m] * u[m * n + i];
-        R[j * n + i] = s;
-      }
+          for (int m = 0; m < n; ++m) {
+            s = __ffma2_rn(tb.D2x[ip * n + m], make_float2(u[j * n + m], u[j * n + m]), s);
+            s = __ffma2_rn(tb.D2y[j * n + m],
+                           make_float2(u[m * n + 2 * ip], u[m * n + 2 * ip + 1]), s);
+          }
+          R[j * n + 2 * ip] = s.x;
+          R[j * n + 2 * ip + 1] = s.y;
+        }
+    } else {
+#pragma unroll
+      for (int j = 0; j < n; ++j)
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+          T s = 0;
+#pragma unroll
+          for (int m = 0; m < n; ++m)
+            s += tb.D2[i * n + m] * u[j * n + m] + tb.D2[j * n + m] * u[m * n + i];
+          R[j * n + i] = s;
+        }
+    }
   }
   if (el < hcnt) {
     T tr[n], d[n];
@@ -604,10 +651,6 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
       // is the node's place inside its own geometry and its density, so a
       // geometry gives the same bits alone or in a batch
       if constexpr (HAS_U0) St::read(so, el, o);
-      auto base = [&](int k) -> T { return HAS_U0 ? o[k] : c.beta * u[k]; };
-      auto inc = [&](int k) -> T {
-        return HAS_U0 ? fmaf(c.beta, u[k] - o[k], gam * R[k]) : gam * R[k];
-      };
       // one avalanche hash per element: its place in its geometry, its
       // density and the bits of its first two input values (they change
       // every stage while the element is advancing)
@@ -615,12 +658,57 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
           ((uint32_t)(a0 + el - __ldg(grange + ci.y).x) * (uint32_t)NP) ^
           ((uint32_t)blockIdx.y * 0x632be5abu) ^ __float_as_uint(u[0]) ^
           (__float_as_uint(u[1]) * 0x85ebca77u));
+      if constexpr (kPacked<T, P>) {  // the same arithmetic, two nodes per instruction
+        const float2 b2 = make_float2(c.beta, c.beta), g2 = make_float2(gam, gam);
 #pragma unroll
-      for (int k = 0; k < NP; ++k) o[k] = add_stochastic(base(k), inc(k), h + (uint32_t)k);
+        for (int k = 0; k < NP; k += 2) {
+          const float2 u2 = make_float2(u[k], u[k + 1]), gr = __fmul2_rn(g2, make_float2(R[k], R[k + 1]));
+          float2 bs, in;
+          if constexpr (HAS_U0) {
+            bs = make_float2(o[k], o[k + 1]);
+            in = __ffma2_rn(b2, __ffma2_rn(bs, make_float2(-1.0f, -1.0f), u2), gr);
+          } else {
+            bs = __fmul2_rn(b2, u2);
+            in = gr;
+          }
+          const float2 w = add_stochastic2(bs, in, h + (uint32_t)k, h + (uint32_t)(k + 1));
+          o[k] = w.x;
+          o[k + 1] = w.y;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+          const T bs = HAS_U0 ? o[k] : c.beta * u[k];
+          const T in = HAS_U0 ? fmaf(c.beta, u[k] - o[k], gam * R[k]) : gam * R[k];
+          o[k] = add_stochastic(bs, in, h + (uint32_t)k);
+        }
+      }
     } else if constexpr (HAS_U0) {
       St::read(so, el, o);
+      if constexpr (kPacked<T, P>) {  // o + (beta (u - o) + gam R)
+        const float2 b2 = make_float2(c.beta, c.beta), g2 = make_float2(gam, gam);
 #pragma unroll
-      for (int k = 0; k < NP; ++k) o[k] = o[k] + c.beta * (u[k] - o[k]) + gam * R[k];
+        for (int k = 0; k < NP; k += 2) {
+          const float2 o2 = make_float2(o[k], o[k + 1]);
+          const float2 d = __ffma2_rn(o2, make_float2(-1.0f, -1.0f), make_float2(u[k], u[k + 1]));
+          const float2 w = __fadd2_rn(
+              o2, __ffma2_rn(b2, d, __fmul2_rn(g2, make_float2(R[k], R[k + 1]))));
+          o[k] = w.x;
+          o[k + 1] = w.y;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) o[k] = o[k] + c.beta * (u[k] - o[k]) + gam * R[k];
+      }
+    } else if constexpr (kPacked<T, P>) {
+      const float2 b2 = make_float2(c.beta, c.beta), g2 = make_float2(gam, gam);
+#pragma unroll
+      for (int k = 0; k < NP; k += 2) {
+        const float2 w = __ffma2_rn(b2, make_float2(u[k], u[k + 1]),
+                                    __fmul2_rn(g2, make_float2(R[k], R[k + 1])));
+        o[k] = w.x;
+        o[k + 1] = w.y;
+      }
     } else {
 #pragma unroll
       for (int k = 0; k < NP; ++k) o[k] = c.beta * u[k] + gam * R[k];
@@ -668,6 +756,12 @@ StageTab<T, P> make_tab(const Gll &g) {
     t.Dout[n + m] = -t.D[m];
   }
   t.inv_w = (T)(1.0 / g.w[0]);
+  for (int ip = 0; ip < n / 2; ++ip)
+    for (int m = 0; m < n; ++m) {
+      t.D2x[ip * n + m].x = t.D2[2 * ip * n + m];
+      t.D2x[ip * n + m].y = t.D2[(2 * ip + 1) * n + m];
+    }
+  for (int k = 0; k < n * n; ++k) t.D2y[k].x = t.D2y[k].y = t.D2[k];
   return t;
 }
 
