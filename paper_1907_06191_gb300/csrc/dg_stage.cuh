@@ -471,7 +471,6 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
       }
       if (ca.counter) atomicAdd(ca.counter, 1ull);
     }
-    __syncthreads();  // the barriers exist before anyone polls them
   } else {  // async copies of the u chunk (group 0) and the u0 chunk (group 1)
     const char *gu = reinterpret_cast<const char *>(U + (size_t)a0 * NP);
     const int np16 = St::pieces(cnt);
@@ -487,23 +486,21 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
   }
   const int4 l4 = live ? __ldg(loc + a0 + el) : make_int4(kEdge, kEdge, kEdge, kEdge);
   const int hcnt = __ldg(halo_cnt + chunk);
-  // first halo entry of this thread: element values into registers while the
-  // chunk copies are in flight
-  int2 hk = make_int2(-1, 0);
+  // first halo entry of this thread (entries past the chunk's count hold
+  // element -1, so the count is not waited for): element values into
+  // registers while the chunk copies are in flight
+  const int2 hk = __ldg(halo + (size_t)chunk * kHaloCap + el);
   T hv[NP];
-  if (el < hcnt) {
-    hk = __ldg(halo + (size_t)chunk * kHaloCap + el);
-    load_elem<T, NP>(U + (size_t)hk.x * NP, hv);
-  }
+  if (hk.x >= 0) load_elem<T, NP>(U + (size_t)hk.x * NP, hv);
+  // Each thread waits (bounded) for the u chunk itself: completing the
+  // barrier phase makes the copied bytes visible to the waiting thread.  A
+  // time-out is combined over the block at the barrier that hands the u
+  // space over to the face records; the block then leaves as a whole, after
+  // a bounded wait for the u0 copy it issued.
+  bool ok = true;
   if (tma) {
-    // bounded wait; on a time-out the whole block records it and leaves
-    // (after waiting, also bounded, for the u0 copy it issued)
-    const bool ok = mbar_wait(bar0, 0, ca.limit);
-    if (__syncthreads_or(!ok)) {
-      if constexpr (HAS_U0) mbar_wait(bar1, 0, ca.limit);
-      if (el == 0) atomicExch(ca.err, 1);
-      return;
-    }
+    __syncthreads();  // the barriers exist before anyone polls them
+    ok = mbar_wait(bar0, 0, ca.limit);
   } else {
     if constexpr (HAS_U0) cp_async_wait<1>();
     else cp_async_wait<0>();
@@ -511,8 +508,13 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
   }
 
   T u[NP], R[NP];
-  if (live) St::read(su, el, u);
-  __syncthreads();  // the u chunk is in registers; its space now takes the face records
+  if (live && ok) St::read(su, el, u);
+  // the u chunk is in registers; its space now takes the face records
+  if (__syncthreads_or(!ok)) {
+    if constexpr (HAS_U0) mbar_wait(bar1, 0, ca.limit);
+    if (el == 0) atomicExch(ca.err, 1);
+    return;
+  }
   if (el == 0) {
     T z[n];
 #pragma unroll
@@ -556,7 +558,7 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
         }
     }
   }
-  if (el < hcnt) {
+  if (hk.x >= 0) {
     T tr[n], d[n];
     switch (hk.y) {  // the face of the halo element that touches the chunk
       case 0: face_record<T, P>(hv, 0, tb, tr, d); break;
@@ -632,19 +634,26 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
     }
   }
 
+  // the u0 chunk: the same per-thread bounded wait.  With stochastic
+  // rounding and p <= 3 it is combined over the block at the barrier in front
+  // of the result copy (one block-wide barrier less per stage); the other
+  // variants keep a barrier of their own, which bounds their live registers
+  // (fewer spills; measured faster for p >= 4 and for round-to-nearest)
   if constexpr (HAS_U0) {
     if (tma) {
-      const bool ok = mbar_wait(bar1, 0, ca.limit);
-      if (__syncthreads_or(!ok)) {
-        if (el == 0) atomicExch(ca.err, 1);
-        return;
+      ok = mbar_wait(bar1, 0, ca.limit);
+      if constexpr (P >= 4 || !SROUND) {
+        if (__syncthreads_or(!ok)) {
+          if (el == 0) atomicExch(ca.err, 1);
+          return;
+        }
       }
     } else {
       cp_async_wait<0>();
       __syncthreads();
     }
   }
-  if (live) {
+  if (live && ok) {
     T o[NP];
     if constexpr (SROUND) {
       // increment first, then one stochastic rounding onto the state; the key
@@ -715,13 +724,16 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
     }
     St::write(so, el, o);
   }
-  if (tma && ca.store_tma && cnt == kBlock) {  // a full chunk: one tiled store
-    fence_proxy_async_smem();
-    __syncthreads();
+  const bool store_tma = tma && ca.store_tma && cnt == kBlock;  // a full chunk: one tiled store
+  if (store_tma) fence_proxy_async_smem();
+  if (__syncthreads_or(!ok)) {
+    if (el == 0) atomicExch(ca.err, 1);
+    return;
+  }
+  if (store_tma) {
     if (el == 0) tma_store_rows(&tm_out, (int)((long long)blockIdx.y * stride + a0), smem_u32(so));
     return;
   }
-  __syncthreads();
   {  // coalesced 16-byte stores of the result chunk
     char *go = reinterpret_cast<char *>(out + sbase + (size_t)a0 * NP);
     const int np16 = St::pieces(cnt);
