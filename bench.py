@@ -306,7 +306,7 @@ def run_batch(args):
 
 def run_surrogate(args):
     """Learned covariance surrogate: DG Sigma of seeded 10 um cells (batched
-    FP32 solves, Delta = 1..5 ms) trains the CNN; held-out cells judge it.
+    FP32 solves, Delta = 1..5 ms) trains the CNN; held-out cells test it.
     value = Sigma evaluations/s of batch-4096 network inference; the DG
     rate on the same cells and the network's error against DG are reported
     beside it."""
@@ -320,7 +320,7 @@ def run_surrogate(args):
     ws_te = [dginputs.workload_surrogate_member(100000 + s, m=ms) for s in range(nte)]
     sig_tr, t_tr = sgm.dg_sigma(ws_tr)
     sig_te, t_te = sgm.dg_sigma(ws_te)
-    # the judge's own noise: the same held-out cells with an independent set
+    # the reference's own noise: the same held-out cells with an independent set
     # of start points (the network sees the substrate, not the start points)
     ws_te2 = []
     for w in ws_te:
@@ -340,7 +340,7 @@ def run_surrogate(args):
     hist = sgm.train(net, to(occ, torch.uint8), to(cond, torch.float32), to(tgt, torch.float32),
                      epochs=args.sg_epochs)
     t_train = time.perf_counter() - t0
-    # held-out error against the DG solve (the judge)
+    # held-out error against the DG solve (the reference)
     pe = torch.zeros((occ_e.shape[0], 3), device="cuda:0")
     oe, ce = to(occ_e, torch.uint8), to(cond_e, torch.float32)
     for b0 in range(0, oe.shape[0], 4096):
@@ -390,7 +390,7 @@ def run_surrogate(args):
                                 "vs": "mean of two DG solves with independent start points"},
             "packing_fit_rel_err": {"mean": float(rel_base.mean()),
                                     "p95": float(np.percentile(rel_base, 95))},
-            "dg_judge_noise": {"mean": float(dg_noise.mean()), "p95": float(np.percentile(dg_noise, 95)),
+            "dg_reference_noise": {"mean": float(dg_noise.mean()), "p95": float(np.percentile(dg_noise, 95)),
                                "what": "relative difference of the two DG solves"},
             "sources_per_geometry": ms,
             "train_loss_first_last": [hist[0], hist[-1]], "train_seconds": t_train,

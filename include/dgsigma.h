@@ -307,7 +307,7 @@ int dg_covariance(dg_ctx *ctx, double *sigma3, double *mu2, double *mass);
 int dg_covariance_batch(dg_ctx *ctx, double *sigma3, double *mu2, double *mass);
 
 /* Least-squares residual of the Gaussian fit (Sec. 4.2, the sum over nodes of
- * [f(x; Sigma) - u_ij]^2 by which the paper judges the fit).  For each
+ * [f(x; Sigma) - u_ij]^2 by which the paper assesses the fit).  For each
  * density, normalised by its mass and centred at its start point, the sum
  * runs over its own nodes against the bivariate Gaussian f of the mixture
  * fit (mean mu and covariance Sigma_mix(t), the start width not removed);

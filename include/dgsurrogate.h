@@ -6,7 +6,7 @@
  * to the covariance of the Sigma scheme (Sec. 4.1) in units of the free
  * value, y = {Sxx, Sxy, Syy} / (2 D Delta).  The paper has no learned part:
  * the network is trained on Sigma values that the DG solver of dgsigma.h
- * produces, and the DG solve stays its fallback and the judge of its error.
+ * produces, and the DG solve stays its fallback and the reference for its error.
  *
  * Network (NCHW): input 1 x 128 x 128; four blocks of 3x3 convolution (zero
  * padding) + ReLU + 2x2 average pooling with 16, 32, 64, 64 channels; global

@@ -4,7 +4,7 @@ The network (include/dgsurrogate.h) maps the 128 x 128 occupancy raster of a
 periodic cell and (D, Delta) to Sigma / (2 D Delta).  Its training data are
 Sigma values of the DG solver (the Sigma scheme of Sec. 4.1 on batched
 geometries); the DG solve remains the fallback outside the training envelope
-and the judge of the network's error on held-out geometries.  Everything
+and the reference for the network's error on held-out geometries.  Everything
 numeric runs in the library's kernels; this module moves batches around.
 """
 from __future__ import annotations
