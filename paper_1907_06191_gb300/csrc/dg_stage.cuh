@@ -298,11 +298,12 @@ __device__ __forceinline__ float2 add_stochastic2(float2 base, float2 inc, uint3
   return make_float2(fabsf(err.x) > thr.x ? up.x : s.x, fabsf(err.y) > thr.y ? up.y : s.y);
 }
 
-// FP32 with an even number of nodes per line: pairs of nodes go through the
-// packed two-lane instructions (fma.rn.f32x2 and friends; each lane rounds
-// like the scalar instruction).
+// FP32: pairs of nodes go through the packed two-lane instructions
+// (fma.rn.f32x2 and friends; each lane rounds like the scalar instruction);
+// with an odd number of nodes per line the last node of a line (and the last
+// node of the element) takes the scalar instruction.
 template <typename T, int P>
-constexpr bool kPacked = sizeof(T) == 4 && (P + 1) % 2 == 0;
+constexpr bool kPacked = sizeof(T) == 4;
 
 // Outward normal derivative (reference units) at the nodes of face f: the
 // face's signed row of D applied along the lines normal to the face.
@@ -545,6 +546,17 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
           R[j * n + 2 * ip] = s.x;
           R[j * n + 2 * ip + 1] = s.y;
         }
+      if constexpr (n % 2 == 1) {  // the last node of each row
+        constexpr int i = n - 1;
+#pragma unroll
+        for (int j = 0; j < n; ++j) {
+          T s = 0;
+#pragma unroll
+          for (int m = 0; m < n; ++m)
+            s += tb.D2[i * n + m] * u[j * n + m] + tb.D2[j * n + m] * u[m * n + i];
+          R[j * n + i] = s;
+        }
+      }
     } else {
 #pragma unroll
       for (int j = 0; j < n; ++j)
@@ -670,7 +682,7 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
       if constexpr (kPacked<T, P>) {  // the same arithmetic, two nodes per instruction
         const float2 b2 = make_float2(c.beta, c.beta), g2 = make_float2(gam, gam);
 #pragma unroll
-        for (int k = 0; k < NP; k += 2) {
+        for (int k = 0; k + 1 < NP; k += 2) {
           const float2 u2 = make_float2(u[k], u[k + 1]), gr = __fmul2_rn(g2, make_float2(R[k], R[k + 1]));
           float2 bs, in;
           if constexpr (HAS_U0) {
@@ -683,6 +695,12 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
           const float2 w = add_stochastic2(bs, in, h + (uint32_t)k, h + (uint32_t)(k + 1));
           o[k] = w.x;
           o[k + 1] = w.y;
+        }
+        if constexpr (NP % 2 == 1) {  // the last node on its own
+          constexpr int k = NP - 1;
+          const T bs = HAS_U0 ? o[k] : c.beta * u[k];
+          const T in = HAS_U0 ? fmaf(c.beta, u[k] - o[k], gam * R[k]) : gam * R[k];
+          o[k] = add_stochastic(bs, in, h + (uint32_t)k);
         }
       } else {
 #pragma unroll
@@ -697,13 +715,17 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
       if constexpr (kPacked<T, P>) {  // o + (beta (u - o) + gam R)
         const float2 b2 = make_float2(c.beta, c.beta), g2 = make_float2(gam, gam);
 #pragma unroll
-        for (int k = 0; k < NP; k += 2) {
+        for (int k = 0; k + 1 < NP; k += 2) {
           const float2 o2 = make_float2(o[k], o[k + 1]);
           const float2 d = __ffma2_rn(o2, make_float2(-1.0f, -1.0f), make_float2(u[k], u[k + 1]));
           const float2 w = __fadd2_rn(
               o2, __ffma2_rn(b2, d, __fmul2_rn(g2, make_float2(R[k], R[k + 1]))));
           o[k] = w.x;
           o[k + 1] = w.y;
+        }
+        if constexpr (NP % 2 == 1) {
+          constexpr int k = NP - 1;
+          o[k] = o[k] + fmaf(c.beta, u[k] - o[k], gam * R[k]);
         }
       } else {
 #pragma unroll
@@ -712,11 +734,15 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
     } else if constexpr (kPacked<T, P>) {
       const float2 b2 = make_float2(c.beta, c.beta), g2 = make_float2(gam, gam);
 #pragma unroll
-      for (int k = 0; k < NP; k += 2) {
+      for (int k = 0; k + 1 < NP; k += 2) {
         const float2 w = __ffma2_rn(b2, make_float2(u[k], u[k + 1]),
                                     __fmul2_rn(g2, make_float2(R[k], R[k + 1])));
         o[k] = w.x;
         o[k + 1] = w.y;
+      }
+      if constexpr (NP % 2 == 1) {
+        constexpr int k = NP - 1;
+        o[k] = fmaf(c.beta, u[k], gam * R[k]);
       }
     } else {
 #pragma unroll
