@@ -298,6 +298,16 @@ __device__ __forceinline__ float2 add_stochastic2(float2 base, float2 inc, uint3
   return make_float2(fabsf(err.x) > thr.x ? up.x : s.x, fabsf(err.y) > thr.y ? up.y : s.y);
 }
 
+// Fused multiply-add in the element type: sums of products are written as
+// chains of these, one rounding and one FP64 / FP32 pipe instruction per
+// product (a * b + c * d left to the compiler becomes a multiply, a fused
+// multiply-add and an add).
+template <typename T>
+__device__ __forceinline__ T fmaT(T a, T b, T c) {
+  if constexpr (sizeof(T) == 4) return fmaf(a, b, c);
+  else return fma(a, b, c);
+}
+
 // FP32: pairs of nodes go through the packed two-lane instructions
 // (fma.rn.f32x2 and friends; each lane rounds like the scalar instruction);
 // with an odd number of nodes per line the last node of a line (and the last
@@ -553,7 +563,7 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
           T s = 0;
 #pragma unroll
           for (int m = 0; m < n; ++m)
-            s += tb.D2[i * n + m] * u[j * n + m] + tb.D2[j * n + m] * u[m * n + i];
+            s = fmaT(tb.D2[j * n + m], u[m * n + i], fmaT(tb.D2[i * n + m], u[j * n + m], s));
           R[j * n + i] = s;
         }
       }
@@ -565,7 +575,7 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
           T s = 0;
 #pragma unroll
           for (int m = 0; m < n; ++m)
-            s += tb.D2[i * n + m] * u[j * n + m] + tb.D2[j * n + m] * u[m * n + i];
+            s = fmaT(tb.D2[j * n + m], u[m * n + i], fmaT(tb.D2[i * n + m], u[j * n + m], s));
           R[j * n + i] = s;
         }
     }
@@ -624,13 +634,17 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
         for (int t = 0; t < n; ++t) {
           const T um = u[Fc::own(f, t)];
           gs[t] = cg_up * up[t] + cg_um * um;
-          R[Fc::own(f, t)] -= c_od * od[t] + c_odn * odn[t] + c_um * um + c_up * up[t];
+          T r = R[Fc::own(f, t)];
+          r = fmaT(-c_od, od[t], r);
+          r = fmaT(-c_odn, odn[t], r);
+          r = fmaT(-c_um, um, r);
+          R[Fc::own(f, t)] = fmaT(-c_up, up[t], r);
         }
       } else {
 #pragma unroll
         for (int t = 0; t < n; ++t) {
           gs[t] = cg_up * up[t] + cg_um * u[Fc::own(f, t)];
-          R[Fc::own(f, t)] -= c_od * od[t] + c_odn * odn[t];
+          R[Fc::own(f, t)] = fmaT(-c_odn, odn[t], fmaT(-c_od, od[t], R[Fc::own(f, t)]));
         }
       }
       // lifting of the u-flux jump: column (x-faces) or row (y-faces) of D

@@ -346,7 +346,8 @@ __global__ void __launch_bounds__(kBlock, tri_min_blocks<T>())
       for (int i = 0; i < N; ++i) {
         T a = 0;
 #pragma unroll
-        for (int j = 0; j < N; ++j) a += tb.G[o][0][i * N + j] * qx[j] + tb.G[o][1][i * N + j] * qy[j];
+        for (int j = 0; j < N; ++j)
+          a = fmaT(tb.G[o][1][i * N + j], qy[j], fmaT(tb.G[o][0][i * N + j], qx[j], a));
         R[i] = a;
       }
     }
