@@ -4,6 +4,7 @@
 // kernels; every arithmetic step of the path runs in the kernels of
 // dg_stage.cuh, dg_geometry.cu and dg_reduce.cu.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -131,12 +132,15 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // Tensor maps of the three state arrays: rows of np values, boxes of kBlock
 // rows, the hardware swizzle that matches Stage's layout (32, 64 or 128 bytes
 // per row; none otherwise).  Left unset (cp.async copies) when the rows are
-// not whole 16-byte slots or the encoder is unavailable.
+// not whole 16-byte slots, when the row count m * n_pad does not fit the
+// tensor copies' 32-bit row coordinate (possible at p = 1, whose rows are
+// 16 or 32 bytes), or when the encoder is unavailable.
 void make_tensor_maps(Ctx &c) {
   c.tmap_ok = false;
   if (c.triangles() || !c.d_state) return;
   const size_t row_bytes = (size_t)c.np() * c.esize();
   if (row_bytes % 16 != 0) return;
+  if ((long long)c.m * c.geo.n_pad > (long long)INT_MAX) return;
   const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return;
   const CUtensorMapSwizzle sw = row_bytes == 32    ? CU_TENSOR_MAP_SWIZZLE_32B

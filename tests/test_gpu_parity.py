@@ -333,6 +333,49 @@ def test_many_sources_and_isolated_element():
     assert abs(np.sum(W * got[0, 4, 4]) / np.sum(W * init[4, 4]) - 1) < 1e-13
 
 
+def test_state_rows_beyond_the_tensor_copy_coordinate():
+    """More state rows (densities x padded elements) than a 32-bit row
+    coordinate holds: the tensor copies address rows with a signed 32-bit
+    coordinate, so the library must move such a state with the per-thread
+    copies, which index in 64 bits.  p = 1 FP32 (16-byte rows, 111 GB for the
+    three state arrays); round-to-nearest, so that the arithmetic of a
+    density does not depend on its index and densities that share a start
+    point agree bit for bit with a small context (tensor copies) and with
+    each other."""
+    act, rng = _random_mesh(41, 200, 200, frac=0.12)
+    h, m, K, nsteps = 0.25, 65535, 7, 3
+    pts = _sources_in(act, rng, K, h, 0.0, 0.0, margin=30)
+    xy = pts[np.arange(m) % K]
+    picks = (0, K - 1, 40000, m - 1)
+    cells = [(int(x / h) + dx, int(y / h) + dy) for x, y in pts
+             for dx in (-1, 0, 1) for dy in (-1, 0, 1)]
+    kw = dict(D=1.0, sigma0=0.3, rounding=dg.DG_ROUND_NEAREST)
+    with _solver(1, "f32", **kw) as big:
+        big.set_geometry_mask(act, h)
+        big.set_sources(xy)
+        inf = big.info()
+        assert inf.m * inf.n_elements_padded > 2**31 - 1
+        dt, _ = big.query_dt()
+        big.step(nsteps, dt)
+        got = big.get_elements([(s, ex, ey) for s in picks for ex, ey in cells])
+        mom = big.moments()[list(picks)]
+        big_tensor = big.debug_copies(0)
+    with _solver(1, "f32", **kw) as small:
+        small.set_geometry_mask(act, h)
+        small.set_sources(pts)
+        small.step(nsteps, dt)
+        ref = small.get_elements([(s % K, ex, ey) for s in picks for ex, ey in cells])
+        mom_ref = small.moments()[[s % K for s in picks]]
+        nodes = small.get_nodes()
+        small_tensor = small.debug_copies(0)
+    assert big_tensor == 0 and small_tensor > 0
+    assert np.array_equal(got, ref)
+    assert np.array_equal(mom, mom_ref)
+    mesh = O.Mesh(p=1, active=act, h=h, k0=1.0)
+    orc = O.rk3(mesh, O.init_gaussian(mesh, *pts[(m - 1) % K], 0.3), nsteps, dt)
+    assert _rel(nodes[(m - 1) % K], orc) < 1e-5
+
+
 @pytest.mark.parametrize("prec,p", [("f32", 3), ("f32", 5), ("f64", 3)])
 def test_mass_conserved_long_run(prec, p):
     """Walls (removed-wall fluxes) and a periodic outer edge: the scheme
