@@ -466,8 +466,8 @@ int set_parts(dg_ctx *ctx, const std::vector<PartSpec> &parts) {
 
 bool check_disk_args(const double *cx, const double *cy, const double *r, int nd, double L,
                      int n_cell, int tiles, std::string &why) {
-  if (nd < 0 || (nd > 0 && (!cx || !cy || !r)) || !(L > 0.0) || n_cell < 1 || tiles < 1 ||
-      tiles % 2 == 0) {
+  if (nd < 0 || (nd > 0 && (!cx || !cy || !r)) || !(L > 0.0) || !std::isfinite(L) || n_cell < 1 ||
+      tiles < 1 || tiles % 2 == 0) {
     why = "bad disk geometry arguments (tiles must be odd)";
     return false;
   }
@@ -477,7 +477,7 @@ bool check_disk_args(const double *cx, const double *cy, const double *r, int nd
     return false;
   }
   for (int d = 0; d < nd; ++d)
-    if (!(r[d] >= 0.0) || !std::isfinite(cx[d]) || !std::isfinite(cy[d])) {
+    if (!(r[d] >= 0.0) || !std::isfinite(r[d]) || !std::isfinite(cx[d]) || !std::isfinite(cy[d])) {
       why = "bad disk " + std::to_string(d);
       return false;
     }
@@ -690,7 +690,8 @@ int dg_set_geometry_mask(dg_ctx *ctx, const uint8_t *active, int nx, int ny, dou
                          double x0, double y0) {
   if (!ctx) return DG_EINVAL;
   Ctx &c = ctx->c;
-  if (!active || nx < 1 || ny < 1 || !(h > 0.0) || !std::isfinite(x0) || !std::isfinite(y0))
+  if (!active || nx < 1 || ny < 1 || !(h > 0.0) || !std::isfinite(h) || !std::isfinite(x0) ||
+      !std::isfinite(y0))
     return fail(ctx, DG_EINVAL, "bad mask geometry arguments");
   if ((long long)nx * ny > (1ll << 31) - 1) return fail(ctx, DG_EINVAL, "domain too large");
   CK(cudaSetDevice(c.device), "set device");
@@ -745,8 +746,8 @@ int dg_set_geometry_batch(dg_ctx *ctx, int G, const int *ndisks, const double *c
 
 int dg_rasterize_disks(const double *cx, const double *cy, const double *r, int ndisks,
                        double L, int npix, uint8_t *out) {
-  if (!out || ndisks < 0 || (ndisks > 0 && (!cx || !cy || !r)) || !(L > 0.0) || npix < 1 ||
-      npix > 16384)
+  if (!out || ndisks < 0 || (ndisks > 0 && (!cx || !cy || !r)) || !(L > 0.0) || !std::isfinite(L) ||
+      npix < 1 || npix > 16384)
     return DG_EINVAL;
   const int nd = ndisks > 0 ? ndisks : 1;
   double *d = nullptr;

@@ -55,6 +55,13 @@ def test_host_only_calls(L):
     assert L.dg_create(ctypes.byref(bad), ctypes.byref(h)) == dg.DG_EINVAL
     assert L.dg_create(None, ctypes.byref(h)) == dg.DG_EINVAL
     assert L.dg_step(None, 1, 1.0) == dg.DG_EINVAL
+    # raster arguments are checked before any device call: a cell side that is
+    # not a positive finite number is refused
+    out = (ctypes.c_uint8 * 16)()
+    one = (ctypes.c_double * 1)(1.0)
+    for side in (0.0, -1.0, float("inf"), float("nan")):
+        assert L.dg_rasterize_disks(one, one, one, 1, ctypes.c_double(side), 4, out) == dg.DG_EINVAL
+    assert L.dg_rasterize_disks(one, one, one, 1, ctypes.c_double(2.0), 0, out) == dg.DG_EINVAL
 
 
 def test_no_device_is_an_error_not_a_crash(L):

@@ -452,6 +452,21 @@ def test_argument_errors():
         with pytest.raises(dg.DgError) as ei:
             s.set_geometry_mask(np.zeros((4, 4), np.uint8), 1.0)
         assert ei.value.code == dg.DG_EINVAL
+        # element sides, cell sides and radii must be finite
+        for h in (0.0, float("inf"), float("nan")):
+            with pytest.raises(dg.DgError) as ei:
+                s.set_geometry_mask(act, h)
+            assert ei.value.code == dg.DG_EINVAL
+        one = np.array([1.0])
+        for L, r in ((float("inf"), 0.5), (4.0, float("inf"))):
+            with pytest.raises(dg.DgError) as ei:
+                s.set_geometry_disks(one, one, np.array([r]), L, 8, 1)
+            assert ei.value.code == dg.DG_EINVAL
+        # after the refusals a good geometry still works
+        s.set_geometry_mask(act, 1.0)
+        s.set_sources(np.array([[5.5, 5.5]]))
+        dt, _ = s.query_dt()
+        s.step(1, dt)
 
 
 def test_torch_stream_and_bound_state():
