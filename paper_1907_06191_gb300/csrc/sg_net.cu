@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/dgsigma.h"
+#include "../../include/dgsurrogate.h"
 
 namespace dg {
 cudaError_t dev_alloc(void **p, size_t bytes);  // the library's allocator (dg_api.cu)
