@@ -463,12 +463,21 @@ int sg_create(int max_batch, unsigned long long seed, int device, sg_net **out) 
   al(&n.y, (size_t)max_batch * kOut * 4); al(&n.dy, (size_t)max_batch * kOut * 4);
   al(&n.loss, 4);
   if (!ok) { free_net(n); cudaStreamDestroy(n.stream); delete net; return DG_ENOMEM; }
-  cudaMemcpy(n.p, h.data(), off * 4, cudaMemcpyHostToDevice);
-  cudaMemset(n.m, 0, off * 4);
-  cudaMemset(n.v, 0, off * 4);
-  cudaMemset(n.g, 0, off * 4);
-  k_to_bf16<<<blocks((long long)off), 256, 0, n.stream>>>(n.p, (long long)off, n.pbf);
-  if (cudaStreamSynchronize(n.stream) != cudaSuccess) { free_net(n); delete net; return DG_ECUDA; }
+  cudaError_t e = cudaMemcpyAsync(n.p, h.data(), off * 4, cudaMemcpyHostToDevice, n.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n.m, 0, off * 4, n.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n.v, 0, off * 4, n.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n.g, 0, off * 4, n.stream);
+  if (e == cudaSuccess) {
+    k_to_bf16<<<blocks((long long)off), 256, 0, n.stream>>>(n.p, (long long)off, n.pbf);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(n.stream);
+  if (e != cudaSuccess) {
+    free_net(n);
+    cudaStreamDestroy(n.stream);
+    delete net;
+    return DG_ECUDA;
+  }
   *out = net;
   return DG_OK;
 }
@@ -540,7 +549,7 @@ int sg_train_step(sg_net *net, const uint8_t *occ, const float *cond, const floa
                   float lr, float *loss_host) {
   int r = check_io(net, occ, cond, B);
   if (r != DG_OK) return r;
-  if (!target || !(lr > 0.0f)) return DG_EINVAL;
+  if (!target || !(lr > 0.0f) || !std::isfinite(lr)) return DG_EINVAL;
   Net &n = net->n;
   SGK(cudaSetDevice(n.device));
   if ((r = forward(net, occ, cond, B)) != DG_OK) return r;
