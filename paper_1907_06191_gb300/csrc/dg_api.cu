@@ -1191,9 +1191,19 @@ int dg_set_state(dg_ctx *ctx, const void *host, size_t bytes) {
   if (hdr[0] != kStateMagic) return fail(ctx, DG_EINVAL, "not a snapshot");
   if (hdr[1] != (uint64_t)c.cfg.precision || hdr[2] != (uint64_t)c.cfg.p || hdr[4] != (uint64_t)c.geo.n_pad)
     return fail(ctx, DG_EINVAL, "snapshot does not match the context (precision, order or mesh)");
-  if (hdr[7] > bytes || hdr[3] < 1 || hdr[3] > 65535) return fail(ctx, DG_EINVAL, "truncated snapshot");
+  if (hdr[3] < 1 || hdr[3] > 65535) return fail(ctx, DG_EINVAL, "snapshot with a bad number of densities");
   const int m = (int)hdr[3];
   const size_t nd = (size_t)m * c.geo.G();
+  // the size the header's m implies for this context must be the stated one
+  // and fit the caller's buffer: a corrupt header must not make the copies
+  // below read past it
+  const size_t need = 64 + nd * 16 + nd * kMomFields * 8 + (size_t)m * c.field_elems() * c.esize();
+  if (hdr[7] != need) return fail(ctx, DG_EINVAL, "snapshot does not match the context (size)");
+  if (need > bytes) return fail(ctx, DG_EINVAL, "truncated snapshot");
+  double t_snap = 0.0;
+  std::memcpy(&t_snap, &hdr[6], 8);
+  if (!std::isfinite(t_snap) || t_snap < 0.0 || (long long)hdr[5] < 0)
+    return fail(ctx, DG_EINVAL, "snapshot with a bad time or step count");
   const char *p = (const char *)host;
   std::vector<double> xy(2 * nd);
   std::memcpy(xy.data(), p + 64, nd * 16);

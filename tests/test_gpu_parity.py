@@ -212,6 +212,16 @@ def test_propagate_and_checkpoint_bitwise(small_ref):
         ref_sig = a.covariance()[0]
     with _solver(w.p, "f64", **kw) as b:
         b.set_geometry_disks(w.disks.cx, w.disks.cy, w.disks.r, w.L, w.n_cell, w.tiles)
+        # damaged snapshots are refused before anything is read past the buffer:
+        # a truncated one, and headers whose density count or size field was changed
+        hdr = np.frombuffer(blob[:64], dtype=np.uint64).copy()
+        bad_m, bad_size = hdr.copy(), hdr.copy()
+        bad_m[3] = 4000
+        bad_size[7] = hdr[7] - 8
+        for bad in (blob[:-8], bad_m.tobytes() + blob[64:], bad_size.tobytes() + blob[64:]):
+            with pytest.raises(dg.DgError) as ei:
+                b.set_state(bad)
+            assert ei.value.code == dg.DG_EINVAL
         b.set_state(blob)
         assert b.info().steps == 100
         b.step(100, dt)
