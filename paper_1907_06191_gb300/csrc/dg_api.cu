@@ -1010,8 +1010,8 @@ int dg_mixture_covariance(dg_ctx *ctx, const double *mom, const double *mom0, in
   std::vector<double> h(2 * (size_t)m * kMomFields, 0.0);
   for (int s = 0; s < m; ++s)
     for (int f = 0; f < 6; ++f) {
-      h[(size_t)s * kMomFields + f] = mom[s * 6 + f];
-      h[((size_t)m + s) * kMomFields + f] = mom0[s * 6 + f];
+      h[(size_t)s * kMomFields + f] = mom[(size_t)s * 6 + f];
+      h[((size_t)m + s) * kMomFields + f] = mom0[(size_t)s * 6 + f];
     }
   double *d = nullptr;
   CK(dev_alloc(&d, sizeof(double) * (h.size() + kCovOut)), "moment buffer");
