@@ -97,13 +97,14 @@ def test_shard_partition():
             assert max(sizes) - min(sizes) <= 1
 
 
-def test_sharded_moments_equal_unsharded_bitwise():
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_moments_equal_unsharded_bitwise(world):
     import oracle as O
     O.build()
     mesh, src = _problem()
     ref = _moments_for(mesh, src)
-    res, codes = _run(2)
-    for r in (0, 1):
+    res, codes = _run(world)
+    for r in range(world):
         status, allm = res[r]
         assert status == "ok", allm
         assert np.array_equal(allm, ref)
