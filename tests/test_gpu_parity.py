@@ -408,20 +408,22 @@ def test_mass_conserved_long_run(prec, p):
     assert drift < (2e-6 if prec == "f32" else 1e-12)
 
 
-def test_fp32_stochastic_rounding_keeps_sigma_on_the_fp64_path():
+@pytest.mark.parametrize("p", [3, 5])
+def test_fp32_stochastic_rounding_keeps_sigma_on_the_fp64_path(p):
     """Round-to-nearest of the FP32 state biases long runs: with p = 3 the
     density lags the FP64 path and Sigma falls ~1e-6 behind after 6000 steps.
     Stochastic rounding of every stage result (the default) is unbiased and
-    keeps the gap at the 1e-7 level."""
+    keeps the gap at the 1e-7 level, at p = 3 and at the p = 5 order of the
+    1024^2-element workload."""
     nel, h = 96, 0.15625
     act = np.ones((nel, nel), np.uint8)
     c = nel * h / 2
     src = np.array([[c + 0.11, c - 0.07], [c - 0.2, c + 0.13], [c + 0.05, c + 0.31]])
-    kw = dict(p=3, D=2.0, sigma0=0.2, boundary=dg.DG_BC_PERIODIC)
+    kw = dict(D=2.0, sigma0=0.2, boundary=dg.DG_BC_PERIODIC)
     out = {}
     for name, prec, rnd in (("f64", "f64", dg.DG_ROUND_NEAREST), ("rn", "f32", dg.DG_ROUND_NEAREST),
                             ("sr", "f32", dg.DG_ROUND_STOCHASTIC)):
-        with _solver(3, prec, rounding=rnd, **{k: v for k, v in kw.items() if k != "p"}) as s:
+        with _solver(p, prec, rounding=rnd, **kw) as s:
             s.set_geometry_mask(act, h)
             s.set_sources(src)
             if name == "f64":
@@ -429,8 +431,10 @@ def test_fp32_stochastic_rounding_keeps_sigma_on_the_fp64_path():
             s.step(6000, dt)
             out[name] = s.covariance()[0]
     err = {k: float(np.abs(out[k] - out["f64"]).max() / np.abs(out["f64"]).max()) for k in ("rn", "sr")}
-    print("FP32 Sigma error after 6000 steps:", err)
-    assert err["sr"] < 3e-7
+    print(f"p = {p}: FP32 Sigma error after 6000 steps:", err)
+    # measured on GB300 (bit-reproducible): p = 3 rn 5.1e-7, sr 1.1e-7;
+    # p = 5 rn 1.5e-6, sr 2.9e-7 (36 rounded values per element instead of 16)
+    assert err["sr"] < (3e-7 if p == 3 else 6e-7)
 
 
 def test_unstable_step_is_reported():
