@@ -344,6 +344,7 @@ int build_geometry(Geometry &geo, const std::vector<PartSpec> &specs, int period
     const uint8_t *m = geo.d_mask + p.dense_off;
     k_tile_count<<<nt, kTile * kTile, 0, s>>>(m, p.nx, p.ny, d_count);
     k_scan_counts<<<1, 1024, 0, s>>>(d_count, nt, offs[g]);
+    GK(cudaGetLastError(), "tile scan", DG_ECUDA);
     int total = 0;
     GK(cudaMemcpyAsync(&total, offs[g] + nt, sizeof(int), cudaMemcpyDeviceToHost, s), "tile scan", DG_ECUDA);
     GK(cudaStreamSynchronize(s), "tile scan", DG_ECUDA);
@@ -369,10 +370,11 @@ int build_geometry(Geometry &geo, const std::vector<PartSpec> &specs, int period
   GK(dev_alloc(&geo.d_exy, sizeof(int2) * (size_t)elems), "coordinate allocation", DG_ENOMEM);
   const int4 pad = make_int4(kEdge, kEdge, kEdge, kEdge);
   k_fill_int4<<<(unsigned)((elems + 255) / 256), 256, 0, s>>>(geo.d_nb, elems, pad);
-  cudaMemsetAsync(geo.d_exy, 0, sizeof(int2) * (size_t)elems, s);
+  GK(cudaGetLastError(), "neighbour table", DG_ECUDA);
+  GK(cudaMemsetAsync(geo.d_exy, 0, sizeof(int2) * (size_t)elems, s), "coordinate table", DG_ECUDA);
   int *d_bad = nullptr;
   GK(tmp.alloc(&d_bad, 1), "flag allocation", DG_ENOMEM);
-  cudaMemsetAsync(d_bad, 0, sizeof(int), s);
+  GK(cudaMemsetAsync(d_bad, 0, sizeof(int), s), "flag", DG_ECUDA);
   for (int g = 0; g < G; ++g) {
     const GeoPart &p = geo.parts[g];
     const int tx = (p.nx + kTile - 1) / kTile, ty = (p.ny + kTile - 1) / kTile;
@@ -382,6 +384,7 @@ int build_geometry(Geometry &geo, const std::vector<PartSpec> &specs, int period
     k_neighbours<<<(unsigned)((p.n_active + 255) / 256), 256, 0, s>>>(
         geo.d_exy, ci, (int)p.off, (int)p.n_active, p.nx, p.ny, p.periodic, (int)p.off,
         (int)(p.off + p.n_active), geo.d_nb, d_bad);
+    GK(cudaGetLastError(), "neighbour table", DG_ECUDA);
   }
   int bad = 0;
   GK(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s), "neighbour table", DG_ECUDA);
@@ -427,6 +430,7 @@ int build_geometry(Geometry &geo, const std::vector<PartSpec> &specs, int period
   GK(dev_alloc(&geo.d_halo_cnt, sizeof(int) * ((size_t)nch + 1)), "halo table allocation", DG_ENOMEM);
   k_halo<<<(unsigned)nch, kBlock, 0, s>>>(geo.d_nb, geo.d_chunk, geo.d_loc, geo.d_halo, geo.d_halo_cnt);
   k_max_int<<<1, 256, 0, s>>>(geo.d_halo_cnt, (int)nch, geo.d_halo_cnt + nch);
+  GK(cudaGetLastError(), "halo table", DG_ECUDA);
   GK(cudaMemcpyAsync(&hmax, geo.d_halo_cnt + nch, sizeof(int), cudaMemcpyDeviceToHost, s), "halo table", DG_ECUDA);
   geo.h_mask.resize((size_t)dense);
   GK(cudaMemcpyAsync(geo.h_mask.data(), geo.d_mask, (size_t)dense, cudaMemcpyDeviceToHost, s), "mask copy", DG_ECUDA);
