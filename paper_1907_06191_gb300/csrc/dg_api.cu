@@ -34,7 +34,11 @@ cudaError_t dev_alloc(void **p, size_t bytes) {
     *p = nullptr;
     return cudaErrorMemoryAllocation;
   }
-  return cudaMalloc(p, bytes);
+  const cudaError_t e = cudaMalloc(p, bytes);
+  // the failure is returned here; clear it from the thread's last-error state
+  // so that a later launch check does not report it as a launch failure
+  if (e != cudaSuccess) (void)cudaGetLastError();
+  return e;
 }
 
 }  // namespace dg
