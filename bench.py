@@ -167,7 +167,7 @@ def run_reference(args, world, rank):
         u = O.rk3(mesh, u, 1, dt)
     el = time.perf_counter() - t0
     v = dof * args.steps / el
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = O.threads()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "DoF-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
@@ -200,7 +200,7 @@ def cpu_baseline_sample(w, seconds_target=20.0):
     t0 = time.perf_counter()
     u = O.rk3(mesh, u, n, 1e-4)
     el = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = O.threads()
     return {"value": dof * n / el, "unit": "DoF-steps/s", "cores": cores, "kind": "oracle",
             "sample": f"1 of 64 densities x {n} SSP-RK3 steps on the full {act.shape[0]}^2 window"}
 

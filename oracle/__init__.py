@@ -74,6 +74,8 @@ def _load():
         lib.orc_mask_disks.restype = None
         lib.orc_power_rho.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64]
         lib.orc_power_rho.restype = ctypes.c_double
+        lib.orc_threads.argtypes = []
+        lib.orc_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -132,6 +134,11 @@ class Mesh:
 def _dp(a: np.ndarray):
     assert a.dtype == np.float64 and a.flags.c_contiguous
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def threads() -> int:
+    """Threads of the OpenMP team the oracle's element loops run on."""
+    return int(_load().orc_threads())
 
 
 def gll(p: int):

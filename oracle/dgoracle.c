@@ -41,6 +41,7 @@
  * that are not in the mesh hold zeros.
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -517,4 +518,16 @@ double orc_power_rho(const orc_mesh *M, int iters, uint64_t seed) {
   }
   free(v);
   return rho;
+}
+
+/* Threads of the OpenMP team the element loops above run on (for reporting
+ * how many host cores a timing used). */
+int orc_threads(void) {
+  int n = 1;
+#pragma omp parallel
+  {
+#pragma omp single
+    n = omp_get_num_threads();
+  }
+  return n;
 }
