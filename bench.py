@@ -202,7 +202,8 @@ def cpu_baseline_sample(w, seconds_target=20.0):
     el = time.perf_counter() - t0
     cores = O.threads()
     return {"value": dof * n / el, "unit": "DoF-steps/s", "cores": cores, "kind": "oracle",
-            "sample": f"1 of 64 densities x {n} SSP-RK3 steps on the full {act.shape[0]}^2 window"}
+            "sample": f"1 of {len(w.sources)} densities x {n} SSP-RK3 steps on the full "
+                      f"{act.shape[0]}^2 window"}
 
 
 def run_batch(args):
