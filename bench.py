@@ -26,6 +26,7 @@ import hashlib
 import json
 import math
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -183,6 +184,20 @@ def run_reference(args, world, rank):
     return 0
 
 
+def _host_cpu() -> str:
+    """Host CPU model (where /proc/cpuinfo names it) and logical CPU count."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu model")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return f"{model or platform.machine()}, {os.cpu_count()} logical CPUs"
+
+
 def cpu_baseline_sample(w, seconds_target=20.0):
     """Oracle DoF-steps/s on a bounded sample: one density of the workload,
     RK steps on the full window until ~seconds_target of CPU work."""
@@ -202,6 +217,7 @@ def cpu_baseline_sample(w, seconds_target=20.0):
     el = time.perf_counter() - t0
     cores = O.threads()
     return {"value": dof * n / el, "unit": "DoF-steps/s", "cores": cores, "kind": "oracle",
+            "cpu": _host_cpu(),
             "sample": f"1 of {len(w.sources)} densities x {n} SSP-RK3 steps on the full "
                       f"{act.shape[0]}^2 window"}
 
