@@ -176,7 +176,7 @@ def run_reference(args, world, rank):
             "config": {"workload": w.name, "window_elements": int(act.size),
                        "active_elements": int(act.sum()), "p": w.p},
             "cpu_baseline": {"value": v, "unit": "DoF-steps/s", "cores": cores,
-                             "kind": "oracle",
+                             "kind": "oracle", "cpu": _host_cpu(),
                              "sample": "1 density x 1 SSP-RK3 step per bench step on the full window"},
             "e2e": {"value": v, "unit": "DoF-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
