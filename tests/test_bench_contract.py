@@ -37,6 +37,7 @@ def test_reference_arm_prints_one_complete_line():
     assert abs(line["value"] * line["ms_per_step"] * 1e-3 / dof - 1) < 1e-9
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1
+    assert cb["cores"] <= (os.cpu_count() or 1) and "logical CPUs" in cb["cpu"]
     assert line["e2e"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
 
