@@ -198,28 +198,87 @@ def _host_cpu() -> str:
     return f"{model or platform.machine()}, {os.cpu_count()} logical CPUs"
 
 
-def cpu_baseline_sample(w, seconds_target=20.0):
+def cpu_baseline_sample(w, seconds_target=20.0, threads=None):
     """Oracle DoF-steps/s on a bounded sample: one density of the workload,
-    RK steps on the full window until ~seconds_target of CPU work."""
+    RK steps on the full window until ~seconds_target of CPU work, on all
+    host cores (threads=None) or on the given number of threads."""
     import oracle as O
     O.build()
-    cell = O.mask_disks(w.L, w.n_cell, w.disks.cx, w.disks.cy, w.disks.r)
-    act = O.window_mask(cell, w.tiles)
-    mesh = O.Mesh(p=w.p, active=act, h=w.h, x0=w.origin, y0=w.origin, k0=w.D)
-    dof = int(act.sum()) * (w.p + 1) ** 2
-    u = O.init_gaussian(mesh, *w.sources[0], w.sigma0)
-    t0 = time.perf_counter()
-    u = O.rk3(mesh, u, 1, 1e-4)
-    one = time.perf_counter() - t0
-    n = max(1, min(20, int(seconds_target / max(one, 1e-3)) - 1))
-    t0 = time.perf_counter()
-    u = O.rk3(mesh, u, n, 1e-4)
-    el = time.perf_counter() - t0
-    cores = O.threads()
+    before = O.threads()
+    if threads:
+        O.set_threads(threads)
+    try:
+        cell = O.mask_disks(w.L, w.n_cell, w.disks.cx, w.disks.cy, w.disks.r)
+        act = O.window_mask(cell, w.tiles)
+        mesh = O.Mesh(p=w.p, active=act, h=w.h, x0=w.origin, y0=w.origin, k0=w.D)
+        dof = int(act.sum()) * (w.p + 1) ** 2
+        u = O.init_gaussian(mesh, *w.sources[0], w.sigma0)
+        t0 = time.perf_counter()
+        u = O.rk3(mesh, u, 1, 1e-4)
+        one = time.perf_counter() - t0
+        n = max(1, min(20, int(seconds_target / max(one, 1e-3)) - 1))
+        t0 = time.perf_counter()
+        u = O.rk3(mesh, u, n, 1e-4)
+        el = time.perf_counter() - t0
+        cores = O.threads()
+    finally:
+        O.set_threads(before)
     return {"value": dof * n / el, "unit": "DoF-steps/s", "cores": cores, "kind": "oracle",
             "cpu": _host_cpu(),
             "sample": f"1 of {len(w.sources)} densities x {n} SSP-RK3 steps on the full "
                       f"{act.shape[0]}^2 window"}
+
+
+def fp64_roofline(p, tri, dof, stage_ms):
+    """FP64 stage kernel against the FP64 pipe (2 FMA/clk/SM on GB300):
+    152 x 2 x 2 flop x 2.07 GHz = 1.26 TFLOP/s, by algorithmic flops."""
+    peak = 152 * 2 * 2 * 2.07e9 / 1e12
+    fl = flops_per_dof_step_tri(p) if tri else flops_per_dof_step(p)
+    ach = fl * dof / 3.0 / (stage_ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "peak_source": "derived from unit counts and max clock"}
+
+
+def sigma_solve(dg, w, s, dev, args, rnd, r_factor=10.0):
+    """Sigma solves/s measured on the bench context: every density carried
+    from its start to Delta = args.solve_delta on the growing window
+    (radius factor 10, the library's setting for p = 3), Sigma formed, host
+    wall clock around propagate_to + covariance.  Then the plain FP64 path
+    solves the first few densities the same way (its rate per density), and
+    the FP32 Sigma of those densities (dg_mixture_covariance of their FP32
+    moments) is compared with the FP64 one."""
+    import torch
+    delta, nd = args.solve_delta, max(1, min(args.solve_fp64_densities, len(w.sources)))
+    s.set_growing_window(r_factor)
+    s.set_sources(w.sources)
+    mom0 = s.moments()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    s.propagate_to(delta)
+    sig32, mu32, mass32 = s.covariance()
+    t32 = time.perf_counter() - t0
+    steps = s.info().steps
+    mom = s.moments()
+    sub32, _ = s.mixture_covariance(mom[:nd], mom0[:nd])
+    s.set_growing_window(0.0)
+    with dg.DGSolver(p=w.p, precision=dg.DG_FP64, D=w.D, sigma0=w.sigma0, device=dev) as d64:
+        d64.set_geometry_disks(w.disks.cx, w.disks.cy, w.disks.r, w.L, w.n_cell, w.tiles)
+        d64.set_growing_window(r_factor)
+        d64.set_sources(w.sources[:nd])
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        d64.propagate_to(delta)
+        sig64, _, _ = d64.covariance()
+        t64 = time.perf_counter() - t0
+    m = len(w.sources)
+    return {"delta_ms": delta, "densities": m, "rk_steps": steps, "seconds": t32,
+            "sigma_solves_per_s": m / t32, "sigma": sig32.tolist(), "mu": mu32.tolist(),
+            "free_value": 2 * w.D * delta, "growing_window_r": r_factor,
+            "fp64_densities": nd, "fp64_seconds": t64, "fp64_sigma_solves_per_s": nd / t64,
+            "sigma_fp64_subset": sig64.tolist(), "sigma_fp32_subset": sub32.tolist(),
+            "sigma_rel_err_vs_fp64": float(np.abs(sub32 - sig64).max() / np.abs(sig64).max()),
+            "what": "measured: start densities to Delta, growing window, Sigma; FP32 default "
+                    "path vs the plain FP64 GPU path on the same densities"}
 
 
 def run_batch(args):
@@ -433,6 +492,13 @@ def main():
     ap.add_argument("--densities", type=int, default=64,
                     help="start points per GPU (64 = the workload; fewer for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="bench steps of the plain FP64 GPU path timed beside the FP32 path")
+    ap.add_argument("--solve-delta", type=float, default=5.0,
+                    help="measure Sigma solves/s: every density to this Delta (ms) on the "
+                         "growing window (0: skip)")
+    ap.add_argument("--solve-fp64-densities", type=int, default=2,
+                    help="densities solved in FP64 for the comparator rate and the error")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--check-delta", type=float, default=0.0,
                     help="compare FP32 with the FP64 GPU path over a solve to this Delta (ms) "
@@ -538,7 +604,9 @@ def main():
     e1.record(stream)
     e1.synchronize()
     stage_ms = e0.elapsed_time(e1) / (3 * R)
-    bytes_per_launch = (BYTES_PER_DOF_STEP_TRI if tri else BYTES_PER_DOF_STEP)[args.precision] * dof / 3.0
+    # algorithmic bytes: the method's 8 state accesses per DoF-step (the
+    # triangles' two-pass design moves more, reported beside as design traffic)
+    bytes_per_launch = BYTES_PER_DOF_STEP[args.precision] * dof / 3.0
     peaks, src = _peaks()
     achieved = bytes_per_launch / (stage_ms * 1e-3) / 1e9
     rec = _traffic_record(os.path.join(ROOT, "paper_1907_06191_gb300", "csrc", "dg_stage.cuh"))
@@ -546,17 +614,19 @@ def main():
     if rec and rec.get("precision") == args.precision and rec.get("p") == w.p and not tri:
         traffic = rec["dram_bytes_per_launch_per_dof"] * dof
     if args.precision == "f64":
-        # FP64 is bound by the FP64 pipe (2 FMA/clk/SM): 152 x 2 x 2 x 2.07 GHz
-        peak_f64 = 152 * 2 * 2 * 2.07e9 / 1e12
-        fl = flops_per_dof_step_tri(w.p) if tri else flops_per_dof_step(w.p)
-        roofline = {"bound": "alu", "achieved": fl * dof / 3.0
-                    / (stage_ms * 1e-3) / 1e12, "peak": peak_f64, "unit": "TFLOP/s",
-                    "traffic": traffic, "peak_source": "derived from unit counts and max clock"}
-        roofline["frac"] = roofline["achieved"] / peak_f64
+        roofline = fp64_roofline(w.p, tri, dof, stage_ms)
+        roofline["traffic"] = traffic
     else:
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                     "peak_source": f"{src} hbm_gbs"}
+        if tri:
+            design = BYTES_PER_DOF_STEP_TRI[args.precision] * dof / 3.0 / (stage_ms * 1e-3) / 1e9
+            roofline["design_bytes_per_dof_step"] = BYTES_PER_DOF_STEP_TRI[args.precision]
+            roofline["design_achieved"] = design
+            roofline["design_frac"] = design / peaks["hbm_gbs"]
+            roofline["note"] = ("achieved counts the method's 32 B per DoF-step; the two-pass "
+                                "triangle design moves 92 B (q written and read back)")
 
     # e2e through the C ABI with host buffers
     xy_host = torch.from_numpy(np.ascontiguousarray(w.sources)).pin_memory()
@@ -580,6 +650,7 @@ def main():
 
     # agreement with the FP64 GPU path on the same steps
     check = None
+    fp64 = None
     if args.check_delta and args.precision == "f32" and rank == 0:
         # a longer solve: the first 4 densities to Delta in both precisions
         nd = 4
@@ -602,6 +673,8 @@ def main():
                  "mass_rel_err": float(np.abs(m32 - m64).max() / np.abs(m64).max()),
                  "seconds_fp32": t32, "seconds_fp64": t64}
     elif not args.no_check and args.precision == "f32" and rank == 0:
+        # the plain FP64 GPU path on the same workload: timed (the metric's
+        # comparator), then the same R steps from the same start compared
         s.set_sources(w.sources)
         s.step(R, dt)
         sig32 = s.covariance()[0]
@@ -609,6 +682,23 @@ def main():
         with dg.DGSolver(p=w.p, precision=dg.DG_FP64, D=w.D, sigma0=w.sigma0, device=dev,
                          element=s.cfg.element) as d64:
             d64.set_geometry_disks(w.disks.cx, w.disks.cy, w.disks.r, w.L, w.n_cell, w.tiles)
+            d64.set_stream(stream.cuda_stream)
+            d64.set_sources(w.sources)
+            d64.step(R, dt)
+            d64.covariance()
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for _ in range(args.fp64_steps):
+                d64.step(R, dt)
+                d64.covariance()
+            e1.record(stream)
+            e1.synchronize()
+            ms64 = e0.elapsed_time(e1)
+            e0.record(stream)
+            d64.step(1, dt)
+            e1.record(stream)
+            e1.synchronize()
+            stage64 = e0.elapsed_time(e1) / 3.0
             d64.set_sources(w.sources)
             d64.step(R, dt)
             sig64 = d64.covariance()[0]
@@ -617,6 +707,17 @@ def main():
         m2_64 = mom64[:, 3:] / mom64[:, :1]
         check = {"steps": R, "sigma_rel_err": float(np.abs(sig32 - sig64).max() / np.abs(sig64).max()),
                  "second_moment_rel_err": float(np.abs(m2_32 - m2_64).max() / np.abs(m2_64).max())}
+        fp64 = {"value": dof * R * args.fp64_steps / (ms64 * 1e-3), "unit": "DoF-steps/s",
+                "steps": args.fp64_steps, "ms_per_step": ms64 / args.fp64_steps,
+                "roofline": fp64_roofline(w.p, tri, dof, stage64),
+                "what": "the plain FP64 GPU path, same workload and bench step, timed in this run"}
+
+    # measured Sigma solves: every density carried to the workload's first
+    # diffusion time on the growing window, the FP32 path timed end to end;
+    # a few densities in FP64 give the comparator's rate and the error
+    solve = None
+    if args.solve_delta > 0 and rank == 0 and not tri:
+        solve = sigma_solve(dg, w, s, dev, args, rnd)
 
     full = None
     if args.full_delta > 0 and rank == 0:
@@ -649,10 +750,22 @@ def main():
                 for a, b in zip(g["snapshots"], full["snapshots"])]
             g["speedup_vs_fixed"] = full["seconds"] / g["seconds"]
             full["growing_window"] = g
+    # multi-GPU: the densities of every rank form one mixture; the one
+    # exchange is the moment gather, then Sigma on each rank's device
+    sharded = None
+    if world > 1:
+        from dginputs import sample_sources, source_box
+        from paper_1907_06191_gb300.multi import sharded_covariance
+        lo, hi = source_box(w.L, w.tiles, w.sigma0, w.D, max(w.deltas))
+        every = np.concatenate([sample_sources(args.seed + 7919 + 1000 * r, w.disks, args.densities,
+                                               lo, hi, margin=w.h) for r in range(world)])
+        s3, mu2, gm, _ = sharded_covariance(s, every, lambda c: c.step(R, dt), device=f"cuda:{dev}")
+        sharded = {"ranks": world, "densities": int(gm.shape[0]), "rk_steps": R,
+                   "sigma": s3.tolist(), "mu": mu2.tolist(),
+                   "what": "start points of all ranks, one moment all-gather, dg_mixture_covariance"}
     s.close()
     if rank != 0:
         return 0
-    nsteps_50 = math.ceil(50.0 / dt)
     line = {
         "metric": METRIC, "value": value, "unit": "DoF-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -667,8 +780,10 @@ def main():
                    "dt_ms": dt, "rho_per_ms": rho, "packing": w.disks.packing,
                    "halo_max_per_block": inf.halo_max,
                    "disks": w.disks.n, "l2": "state (>=16 GB) larger than L2, no flush"},
-        "sigma_solves_per_s": value / (inf.dof_per_source * nsteps_50),
-        "sigma_solve_note": f"derived: one density to Delta = 50 ms takes {nsteps_50} RK steps",
+        "sigma_solves_per_s": solve["sigma_solves_per_s"] if solve else None,
+        "sigma_solve": solve,
+        "fp64_value": fp64["value"] if fp64 else None,
+        "fp64_path": fp64,
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": args.steps * (3 * R + 3),
@@ -677,8 +792,11 @@ def main():
     }
     if full is not None:
         line["full_solve"] = full
+    if sharded is not None:
+        line["sharded_sigma"] = sharded
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline_sample(w)
+        line["cpu_baseline_1thread"] = cpu_baseline_sample(w, seconds_target=10.0, threads=1)
     print(json.dumps(line), flush=True)
     return 0
 

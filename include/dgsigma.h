@@ -377,13 +377,18 @@ int dg_bind_state(dg_ctx *ctx, void *device_ptr, size_t bytes);
  * 1.09 MB inside the library (room for m <= 128), which every GPU that loads
  * the library holds until the process exits.  The first call on a device
  * looks up that array's address with the device current; make that first
- * call before any stream capture.  All calls share the array: calls whose
- * work overlaps on the GPU (different streams, or threads) race and give
- * wrong moments; serialise them.  The array needs no clearing (each call
- * overwrites every partial it reads).
+ * call before any stream capture.  The address is kept for the life of the
+ * process: after cudaDeviceReset (or any other end of the device's primary
+ * context) it is stale, and this entry point must not be called again in
+ * that process.  All calls share the array: calls whose work overlaps on the
+ * GPU (different streams, or threads) race and give wrong moments; serialise
+ * them.  The array needs no clearing (each call overwrites every partial it
+ * reads).
  * Errors: DG_EINVAL (NULL pointer, m < 1 or m > 128, p outside 1..5, nx or
- * ny < 1, h <= 0, bad precision), DG_ECUDA (launch failure).  No
- * cudaMalloc, cudaFree or other allocating call is made. */
+ * ny < 1, h <= 0, h, x0 or y0 not finite, bad precision), DG_ECUDA (a CUDA
+ * error already pending on the calling thread from earlier work -- reported,
+ * not consumed, and nothing is launched -- or a launch failure of this
+ * call).  No cudaMalloc, cudaFree or other allocating call is made. */
 int dg_moments_dense_static(const void *u, int precision, int m, int nx, int ny, int p,
                             double h, double x0, double y0, const double *xy, double *mom,
                             void *stream);

@@ -76,6 +76,8 @@ def _load():
         lib.orc_power_rho.restype = ctypes.c_double
         lib.orc_threads.argtypes = []
         lib.orc_threads.restype = ctypes.c_int
+        lib.orc_set_threads.argtypes = [ctypes.c_int]
+        lib.orc_set_threads.restype = None
         _lib = lib
     return _lib
 
@@ -139,6 +141,11 @@ def _dp(a: np.ndarray):
 def threads() -> int:
     """Threads of the OpenMP team the oracle's element loops run on."""
     return int(_load().orc_threads())
+
+
+def set_threads(n: int) -> None:
+    """Run the oracle's element loops on n threads from now on."""
+    _load().orc_set_threads(int(n))
 
 
 def gll(p: int):

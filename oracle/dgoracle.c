@@ -531,3 +531,9 @@ int orc_threads(void) {
   }
   return n;
 }
+
+/* Size of the OpenMP team of the next element loops (n >= 1); used to time
+ * the oracle on one host core as well as on all of them. */
+void orc_set_threads(int n) {
+  if (n >= 1) omp_set_num_threads(n);
+}

@@ -824,6 +824,9 @@ static __device__ __align__(256) double
 
 // Moments of densities in the dense node layout [m][ny][nx][n][n]; elements
 // outside the mesh hold zeros and add nothing.  grid (kStaticMomBlocks, m).
+// Per element the weighted node sums are formed in the state precision
+// (local_moments, as k_moments does) and combined with the FP64 element
+// centre in FP64, so an FP32 density costs no FP64 arithmetic per node.
 template <typename T, int P>
 __global__ void __launch_bounds__(256)
     k_moments_dense(const T *__restrict__ u, int nx, int ny, const double *__restrict__ xy,
@@ -832,29 +835,27 @@ __global__ void __launch_bounds__(256)
   const int s = blockIdx.y;
   const double xs = xy[2 * s], ys = xy[2 * s + 1];
   const double J = 0.5 * g.h;
+  T w[n], wx[n], wxx[n];
+#pragma unroll
+  for (int i = 0; i < n; ++i) {
+    w[i] = (T)g.w[i];
+    wx[i] = (T)(g.w[i] * g.xi[i]);
+    wxx[i] = (T)(g.w[i] * g.xi[i] * g.xi[i]);
+  }
   const long long ne = (long long)nx * ny;
   double acc[kMomFields] = {0, 0, 0, 0, 0, 0, 0};
   const T *U = u + (size_t)s * ne * NP;
   for (long long e = (long long)blockIdx.x * 256 + threadIdx.x; e < ne;
        e += (long long)gridDim.x * 256) {
     const int ex = (int)(e % nx), ey = (int)(e / nx);
-    const T *ue = U + (size_t)e * NP;
+    T lmT[7];
+    local_moments<T, P>(U + (size_t)e * NP, w, wx, wxx, lmT);
+    double lm[7];
 #pragma unroll
-    for (int j = 0; j < n; ++j) {
-      const double y = g.y0 + (ey + 0.5) * g.h + J * g.xi[j] - ys;
-#pragma unroll
-      for (int i = 0; i < n; ++i) {
-        const double x = g.x0 + (ex + 0.5) * g.h + J * g.xi[i] - xs;
-        const double wu = J * J * g.w[i] * g.w[j] * (double)ue[j * n + i];
-        acc[0] += wu;
-        acc[1] += wu * x;
-        acc[2] += wu * y;
-        acc[3] += wu * x * x;
-        acc[4] += wu * x * y;
-        acc[5] += wu * y * y;
-        acc[6] += fabs(wu);
-      }
-    }
+    for (int q = 0; q < 7; ++q) lm[q] = (double)lmT[q];
+    const double X = g.x0 + (ex + 0.5) * g.h - xs;
+    const double Y = g.y0 + (ey + 0.5) * g.h - ys;
+    add_element_moments(X, Y, J, lm, acc);
   }
   block_sum7(acc);
   if (threadIdx.x == 0) {
@@ -915,6 +916,7 @@ extern "C" int dg_moments_dense_static(const void *u, int precision, int m, int 
   if (!u || !xy || !mom) return DG_EINVAL;
   if (m < 1 || m > kStaticMomMaxDensities) return DG_EINVAL;
   if (p < 1 || p > kMaxP || nx < 1 || ny < 1 || !(h > 0.0)) return DG_EINVAL;
+  if (!std::isfinite(h) || !std::isfinite(x0) || !std::isfinite(y0)) return DG_EINVAL;
   if (precision != DG_FP64 && precision != DG_FP32) return DG_EINVAL;
   Gll gl;
   if (!gll_tables(p, &gl)) return DG_EINVAL;
@@ -926,6 +928,9 @@ extern "C" int dg_moments_dense_static(const void *u, int precision, int m, int 
   g.h = h;
   g.x0 = x0;
   g.y0 = y0;
+  // an error that earlier work left pending on this thread is not this
+  // call's: report it without consuming it, so that its owner still sees it
+  if (cudaPeekAtLastError() != cudaSuccess) return DG_ECUDA;
   double *part = nullptr;
   if (static_scratch(&part) != cudaSuccess) return DG_ECUDA;
   cudaStream_t s = (cudaStream_t)stream;
@@ -939,7 +944,7 @@ extern "C" int dg_moments_dense_static(const void *u, int precision, int m, int 
                          (const float *)u, nx, ny, xy, g, part)));
     }
     k_moments_dense_final<<<m, 256, 0, s>>>(part, kStaticMomBlocks, mom);
-    return cudaGetLastError();
+    return cudaGetLastError();  // nothing was pending before: only these launches
   };
   return launch() == cudaSuccess ? DG_OK : DG_ECUDA;
 }

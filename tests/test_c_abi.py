@@ -43,7 +43,7 @@ int main(void) {
 """
 
 
-def test_c_program_compiles_links_and_runs(tmp_path):
+def _compile_and_run(tmp_path):
     gcc = shutil.which("gcc")
     if gcc is None:
         pytest.skip("no C compiler")
@@ -60,11 +60,30 @@ def test_c_program_compiles_links_and_runs(tmp_path):
     assert r.returncode == 0, r.stderr
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
-    out = r.stdout.strip()
+    return r.stdout.strip()
+
+
+def _check_sigma(out):
+    assert out.startswith("sigma "), out
+    sxx, sxy, syy = (float(v) for v in out.split()[1:])
+    # free diffusion would give 2 D t = 2 um^2; walls only lower it
+    assert 0 < sxx < 2.0 + 1e-6 and 0 < syy < 2.0 + 1e-6 and sxx * syy > sxy ** 2
+
+
+def test_c_program_compiles_links_and_runs(tmp_path):
+    out = _compile_and_run(tmp_path)
     if out.startswith("dg_create"):
         # no usable device here: an error status, no handle, no crash
         assert out == "dg_create: 3 CUDA error handle=null", out
     else:
-        sxx, sxy, syy = (float(v) for v in out.split()[1:])
-        # free diffusion would give 2 D t = 2 um^2; walls only lower it
-        assert 0 < sxx < 2.0 + 1e-6 and 0 < syy < 2.0 + 1e-6 and sxx * syy > sxy ** 2
+        _check_sigma(out)
+
+
+@pytest.mark.gpu
+def test_c_program_sigma_solve_on_the_gpu(tmp_path):
+    """The plain-C usage sequence (create, disks, start point, propagate_to,
+    covariance, destroy) on a device: it must take the solve branch."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    _check_sigma(_compile_and_run(tmp_path))

@@ -119,3 +119,82 @@ def test_dead_rank_is_reported_not_hung():
     assert codes[1] == 3
     status, payload = res[0]
     assert status == "error"
+
+
+class _OracleSolver:
+    """Stand-in for one rank's DGSolver on the CPU: the same four calls
+    sharded_covariance makes, answered by the oracle."""
+
+    def __init__(self, mesh, nsteps=6, dt=0.004):
+        self.mesh, self.nsteps, self.dt = mesh, nsteps, dt
+        self.src, self.u = None, None
+
+    def set_sources(self, xy):
+        import oracle as O
+        self.src = np.asarray(xy).reshape(-1, 2)
+        self.u = [O.init_gaussian(self.mesh, x, y, 0.3) for x, y in self.src]
+
+    def moments(self):
+        import oracle as O
+        return np.array([O.moments(self.mesh, u, x, y) for u, (x, y) in zip(self.u, self.src)])
+
+    def advance(self):
+        import oracle as O
+        self.u = [O.rk3(self.mesh, u, self.nsteps, self.dt) for u in self.u]
+
+    def mixture_covariance(self, mom, mom0):
+        import oracle as O
+        s3, mu, _ = O.aggregate(mom, mom0)
+        return s3, mu
+
+
+def _sigma_worker(rank, world, port, q, m):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    import torch.distributed as dist
+    from paper_1907_06191_gb300.multi import sharded_covariance
+    try:
+        dist.init_process_group("gloo", rank=rank, world_size=world,
+                                timeout=datetime.timedelta(seconds=20))
+        mesh, src = _problem()
+        s3, mu, mom, mom0 = sharded_covariance(_OracleSolver(mesh), src[:m],
+                                               lambda s: s.advance())
+        q.put((rank, "ok", (s3, mu, mom, mom0)))
+        dist.destroy_process_group()
+    except Exception as e:  # noqa: BLE001
+        q.put((rank, "error", repr(e)))
+
+
+@pytest.mark.parametrize("world,m", [(2, 7), (3, 7), (3, 2)])
+def test_sharded_covariance_equals_unsharded(world, m):
+    """The host side of the sharded Sigma: start points split over gloo
+    ranks, raw moments at 0 and at t gathered in one collective, Sigma of the
+    whole mixture on every rank.  It must equal the unsharded aggregation bit
+    for bit, also when a rank owns no start point (m = 2 < 3 ranks)."""
+    import oracle as O
+    O.build()
+    mesh, src = _problem()
+    ref = _OracleSolver(mesh)
+    ref.set_sources(src[:m])
+    mom0 = ref.moments()
+    ref.advance()
+    mom = ref.moments()
+    s_ref, mu_ref, _ = O.aggregate(mom, mom0)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_sigma_worker, args=(r, world, port, q, m)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = {}
+    for _ in range(world):
+        r, status, payload = q.get(timeout=120)
+        res[r] = (status, payload)
+    for p in procs:
+        p.join(timeout=30)
+    for r in range(world):
+        status, payload = res[r]
+        assert status == "ok", payload
+        s3, mu, gm, gm0 = payload
+        assert np.array_equal(gm, mom) and np.array_equal(gm0, mom0)
+        assert np.array_equal(s3, s_ref) and np.array_equal(mu, mu_ref)

@@ -402,6 +402,52 @@ def test_aggregation_is_mixture_covariance():
 
 
 # --------------------------------------------------------------------------
+# Start density (Sec. 4.1: regularised Dirac data) and its nodal moments
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("ratio", [2.0, 4.0])
+def test_start_density_is_a_unit_mass_gaussian(p, ratio):
+    """A Gaussian of width sigma0 >= 2h, interpolated at the GLL nodes and
+    integrated by the nodal quadrature far from any wall or edge, has the
+    moments of the normalised bivariate normal: mass 1, mean at the start
+    point, covariance sigma0^2 I.  A wrong amplitude (e.g. 1/(2 pi sigma0)),
+    a wrong exponent, a shifted node or a wrong quadrature weight fails."""
+    h = 0.1
+    s0 = ratio * h
+    m = O.Mesh(p=p, active=np.ones((80, 80), np.uint8), h=h, x0=-1.0, y0=0.5)
+    xs, ys = 3.03, 4.47   # off the element corners, 2.3 and 3.7 from the edges
+    mom = O.moments(m, O.init_gaussian(m, xs, ys, s0), xs, ys)
+    assert abs(mom[0] - 1.0) < 1e-12
+    assert abs(mom[1]) < 1e-12 and abs(mom[2]) < 1e-12 and abs(mom[4]) < 1e-12
+    assert abs(mom[3] - s0 * s0) < 1e-12 and abs(mom[5] - s0 * s0) < 1e-12
+
+
+@pytest.mark.parametrize("p,tol", [(3, 2e-8), (5, 1e-12)])
+@pytest.mark.parametrize("d", [0.0, 0.17, 0.35])
+def test_start_density_cut_by_a_straight_wall(p, tol, d):
+    """Rows of removed elements below y = y_w cut the Gaussian; the
+    extracellular part has the closed-form moments of a truncated normal:
+    M0 = erfc(-d/(sqrt2 s0))/2, My = s0 phi(d/s0), Myy = s0^2 M0 - s0 d
+    phi(d/s0), Mxx = s0^2 M0 (d = ys - y_w).  The nodal quadrature of the
+    smooth Gaussian on whole elements converges spectrally in p."""
+    h, s0 = 0.1, 0.25
+    act = np.ones((60, 60), np.uint8)
+    act[:20, :] = 0
+    m = O.Mesh(p=p, active=act, h=h)
+    yw = 20 * h
+    xs, ys = 3.02, yw + d
+    mom = O.moments(m, O.init_gaussian(m, xs, ys, s0), xs, ys)
+    phi = math.exp(-d * d / (2 * s0 * s0)) / math.sqrt(2 * math.pi)
+    M0 = 0.5 * math.erfc(-d / (math.sqrt(2) * s0))
+    assert abs(mom[0] - M0) < tol
+    assert abs(mom[1]) < tol and abs(mom[4]) < tol
+    assert abs(mom[2] - s0 * phi) < tol
+    assert abs(mom[3] - s0 * s0 * M0) < tol
+    assert abs(mom[5] - (s0 * s0 * M0 - s0 * d * phi)) < tol
+
+
+# --------------------------------------------------------------------------
 # Convergence to analytic heat solutions
 # --------------------------------------------------------------------------
 
