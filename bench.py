@@ -491,6 +491,12 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--densities", type=int, default=64,
                     help="start points per GPU (64 = the workload; fewer for profiling)")
+    ap.add_argument("--launch", type=int, default=-1,
+                    help="stage-kernel launch shape: -1 tuned (library default), 0 one block "
+                         "per chunk, k persistent blocks per SM")
+    ap.add_argument("--contraction", type=int, default=-1,
+                    help="FP32 p = 5 element contractions: -1 tuned (library default), "
+                         "0 CUDA cores, 1 tensor cores")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="bench steps of the plain FP64 GPU path timed beside the FP32 path")
@@ -558,6 +564,8 @@ def main():
     s = dg.DGSolver(p=w.p, precision=prec, D=w.D, sigma0=w.sigma0, device=dev, rounding=rnd,
                     element=dg.DG_ELEMENT_TRIANGLE if tri else dg.DG_ELEMENT_SQUARE)
     s.set_geometry_disks(w.disks.cx, w.disks.cy, w.disks.r, w.L, w.n_cell, w.tiles)
+    s.set_launch(args.launch)
+    s.set_contraction(args.contraction)
     stream = torch.cuda.Stream(device=dev)
     s.set_stream(stream.cuda_stream)
     s.set_sources(w.sources)
@@ -574,6 +582,8 @@ def main():
     for _ in range(args.warmup):
         bench_step()
     torch.cuda.synchronize(dev)
+    launch_used = s.get_launch()
+    contraction_used = s.get_contraction()
 
     # device-timed region: state resident (16 GB > L2, no flush needed)
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -779,6 +789,9 @@ def main():
                    "dof_per_density": inf.dof_per_source, "rk_steps_per_bench_step": R,
                    "dt_ms": dt, "rho_per_ms": rho, "packing": w.disks.packing,
                    "halo_max_per_block": inf.halo_max,
+                   "launch_blocks_per_sm": launch_used,
+                   "contraction": "tensor cores (FP16 hi/lo split, FP32 accumulation)"
+                   if contraction_used else "CUDA cores",
                    "disks": w.disks.n, "l2": "state (>=16 GB) larger than L2, no flush"},
         "sigma_solves_per_s": solve["sigma_solves_per_s"] if solve else None,
         "sigma_solve": solve,

@@ -275,6 +275,43 @@ int dg_set_growing_window(dg_ctx *ctx, double r_factor);
  * the last call.  Errors: DG_EINVAL (mode outside 0..2). */
 int dg_debug_copies(dg_ctx *ctx, int mode, unsigned long long *tensor_copies);
 
+/* Launch shape of the FP32 stage kernel (no counterpart in the paper: how the
+ * element updates of Sec. 3.3, one independent update per element, are
+ * mapped onto the GPU).  blocks_per_sm = 0: one block of 256 threads per
+ * chunk of 256 elements and density (all chunks in one launch per RK
+ * stage); k >= 1: a persistent launch of k blocks per SM that walk the
+ * (density, chunk) work items of every geometry of the context and copy the
+ * next item's chunks into shared memory behind the current item's work
+ * (clamped to the blocks that fit; FP32 at p = 1 and 3 with tensor copies,
+ * every other variant keeps the one-block-per-chunk launch); -1 (the
+ * default): tuned -- before the first steps after a change of the densities
+ * or geometry, each shape runs stage 1 with dt = 0 (which leaves the
+ * state's values unchanged) four times on the context's stream and the
+ * fastest is kept (under stream capture, where nothing can be timed, the
+ * one-block-per-chunk launch).  Every shape gives the same bits.  Errors: DG_EINVAL
+ * (blocks_per_sm < -1 or > 64). */
+int dg_set_launch(dg_ctx *ctx, int blocks_per_sm);
+
+/* The launch shape the last steps used (0 or blocks per SM, see
+ * dg_set_launch). */
+int dg_get_launch(dg_ctx *ctx, int *blocks_per_sm);
+
+/* Where the element contractions of the FP32 stage at p = 5 run.  Sec. 3.1
+ * (Remark) notes that each element's update is a small dense local system;
+ * the element's volume term and the normal derivatives at its faces are one
+ * dense [60 x 36] operator applied to its 36 nodal values, for 256 elements
+ * at a time a GEMM.  mode 0: sum-factorised on the CUDA cores (FP32); 1: on
+ * the tensor cores (tcgen05.mma, FP16 operands, FP32 accumulation) with
+ * both operands split into FP16 high and low parts after a per-element
+ * power-of-two scaling (three products, ~2^-21 of each element's largest
+ * term); -1 (default): tuned together with the launch shape (see
+ * dg_set_launch).  Other orders and FP64 always use the CUDA cores.
+ * Errors: DG_EINVAL (mode outside -1..1). */
+int dg_set_contraction(dg_ctx *ctx, int mode);
+
+/* The contraction the last steps used (0 CUDA cores, 1 tensor cores). */
+int dg_get_contraction(dg_ctx *ctx, int *mode);
+
 /* Test hook (no counterpart in the paper): the n-th device allocation of the
  * library from now on (0 = the next one, in any context) fails as if the
  * device were out of memory; -1 disarms.  Calls that hit it return

@@ -95,6 +95,10 @@ EXPORTS = {
     "dg_basis_tables": (_I, [_I, _I, _DP, _DP, _DP, _DP]),
     "dg_set_growing_window": (_I, [_P, _D]),
     "dg_debug_fail_alloc": (_I, [_I]),
+    "dg_set_launch": (_I, [_P, _I]),
+    "dg_get_launch": (_I, [_P, ctypes.POINTER(_I)]),
+    "dg_set_contraction": (_I, [_P, _I]),
+    "dg_get_contraction": (_I, [_P, ctypes.POINTER(_I)]),
     "dg_debug_copies": (_I, [_P, _I, ctypes.POINTER(ctypes.c_ulonglong)]),
     "dg_triangle_tables": (_I, [_I, _DP, _DP, _DP, _DP, _DP]),
     # learned surrogate (include/dgsurrogate.h)
@@ -278,6 +282,26 @@ class DGSolver:
         """Advance only elements within r_factor sqrt(sigma0^2 + 2 D t) of the
         start-point box (0 turns it off)."""
         self._ck(self._L.dg_set_growing_window(self.ctx, float(r_factor)), "dg_set_growing_window")
+
+    def set_launch(self, blocks_per_sm: int):
+        """Stage-kernel launch shape: -1 tuned, 0 one block per chunk, k
+        persistent blocks per SM."""
+        self._ck(self._L.dg_set_launch(self.ctx, int(blocks_per_sm)), "dg_set_launch")
+
+    def get_launch(self) -> int:
+        k = ctypes.c_int()
+        self._ck(self._L.dg_get_launch(self.ctx, ctypes.byref(k)), "dg_get_launch")
+        return k.value
+
+    def set_contraction(self, mode: int):
+        """FP32 p = 5 element contractions: -1 tuned, 0 CUDA cores, 1 tensor
+        cores."""
+        self._ck(self._L.dg_set_contraction(self.ctx, int(mode)), "dg_set_contraction")
+
+    def get_contraction(self) -> int:
+        k = ctypes.c_int()
+        self._ck(self._L.dg_get_contraction(self.ctx, ctypes.byref(k)), "dg_get_contraction")
+        return k.value
 
     def step(self, nsteps: int, dt: float):
         self._ck(self._L.dg_step(self.ctx, int(nsteps), float(dt)), "dg_step")

@@ -176,6 +176,8 @@ int take_device_error(dg_ctx *ctx) {
   CK(cudaStreamSynchronize(c.stream), "error flag");
   if (flag) {
     CK(cudaMemsetAsync(c.d_err, 0, sizeof(int), c.stream), "error flag");
+    if (flag == 2)
+      return fail(ctx, DG_ECUDA, "a stage kernel found its shared memory misaligned for tensor copies");
     return fail(ctx, DG_ETIMEOUT, "a stage kernel gave up waiting for its shared-memory copies");
   }
   return DG_OK;
@@ -194,7 +196,97 @@ StageCopies stage_copies(Ctx &c, int in_array, bool with_u0) {
   cp.limit = c.copy_mode == 2 ? (1 << 12) : (1 << 22);
   cp.err = c.d_err;
   cp.counter = c.d_tma;
+  cp.pipe_blocks = c.launch_blocks;
+  cp.tensor_core = c.contraction_tc;
   return cp;
+}
+
+// Launch shape of the FP32 stage kernel (one block per chunk, or persistent
+// with k blocks per SM) and, at p = 5, where its element contractions run
+// (CUDA cores or tensor cores).  Tuned: each candidate runs RK stage 1 with
+// dt = 0 (U1 = U, bit for bit, so the probe changes nothing the next step
+// reads) once untimed and three times timed with CUDA events on the
+// context's stream; the fastest is kept for this number of densities and
+// elements.  Under stream capture nothing can be timed: the one-block-per-
+// chunk launch on the CUDA cores is taken.
+int resolve_launch(dg_ctx *ctx) {
+  Ctx &c = ctx->c;
+  const bool fp32 = c.cfg.precision == DG_FP32 && !c.triangles() && c.tmap_ok && c.copy_mode != 1;
+  const int maxb = fp32 ? stage_pipe_max_blocks(c.cfg.precision, c.cfg.p, c.geo) : 0;
+  const bool tc_ok = fp32 && c.cfg.p == 5 && stage_tc_max_blocks(c.geo) >= 1;
+  int want = 0, want_tc = 0;
+  const bool fixed = c.launch_req >= 0 || maxb < 1;
+  const bool fixed_tc = c.contraction_req >= 0 || !tc_ok;
+  if (fixed) want = maxb < 1 ? 0 : std::min(c.launch_req, maxb);
+  if (fixed_tc) want_tc = tc_ok && c.contraction_req == 1 ? 1 : 0;
+  if (!(fixed && fixed_tc)) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(c.stream, &cap), "capture status");
+    if (c.copy_mode != 0 || cap != cudaStreamCaptureStatusNone) {
+      // a test hook is active or nothing can be timed: the plain launch
+      if (!fixed) want = 0;
+      if (!fixed_tc) want_tc = 0;
+    } else if (c.tuned_key[0] == c.m && c.tuned_key[1] == c.geo.n_pad && c.tuned_blocks >= 0) {
+      if (!fixed) want = std::min(c.tuned_blocks, maxb);
+      if (!fixed_tc) want_tc = c.tuned_tc;
+    } else {
+      TraceRange trace("launch tuning");
+      std::vector<std::pair<int, int>> cand;  // (blocks per SM, tensor cores)
+      for (int k = fixed ? want : 0; k <= (fixed ? want : maxb); ++k)
+        for (int t = fixed_tc ? want_tc : 0; t <= (fixed_tc ? want_tc : 1); ++t)
+          if (t == 0 || k == 0) cand.push_back({k, t});  // no persistent tensor-core kernel
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      CK(cudaEventCreate(&e0), "tuning event");
+      cudaError_t e = cudaEventCreate(&e1);
+      const double pen = c.cfg.eta * (c.cfg.p + 1.0) * (c.cfg.p + 1.0) * 0.5;
+      const StageCoef<float> sc{0.0f, 1.0f, 0.0f, (float)pen, c.cfg.wall_mode == DG_WALL_PAPER,
+                                c.cfg.rounding == DG_ROUND_STOCHASTIC};
+      float best = 0.0f;
+      std::pair<int, int> best_c = cand[0];
+      for (size_t q = 0; q < cand.size() && e == cudaSuccess; ++q) {
+        StageCopies cp = stage_copies(c, 0, false);
+        cp.pipe_blocks = cand[q].first;
+        cp.tensor_core = cand[q].second;
+        auto probe = [&]() {
+          return launch_stage_f32(c.cfg.p, (const float *)state_array(c, 0), nullptr,
+                                  (float *)state_array(c, 1), c.geo, c.geo.n_pad, c.m, c.gll, sc,
+                                  c.stream, ChunkSel{}, cp);
+        };
+        e = probe();
+        if (e == cudaSuccess) e = cudaEventRecord(e0, c.stream);
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = probe();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c.stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && (q == 0 || ms < best)) {
+          best = ms;
+          best_c = cand[q];
+        }
+      }
+      cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "launch tuning");
+      if (const int r = take_device_error(ctx); r != DG_OK) return r;
+      c.tuned_blocks = best_c.first;
+      c.tuned_tc = best_c.second;
+      c.tuned_key[0] = c.m;
+      c.tuned_key[1] = c.geo.n_pad;
+      if (!fixed) want = best_c.first;
+      if (!fixed_tc) want_tc = best_c.second;
+    }
+  }
+  if (want_tc) {  // the tensor-core kernel's operator table, before any capture
+    const cudaError_t e = stage_tc_prepare(c.gll, c.stream);
+    if (e == cudaErrorNotSupported) want_tc = 0;
+    else if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core operator");
+  }
+  if (want != c.launch_blocks || want_tc != c.contraction_tc) {
+    c.launch_blocks = want;
+    c.contraction_tc = want_tc;
+    drop_graph(c);  // captured launches carry the old shape
+  }
+  return DG_OK;
 }
 
 // One SSP-RK3 step: U1 = U + dt L U; U2 = 3/4 U + 1/4 (U1 + dt L U1);
@@ -381,6 +473,9 @@ int run_steps_window(dg_ctx *ctx, int nsteps, double dt, double t0) {
 }
 
 int run_steps(dg_ctx *ctx, int nsteps, double dt, double t0) {
+  if (nsteps > 0) {
+    if (const int r = resolve_launch(ctx); r != DG_OK) return r;
+  }
   if (ctx->c.gw_r > 0.0) return run_steps_window(ctx, nsteps, dt, t0);
   return run_steps_fixed(ctx, nsteps, dt);
 }
@@ -870,6 +965,40 @@ int dg_debug_copies(dg_ctx *ctx, int mode, unsigned long long *tensor_copies) {
     c.copy_mode = mode;
     drop_graph(c);  // captured launches carry the old settings
   }
+  return DG_OK;
+}
+
+int dg_set_launch(dg_ctx *ctx, int blocks_per_sm) {
+  if (!ctx || blocks_per_sm < -1 || blocks_per_sm > 64) return DG_EINVAL;
+  Ctx &c = ctx->c;
+  if (blocks_per_sm != c.launch_req) {
+    c.launch_req = blocks_per_sm;
+    c.tuned_blocks = -1;
+    c.tuned_key[0] = c.tuned_key[1] = -1;
+  }
+  return DG_OK;
+}
+
+int dg_set_contraction(dg_ctx *ctx, int mode) {
+  if (!ctx || mode < -1 || mode > 1) return DG_EINVAL;
+  Ctx &c = ctx->c;
+  if (mode != c.contraction_req) {
+    c.contraction_req = mode;
+    c.tuned_blocks = -1;
+    c.tuned_key[0] = c.tuned_key[1] = -1;
+  }
+  return DG_OK;
+}
+
+int dg_get_contraction(dg_ctx *ctx, int *mode) {
+  if (!ctx || !mode) return DG_EINVAL;
+  *mode = ctx->c.contraction_tc;
+  return DG_OK;
+}
+
+int dg_get_launch(dg_ctx *ctx, int *blocks_per_sm) {
+  if (!ctx || !blocks_per_sm) return DG_EINVAL;
+  *blocks_per_sm = ctx->c.launch_blocks;
   return DG_OK;
 }
 

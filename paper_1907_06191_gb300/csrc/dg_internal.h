@@ -219,6 +219,21 @@ struct Ctx {
   bool tmap_ok = false;
   int copy_mode = 0;              // 0 tensor copies where possible, 1 cp.async only,
                                   // 2 test hook: barriers that never complete
+  // Launch shape of the FP32 stage kernel: launch_req -1 = tuned (the
+  // candidates are timed before the first steps of a set of densities),
+  // 0 = one block per chunk, k >= 1 = persistent with k blocks per SM.
+  // launch_blocks is the shape in use; the tuned value is kept per
+  // (densities, padded elements).
+  int launch_req = -1;
+  int launch_blocks = 0;
+  int tuned_blocks = -1;
+  // Element contractions of the FP32 p = 5 stage: contraction_req -1 =
+  // tuned with the launch shape, 0 = CUDA cores, 1 = tensor cores;
+  // contraction_tc is the choice in use.
+  int contraction_req = -1;
+  int contraction_tc = 0;
+  int tuned_tc = 0;
+  long long tuned_key[2] = {-1, -1};
   int *d_err = nullptr;           // a bounded device wait gave up (and the copy counter)
   unsigned long long *d_tma = nullptr;
   size_t part_elems = 0;
@@ -276,7 +291,23 @@ struct StageCopies {
   int use_tma = 0, extra_tx = 0, limit = 1 << 22;
   int *err = nullptr;
   unsigned long long *counter = nullptr;
+  // persistent launch (k_stage_pipe) with this many blocks per SM where the
+  // variant has one (FP32 p = 1, 3 with tensor copies); 0: one block per chunk
+  int pipe_blocks = 0;
+  // FP32 p = 5: element contractions on the tensor cores (k_stage_tc)
+  int tensor_core = 0;
 };
+// Blocks per SM the persistent stage kernel of (precision, p) can keep
+// resident with this geometry's shared memory; 0 if it has no such variant.
+int stage_pipe_max_blocks(int precision, int p, const Geometry &geo);
+// The FP32 stage at p = 5 with the element contractions on the tensor cores;
+// cudaErrorNotSupported where it does not apply (other p, no tensor copies).
+cudaError_t launch_stage_tc_f32(const float *u, const float *u0, float *out, const Geometry &geo,
+                                long long stride, int m, const Gll &g,
+                                const StageCoef<float> &c, cudaStream_t s, const ChunkSel &sel,
+                                const StageCopies &cp);
+int stage_tc_max_blocks(const Geometry &geo);
+cudaError_t stage_tc_prepare(const Gll &g, cudaStream_t s);
 // One stage over all m densities: out = u0 + beta (u - u0) + gamma R(u).
 cudaError_t launch_stage_f64(int p, const double *u, const double *u0, double *out,
                              const Geometry &geo, long long stride, int m,

@@ -213,6 +213,60 @@ __device__ __forceinline__ void tma_store_rows(const CUtensorMap *map, int row, 
   asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
   asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
 }
+// L2 eviction priorities.  The stage kernels stream three state arrays
+// (gigabytes) past the small per-chunk geometry tables that every density's
+// blocks read again; marking the streams that no later block of the launch
+// reads (u0 chunks, result chunks) evict-first and the tables evict-last
+// keeps the tables in L2 from one density to the next.
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void tma_load_rows_hint(uint32_t dst, const CUtensorMap *map, int row,
+                                                   uint32_t bar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+      "[%0], [%1, {%2, %3}], [%4], %5;\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(row), "r"(bar), "l"(pol)
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_rows_hint(const CUtensorMap *map, int row, uint32_t src,
+                                                    uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group.L2::cache_hint [%0, {%1, %2}], [%3], "
+      "%4;\n" ::"l"(reinterpret_cast<uint64_t>(map)),
+      "r"(0), "r"(row), "r"(src), "l"(pol)
+      : "memory");
+  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+// Read-only loads of table entries with an L2 policy.
+__device__ __forceinline__ int4 ldg_hint(const int4 *p, uint64_t pol) {
+  int4 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;\n"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ int2 ldg_hint(const int2 *p, uint64_t pol) {
+  int2 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.s32 {%0, %1}, [%2], %3;\n"
+               : "=r"(v.x), "=r"(v.y)
+               : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ int ldg_hint(const int *p, uint64_t pol) {
+  int v;
+  asm volatile("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;\n" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+
 // Make this thread's shared-memory writes visible to the tensor copies.
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -396,6 +450,240 @@ __device__ __forceinline__ void face_record(const T (&u)[(P + 1) * (P + 1)], int
   for (int t = 0; t < P + 1; ++t) tr[t] = u[Faces<P>::own(f, t)];
 }
 
+// ---- one stage on one element: the pieces both stage kernels share --------
+
+// The element's face records (trace and outward derivative of each face,
+// record f*kBlock + el) and its volume term R = sum_i (DD)_ai u_ib +
+// sum_j (DD)_bj u_aj.
+template <typename T, int P>
+__device__ __forceinline__ void element_records_volume(const T (&u)[(P + 1) * (P + 1)],
+                                                       const StageTab<T, P> &tb,
+                                                       const Records<T, P> &rec, int el,
+                                                       T (&R)[(P + 1) * (P + 1)]) {
+  constexpr int n = P + 1;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    T tr[n], d[n];
+    face_record<T, P>(u, f, tb, tr, d);
+    rec.put(f * kBlock + el, tr, d);
+  }
+  if constexpr (kPacked<T, P>) {
+    // nodes (j, i) and (j, i + 1) together: the x part pairs a column of
+    // D2 with u_jm, the y part a value of D2 with u_m,i..i+1
+#pragma unroll
+    for (int j = 0; j < n; ++j)
+#pragma unroll
+      for (int ip = 0; ip < n / 2; ++ip) {
+        float2 s = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int m = 0; m < n; ++m) {
+          s = __ffma2_rn(tb.D2x[ip * n + m], make_float2(u[j * n + m], u[j * n + m]), s);
+          s = __ffma2_rn(tb.D2y[j * n + m],
+                         make_float2(u[m * n + 2 * ip], u[m * n + 2 * ip + 1]), s);
+        }
+        R[j * n + 2 * ip] = s.x;
+        R[j * n + 2 * ip + 1] = s.y;
+      }
+    if constexpr (n % 2 == 1) {  // the last node of each row
+      constexpr int i = n - 1;
+#pragma unroll
+      for (int j = 0; j < n; ++j) {
+        T s = 0;
+#pragma unroll
+        for (int m = 0; m < n; ++m)
+          s = fmaT(tb.D2[j * n + m], u[m * n + i], fmaT(tb.D2[i * n + m], u[j * n + m], s));
+        R[j * n + i] = s;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < n; ++j)
+#pragma unroll
+      for (int i = 0; i < n; ++i) {
+        T s = 0;
+#pragma unroll
+        for (int m = 0; m < n; ++m)
+          s = fmaT(tb.D2[j * n + m], u[m * n + i], fmaT(tb.D2[i * n + m], u[j * n + m], s));
+        R[j * n + i] = s;
+      }
+  }
+}
+
+// Record of the face `face` of a halo element (values v) in record `r`.
+template <typename T, int P>
+__device__ __forceinline__ void halo_face_record(const T (&v)[(P + 1) * (P + 1)], int face,
+                                                 const StageTab<T, P> &tb,
+                                                 const Records<T, P> &rec, int r) {
+  constexpr int n = P + 1;
+  T tr[n], d[n];
+  switch (face) {  // the face of the halo element that touches the chunk
+    case 0: face_record<T, P>(v, 0, tb, tr, d); break;
+    case 1: face_record<T, P>(v, 1, tb, tr, d); break;
+    case 2: face_record<T, P>(v, 2, tb, tr, d); break;
+    default: face_record<T, P>(v, 3, tb, tr, d); break;
+  }
+  rec.put(r, tr, d);
+}
+
+// Flux and lifting terms of the four faces added to R (see the file header);
+// lq: the element's neighbour codes (chunk slot, kBlock + halo slot, kWall,
+// kEdge).
+template <typename T, int P, bool FULL>
+__device__ __forceinline__ void element_flux(const T (&u)[(P + 1) * (P + 1)],
+                                             T (&R)[(P + 1) * (P + 1)], const int (&lq)[4],
+                                             int el, int zero_rec, const Records<T, P> &rec,
+                                             const StageTab<T, P> &tb, const StageCoef<T> &c) {
+  constexpr int n = P + 1;
+  using Fc = Faces<P>;
+  const T half = (T)0.5, iw = tb.inv_w;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    const int L = lq[f];
+    const int fo = Fc::opp(f);
+    // neighbour record: chunk element, halo entry, or the zero record
+    const int rn = L >= kBlock ? 4 * kBlock + (L - kBlock) : (L >= 0 ? fo * kBlock + L : zero_rec);
+    // face-kind coefficients with 1/w (and, for the lifting, the face sign)
+    // folded in: gs = s_f g / w = cg_up u+ + cg_um u-, and the face term
+    // F / w = c_od d- + c_odn d+ (+ c_um u- + c_up u+)   (see file header)
+    const bool in = L >= 0, wl = L == kWall, wa = wl && c.wallA, ed = L == kEdge;
+    const T sw = (f & 1) ? -iw : iw;
+    const T cg_up = in ? half * sw : (T)0;
+    const T cg_um = in ? -half * sw : (wa ? -half * sw : (ed ? -sw : (T)0));
+    const T c_od = in ? half * iw : (ed ? (T)0 : iw);
+    const T c_odn = in ? half * iw : (T)0;
+    T up[n], odn[n], od[n];
+    rec.get_tr(rn, up);
+    rec.get_d(rn, odn);
+    rec.get_d(f * kBlock + el, od);
+    T gs[n];
+    if constexpr (FULL) {
+      const T c_um = (in ? c.pen : (wa ? -half * iw : (ed ? c.pen : (T)0))) * iw;
+      const T c_up = in ? -c.pen * iw : (T)0;
+#pragma unroll
+      for (int t = 0; t < n; ++t) {
+        const T um = u[Fc::own(f, t)];
+        gs[t] = cg_up * up[t] + cg_um * um;
+        T r = R[Fc::own(f, t)];
+        r = fmaT(-c_od, od[t], r);
+        r = fmaT(-c_odn, odn[t], r);
+        r = fmaT(-c_um, um, r);
+        R[Fc::own(f, t)] = fmaT(-c_up, up[t], r);
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < n; ++t) {
+        gs[t] = cg_up * up[t] + cg_um * u[Fc::own(f, t)];
+        R[Fc::own(f, t)] = fmaT(-c_odn, odn[t], fmaT(-c_od, od[t], R[Fc::own(f, t)]));
+      }
+    }
+    // lifting of the u-flux jump: column (x-faces) or row (y-faces) of D
+    const int r = Fc::row(f);
+#pragma unroll
+    for (int t = 0; t < n; ++t) {
+#pragma unroll
+      for (int q = 0; q < n; ++q) {
+        if (f < 2) R[t * n + q] += tb.D[q * n + r] * gs[t];
+        else R[q * n + t] += tb.D[q * n + r] * gs[t];
+      }
+    }
+  }
+}
+
+// Stage update of one element: o = o + beta (u - o) + gam R with o = u0 on
+// entry (HAS_U0), else o = beta u + gam R; FP32 with stochastic rounding
+// rounds o + increment once per node, keyed by the element hash h.
+template <typename T, int P, bool HAS_U0, bool SROUND>
+__device__ __forceinline__ void element_update(const T (&u)[(P + 1) * (P + 1)],
+                                               const T (&R)[(P + 1) * (P + 1)],
+                                               T (&o)[(P + 1) * (P + 1)], T gam, uint32_t h,
+                                               const StageCoef<T> &c) {
+  constexpr int NP = (P + 1) * (P + 1);
+  if constexpr (SROUND) {
+    // increment first, then one stochastic rounding onto the state
+    if constexpr (kPacked<T, P>) {  // the same arithmetic, two nodes per instruction
+      const float2 b2 = make_float2(c.beta, c.beta), g2 = make_float2(gam, gam);
+#pragma unroll
+      for (int k = 0; k + 1 < NP; k += 2) {
+        const float2 u2 = make_float2(u[k], u[k + 1]), gr = __fmul2_rn(g2, make_float2(R[k], R[k + 1]));
+        float2 bs, in;
+        if constexpr (HAS_U0) {
+          bs = make_float2(o[k], o[k + 1]);
+          in = __ffma2_rn(b2, __ffma2_rn(bs, make_float2(-1.0f, -1.0f), u2), gr);
+        } else {
+          bs = __fmul2_rn(b2, u2);
+          in = gr;
+        }
+        const float2 w = add_stochastic2(bs, in, h + (uint32_t)k, h + (uint32_t)(k + 1));
+        o[k] = w.x;
+        o[k + 1] = w.y;
+      }
+      if constexpr (NP % 2 == 1) {  // the last node on its own
+        constexpr int k = NP - 1;
+        const T bs = HAS_U0 ? o[k] : c.beta * u[k];
+        const T in = HAS_U0 ? fmaf(c.beta, u[k] - o[k], gam * R[k]) : gam * R[k];
+        o[k] = add_stochastic(bs, in, h + (uint32_t)k);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        const T bs = HAS_U0 ? o[k] : c.beta * u[k];
+        const T in = HAS_U0 ? fmaf(c.beta, u[k] - o[k], gam * R[k]) : gam * R[k];
+        o[k] = add_stochastic(bs, in, h + (uint32_t)k);
+      }
+    }
+  } else if constexpr (HAS_U0) {
+    if constexpr (kPacked<T, P>) {  // o + (beta (u - o) + gam R)
+      const float2 b2 = make_float2(c.beta, c.beta), g2 = make_float2(gam, gam);
+#pragma unroll
+      for (int k = 0; k + 1 < NP; k += 2) {
+        const float2 o2 = make_float2(o[k], o[k + 1]);
+        const float2 d = __ffma2_rn(o2, make_float2(-1.0f, -1.0f), make_float2(u[k], u[k + 1]));
+        const float2 w = __fadd2_rn(
+            o2, __ffma2_rn(b2, d, __fmul2_rn(g2, make_float2(R[k], R[k + 1]))));
+        o[k] = w.x;
+        o[k + 1] = w.y;
+      }
+      if constexpr (NP % 2 == 1) {
+        constexpr int k = NP - 1;
+        o[k] = o[k] + fmaf(c.beta, u[k] - o[k], gam * R[k]);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < NP; ++k) o[k] = o[k] + c.beta * (u[k] - o[k]) + gam * R[k];
+    }
+  } else if constexpr (kPacked<T, P>) {
+    const float2 b2 = make_float2(c.beta, c.beta), g2 = make_float2(gam, gam);
+#pragma unroll
+    for (int k = 0; k + 1 < NP; k += 2) {
+      const float2 w = __ffma2_rn(b2, make_float2(u[k], u[k + 1]),
+                                  __fmul2_rn(g2, make_float2(R[k], R[k + 1])));
+      o[k] = w.x;
+      o[k + 1] = w.y;
+    }
+    if constexpr (NP % 2 == 1) {
+      constexpr int k = NP - 1;
+      o[k] = fmaf(c.beta, u[k], gam * R[k]);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < NP; ++k) o[k] = c.beta * u[k] + gam * R[k];
+  }
+}
+
+// Stochastic-rounding key of an element: one avalanche hash of its place in
+// its own geometry, its density and the bits of its first two input values
+// (they change every stage while the element is advancing), so a geometry
+// gives the same bits alone or in a batch, and either stage kernel the same.
+template <typename T>
+__device__ __forceinline__ uint32_t element_key(long long elem_in_geo, int np, int density,
+                                                const T *u) {
+  if constexpr (sizeof(T) == 4)
+    return fmix32(((uint32_t)elem_in_geo * (uint32_t)np) ^ ((uint32_t)density * 0x632be5abu) ^
+                  __float_as_uint(u[0]) ^ (__float_as_uint(u[1]) * 0x85ebca77u));
+  else
+    return 0u;
+}
+
 // grid: (chunks launched, m): block x takes chunk chunk_list[x] (x itself
 // without a list); density s = blockIdx.y starts at s * stride
 // elements.  loc/halo tables come from the geometry (entries checked when
@@ -436,7 +724,6 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
             const __grid_constant__ CUtensorMap tm_out, const CopyArgs ca) {
   constexpr int n = P + 1, NP = n * n;
   using St = Stage<T, NP>;
-  using Fc = Faces<P>;
   // shared memory: [u chunk, later the face records][u0 chunk, later the
   // result][two mbarriers]; the first two start on 1024-byte boundaries so
   // that the swizzled tensor copies land in the Stage layout
@@ -452,7 +739,8 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
 
   const int chunk = chunk_list ? __ldg(chunk_list + blockIdx.x) : (int)blockIdx.x;
   const long long a0 = (long long)chunk * kBlock;
-  const int2 ci = __ldg(chunk_tab + chunk);  // {elements in the mesh, geometry}
+  const uint64_t pol_last = l2_policy_evict_last();
+  const int2 ci = ldg_hint(chunk_tab + chunk, pol_last);
   const int cnt = ci.x;
   const int el = threadIdx.x;
   const bool live = el < cnt;
@@ -478,7 +766,7 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
       tma_load_rows(smem_u32(su), &tm_u, row, bar0);
       if constexpr (HAS_U0) {
         mbar_expect_tx(bar1, bytes);
-        tma_load_rows(smem_u32(so), &tm_u0, row, bar1);
+        tma_load_rows_hint(smem_u32(so), &tm_u0, row, bar1, l2_policy_evict_first());
       }
       if (ca.counter) atomicAdd(ca.counter, 1ull);
     }
@@ -495,12 +783,12 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
       cp_async_commit();
     }
   }
-  const int4 l4 = live ? __ldg(loc + a0 + el) : make_int4(kEdge, kEdge, kEdge, kEdge);
-  const int hcnt = __ldg(halo_cnt + chunk);
+  const int4 l4 = live ? ldg_hint(loc + a0 + el, pol_last) : make_int4(kEdge, kEdge, kEdge, kEdge);
+  const int hcnt = ldg_hint(halo_cnt + chunk, pol_last);
   // first halo entry of this thread (entries past the chunk's count hold
   // element -1, so the count is not waited for): element values into
   // registers while the chunk copies are in flight
-  const int2 hk = __ldg(halo + (size_t)chunk * kHaloCap + el);
+  const int2 hk = ldg_hint(halo + (size_t)chunk * kHaloCap + el, pol_last);
   T hv[NP];
   if (hk.x >= 0) load_elem<T, NP>(U + (size_t)hk.x * NP, hv);
   // Each thread waits (bounded) for the u chunk itself: completing the
@@ -532,132 +820,19 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
     for (int t = 0; t < n; ++t) z[t] = (T)0;
     rec.put(zero_rec, z, z);
   }
-  if (live) {
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      T tr[n], d[n];
-      face_record<T, P>(u, f, tb, tr, d);
-      rec.put(f * kBlock + el, tr, d);
-    }
-    if constexpr (kPacked<T, P>) {
-      // nodes (j, i) and (j, i + 1) together: the x part pairs a column of
-      // D2 with u_jm, the y part a value of D2 with u_m,i..i+1
-#pragma unroll
-      for (int j = 0; j < n; ++j)
-#pragma unroll
-        for (int ip = 0; ip < n / 2; ++ip) {
-          float2 s = make_float2(0.0f, 0.0f);
-#pragma unroll
-          for (int m = 0; m < n; ++m) {
-            s = __ffma2_rn(tb.D2x[ip * n + m], make_float2(u[j * n + m], u[j * n + m]), s);
-            s = __ffma2_rn(tb.D2y[j * n + m],
-                           make_float2(u[m * n + 2 * ip], u[m * n + 2 * ip + 1]), s);
-          }
-          R[j * n + 2 * ip] = s.x;
-          R[j * n + 2 * ip + 1] = s.y;
-        }
-      if constexpr (n % 2 == 1) {  // the last node of each row
-        constexpr int i = n - 1;
-#pragma unroll
-        for (int j = 0; j < n; ++j) {
-          T s = 0;
-#pragma unroll
-          for (int m = 0; m < n; ++m)
-            s = fmaT(tb.D2[j * n + m], u[m * n + i], fmaT(tb.D2[i * n + m], u[j * n + m], s));
-          R[j * n + i] = s;
-        }
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < n; ++j)
-#pragma unroll
-        for (int i = 0; i < n; ++i) {
-          T s = 0;
-#pragma unroll
-          for (int m = 0; m < n; ++m)
-            s = fmaT(tb.D2[j * n + m], u[m * n + i], fmaT(tb.D2[i * n + m], u[j * n + m], s));
-          R[j * n + i] = s;
-        }
-    }
-  }
-  if (hk.x >= 0) {
-    T tr[n], d[n];
-    switch (hk.y) {  // the face of the halo element that touches the chunk
-      case 0: face_record<T, P>(hv, 0, tb, tr, d); break;
-      case 1: face_record<T, P>(hv, 1, tb, tr, d); break;
-      case 2: face_record<T, P>(hv, 2, tb, tr, d); break;
-      default: face_record<T, P>(hv, 3, tb, tr, d); break;
-    }
-    rec.put(4 * kBlock + el, tr, d);
-  }
+  if (live) element_records_volume<T, P>(u, tb, rec, el, R);
+  if (hk.x >= 0) halo_face_record<T, P>(hv, hk.y, tb, rec, 4 * kBlock + el);
   for (int h = el + kBlock; h < hcnt; h += kBlock) {  // chunks with > kBlock halo entries
     const int2 q = __ldg(halo + (size_t)chunk * kHaloCap + h);
-    T v[NP], tr[n], d[n];
+    T v[NP];
     load_elem<T, NP>(U + (size_t)q.x * NP, v);
-    switch (q.y) {
-      case 0: face_record<T, P>(v, 0, tb, tr, d); break;
-      case 1: face_record<T, P>(v, 1, tb, tr, d); break;
-      case 2: face_record<T, P>(v, 2, tb, tr, d); break;
-      default: face_record<T, P>(v, 3, tb, tr, d); break;
-    }
-    rec.put(4 * kBlock + h, tr, d);
+    halo_face_record<T, P>(v, q.y, tb, rec, 4 * kBlock + h);
   }
   __syncthreads();
 
   if (live) {
     const int lq[4] = {l4.x, l4.y, l4.z, l4.w};
-    const T half = (T)0.5, iw = tb.inv_w;
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      const int L = lq[f];
-      const int fo = Fc::opp(f);
-      // neighbour record: chunk element, halo entry, or the zero record
-      const int rn = L >= kBlock ? 4 * kBlock + (L - kBlock) : (L >= 0 ? fo * kBlock + L : zero_rec);
-      // face-kind coefficients with 1/w (and, for the lifting, the face sign)
-      // folded in: gs = s_f g / w = cg_up u+ + cg_um u-, and the face term
-      // F / w = c_od d- + c_odn d+ (+ c_um u- + c_up u+)   (see file header)
-      const bool in = L >= 0, wl = L == kWall, wa = wl && c.wallA, ed = L == kEdge;
-      const T sw = (f & 1) ? -iw : iw;
-      const T cg_up = in ? half * sw : (T)0;
-      const T cg_um = in ? -half * sw : (wa ? -half * sw : (ed ? -sw : (T)0));
-      const T c_od = in ? half * iw : (ed ? (T)0 : iw);
-      const T c_odn = in ? half * iw : (T)0;
-      T up[n], odn[n], od[n];
-      rec.get_tr(rn, up);
-      rec.get_d(rn, odn);
-      rec.get_d(f * kBlock + el, od);
-      T gs[n];
-      if constexpr (FULL) {
-        const T c_um = (in ? c.pen : (wa ? -half * iw : (ed ? c.pen : (T)0))) * iw;
-        const T c_up = in ? -c.pen * iw : (T)0;
-#pragma unroll
-        for (int t = 0; t < n; ++t) {
-          const T um = u[Fc::own(f, t)];
-          gs[t] = cg_up * up[t] + cg_um * um;
-          T r = R[Fc::own(f, t)];
-          r = fmaT(-c_od, od[t], r);
-          r = fmaT(-c_odn, odn[t], r);
-          r = fmaT(-c_um, um, r);
-          R[Fc::own(f, t)] = fmaT(-c_up, up[t], r);
-        }
-      } else {
-#pragma unroll
-        for (int t = 0; t < n; ++t) {
-          gs[t] = cg_up * up[t] + cg_um * u[Fc::own(f, t)];
-          R[Fc::own(f, t)] = fmaT(-c_odn, odn[t], fmaT(-c_od, od[t], R[Fc::own(f, t)]));
-        }
-      }
-      // lifting of the u-flux jump: column (x-faces) or row (y-faces) of D
-      const int r = Fc::row(f);
-#pragma unroll
-      for (int t = 0; t < n; ++t) {
-#pragma unroll
-        for (int q = 0; q < n; ++q) {
-          if (f < 2) R[t * n + q] += tb.D[q * n + r] * gs[t];
-          else R[q * n + t] += tb.D[q * n + r] * gs[t];
-        }
-      }
-    }
+    element_flux<T, P, FULL>(u, R, lq, el, zero_rec, rec, tb, c);
   }
 
   // the u0 chunk: the same per-thread bounded wait.  With stochastic
@@ -681,87 +856,11 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
   }
   if (live && ok) {
     T o[NP];
-    if constexpr (SROUND) {
-      // increment first, then one stochastic rounding onto the state; the key
-      // is the node's place inside its own geometry and its density, so a
-      // geometry gives the same bits alone or in a batch
-      if constexpr (HAS_U0) St::read(so, el, o);
-      // one avalanche hash per element: its place in its geometry, its
-      // density and the bits of its first two input values (they change
-      // every stage while the element is advancing)
-      const uint32_t h = fmix32(
-          ((uint32_t)(a0 + el - __ldg(grange + ci.y).x) * (uint32_t)NP) ^
-          ((uint32_t)blockIdx.y * 0x632be5abu) ^ __float_as_uint(u[0]) ^
-          (__float_as_uint(u[1]) * 0x85ebca77u));
-      if constexpr (kPacked<T, P>) {  // the same arithmetic, two nodes per instruction
-        const float2 b2 = make_float2(c.beta, c.beta), g2 = make_float2(gam, gam);
-#pragma unroll
-        for (int k = 0; k + 1 < NP; k += 2) {
-          const float2 u2 = make_float2(u[k], u[k + 1]), gr = __fmul2_rn(g2, make_float2(R[k], R[k + 1]));
-          float2 bs, in;
-          if constexpr (HAS_U0) {
-            bs = make_float2(o[k], o[k + 1]);
-            in = __ffma2_rn(b2, __ffma2_rn(bs, make_float2(-1.0f, -1.0f), u2), gr);
-          } else {
-            bs = __fmul2_rn(b2, u2);
-            in = gr;
-          }
-          const float2 w = add_stochastic2(bs, in, h + (uint32_t)k, h + (uint32_t)(k + 1));
-          o[k] = w.x;
-          o[k + 1] = w.y;
-        }
-        if constexpr (NP % 2 == 1) {  // the last node on its own
-          constexpr int k = NP - 1;
-          const T bs = HAS_U0 ? o[k] : c.beta * u[k];
-          const T in = HAS_U0 ? fmaf(c.beta, u[k] - o[k], gam * R[k]) : gam * R[k];
-          o[k] = add_stochastic(bs, in, h + (uint32_t)k);
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < NP; ++k) {
-          const T bs = HAS_U0 ? o[k] : c.beta * u[k];
-          const T in = HAS_U0 ? fmaf(c.beta, u[k] - o[k], gam * R[k]) : gam * R[k];
-          o[k] = add_stochastic(bs, in, h + (uint32_t)k);
-        }
-      }
-    } else if constexpr (HAS_U0) {
-      St::read(so, el, o);
-      if constexpr (kPacked<T, P>) {  // o + (beta (u - o) + gam R)
-        const float2 b2 = make_float2(c.beta, c.beta), g2 = make_float2(gam, gam);
-#pragma unroll
-        for (int k = 0; k + 1 < NP; k += 2) {
-          const float2 o2 = make_float2(o[k], o[k + 1]);
-          const float2 d = __ffma2_rn(o2, make_float2(-1.0f, -1.0f), make_float2(u[k], u[k + 1]));
-          const float2 w = __fadd2_rn(
-              o2, __ffma2_rn(b2, d, __fmul2_rn(g2, make_float2(R[k], R[k + 1]))));
-          o[k] = w.x;
-          o[k + 1] = w.y;
-        }
-        if constexpr (NP % 2 == 1) {
-          constexpr int k = NP - 1;
-          o[k] = o[k] + fmaf(c.beta, u[k] - o[k], gam * R[k]);
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < NP; ++k) o[k] = o[k] + c.beta * (u[k] - o[k]) + gam * R[k];
-      }
-    } else if constexpr (kPacked<T, P>) {
-      const float2 b2 = make_float2(c.beta, c.beta), g2 = make_float2(gam, gam);
-#pragma unroll
-      for (int k = 0; k + 1 < NP; k += 2) {
-        const float2 w = __ffma2_rn(b2, make_float2(u[k], u[k + 1]),
-                                    __fmul2_rn(g2, make_float2(R[k], R[k + 1])));
-        o[k] = w.x;
-        o[k + 1] = w.y;
-      }
-      if constexpr (NP % 2 == 1) {
-        constexpr int k = NP - 1;
-        o[k] = fmaf(c.beta, u[k], gam * R[k]);
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < NP; ++k) o[k] = c.beta * u[k] + gam * R[k];
-    }
+    if constexpr (HAS_U0) St::read(so, el, o);
+    const uint32_t h = SROUND ? element_key<T>(a0 + el - __ldg(grange + ci.y).x, NP,
+                                               (int)blockIdx.y, u)
+                              : 0u;
+    element_update<T, P, HAS_U0, SROUND>(u, R, o, gam, h, c);
     St::write(so, el, o);
   }
   const bool store_tma = tma && ca.store_tma && cnt == kBlock;  // a full chunk: one tiled store
@@ -771,7 +870,10 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
     return;
   }
   if (store_tma) {
-    if (el == 0) tma_store_rows(&tm_out, (int)((long long)blockIdx.y * stride + a0), smem_u32(so));
+    if (el == 0) {
+      const int row = (int)((long long)blockIdx.y * stride + a0);
+      tma_store_rows_hint(&tm_out, row, smem_u32(so), l2_policy_evict_first());
+    }
     return;
   }
   {  // coalesced 16-byte stores of the result chunk
@@ -781,6 +883,245 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
       *reinterpret_cast<float4 *>(go + 16 * (size_t)j) =
           *reinterpret_cast<const float4 *>(reinterpret_cast<unsigned char *>(so) + 16 * St::piece_dst(j));
   }
+}
+
+// ---- persistent variant: each block walks many chunks, one ahead ---------
+//
+// The kernel above spends a block's life in three phases -- wait for the
+// chunk copies and the tables, compute, store -- and with 4 blocks of 256 per
+// SM the SM often has every block in the same phase.  This variant launches a
+// few blocks per SM that stay resident and walk the work items (density,
+// chunk) item = blockIdx.x + k gridDim.x, density-major so that the items in
+// flight are neighbouring chunks of one density (their halos come from L2).
+// Everything the next item needs is fetched behind the current item's work:
+// its u chunk (tensor copy) as soon as this item's u is in registers, its
+// neighbour codes, halo entry and halo element values (registers) right
+// after, and its u0 chunk into the second of two u0 / result buffers, whose
+// previous result store has long been read.  Shared memory: [u chunk]
+// [u0 / result chunk x 2][face records][two mbarriers]; the chunks start on
+// 1024-byte boundaries (hardware swizzle).  Tensor copies only (element rows
+// of whole 16-byte slots); every item gives the same bits as the kernel above
+// (same arithmetic, same rounding keys).
+template <typename T, int P>
+__host__ __device__ constexpr int pipe_chunk_bytes() {
+  return (Stage<T, (P + 1) * (P + 1)>::CHUNK_BYTES + 1023) / 1024 * 1024;
+}
+
+template <typename T, int P>
+int pipe_smem_bytes(int halo_max) {
+  const int nrec = 4 * kBlock + halo_max + 1;
+  return 3 * pipe_chunk_bytes<T, P>() + Records<T, P>::bytes(nrec) + 16;
+}
+
+constexpr int kPipeMinBlocks = 2;  // blocks of 256 per SM the registers are sized for
+// the variants that have a persistent kernel: FP32 with whole-slot rows and
+// at least two such blocks per SM in shared memory (p = 1, 3)
+template <typename T, int P>
+constexpr bool kHasPipe = sizeof(T) == 4 && (P == 1 || P == 3);
+
+// What one thread needs of a work item besides the chunk copies.
+template <typename T, int P>
+struct PipeItem {
+  int sd, chunk;   // density, chunk
+  int2 ci;         // {elements in the mesh, geometry}
+  T gam;           // beta dt D / J^2, 0 for an element held by the growing window
+  int4 l4;         // neighbour codes of this thread's element
+  int hcnt;        // halo entries of the chunk
+  int2 hk;         // this thread's first halo entry
+  T hv[(P + 1) * (P + 1)];  // its element values
+};
+
+template <typename T, int P>
+__device__ __forceinline__ void pipe_fetch(PipeItem<T, P> &it, long long item, int nch, int el,
+                                           const T *__restrict__ uin, long long stride,
+                                           const int4 *__restrict__ loc,
+                                           const int2 *__restrict__ halo,
+                                           const int *__restrict__ halo_cnt,
+                                           const int2 *__restrict__ chunk_tab,
+                                           const T *__restrict__ gscale,
+                                           const int *__restrict__ chunk_list,
+                                           const uint8_t *__restrict__ adv, T gamma) {
+  constexpr int NP = (P + 1) * (P + 1);
+  it.sd = (int)(item / nch);
+  const int x = (int)(item - (long long)it.sd * nch);
+  it.chunk = chunk_list ? __ldg(chunk_list + x) : x;
+  const long long a0 = (long long)it.chunk * kBlock;
+  it.ci = __ldg(chunk_tab + it.chunk);
+  const bool live = el < it.ci.x;
+  it.gam = gamma * __ldg(gscale + it.ci.y);
+  if (adv != nullptr && live && __ldg(adv + a0 + el) == 0) it.gam = (T)0;
+  it.l4 = live ? __ldg(loc + a0 + el) : make_int4(kEdge, kEdge, kEdge, kEdge);
+  it.hcnt = __ldg(halo_cnt + it.chunk);
+  it.hk = __ldg(halo + (size_t)it.chunk * kHaloCap + el);
+  if (it.hk.x >= 0)
+    load_elem<T, NP>(uin + (size_t)it.sd * (size_t)stride * NP + (size_t)it.hk.x * NP, it.hv);
+}
+
+template <typename T, int P, bool HAS_U0, bool SROUND, bool FULL>
+__global__ void __launch_bounds__(kBlock, kPipeMinBlocks)
+    k_stage_pipe(const T *__restrict__ uin, const T *u0, T *out,
+                 const int4 *__restrict__ loc, const int2 *__restrict__ halo,
+                 const int *__restrict__ halo_cnt, const int2 *__restrict__ chunk_tab,
+                 const int2 *__restrict__ grange, const T *__restrict__ gscale, long long stride,
+                 int nrec, const int *__restrict__ chunk_list, const uint8_t *__restrict__ adv,
+                 const StageTab<T, P> tb, const StageCoef<T> c,
+                 const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_u0,
+                 const __grid_constant__ CUtensorMap tm_out, const CopyArgs ca, long long n_items,
+                 int nch) {
+  constexpr int n = P + 1, NP = n * n;
+  using St = Stage<T, NP>;
+  constexpr int CB = pipe_chunk_bytes<T, P>();
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  T *su = reinterpret_cast<T *>(smem_raw);
+  unsigned char *so_raw = smem_raw + CB;  // two buffers of CB bytes
+  T *rec_base = reinterpret_cast<T *>(smem_raw + 3 * CB);
+  Records<T, P> rec{rec_base,
+                    rec_base + ((nrec * n * (int)sizeof(T) + 15) / 16) * 16 / (int)sizeof(T), nrec};
+  const int zero_rec = nrec - 1;
+  const uint32_t bar0 = smem_u32(smem_raw + 3 * CB + Records<T, P>::bytes(nrec)), bar1 = bar0 + 8;
+  const int el = threadIdx.x;
+  if ((smem_u32(smem_raw) & 1023u) != 0) {  // the swizzled copies need this; never expected
+    if (el == 0) atomicExch(ca.err, 2);
+    return;
+  }
+  const long long G = gridDim.x;
+  long long item = blockIdx.x;
+  // first row of an item's chunk in the 2D state tensor [densities x padded elements]
+  auto item_row = [&](long long it) -> int {
+    const long long sd = it / nch, x = it - sd * nch;
+    const long long chunk = chunk_list ? __ldg(chunk_list + x) : x;
+    return (int)(sd * stride + chunk * kBlock);
+  };
+  const uint32_t bytes = (uint32_t)(kBlock * NP * sizeof(T)) + (uint32_t)ca.extra_tx;
+  if (el == 0) {
+    mbar_init(bar0, 1);
+    if constexpr (HAS_U0) mbar_init(bar1, 1);
+    mbar_fence_init();
+    if (item < n_items) {
+      const int row = item_row(item);
+      mbar_expect_tx(bar0, bytes);
+      tma_load_rows(smem_u32(su), &tm_u, row, bar0);
+      if constexpr (HAS_U0) {
+        mbar_expect_tx(bar1, bytes);
+        tma_load_rows(smem_u32(so_raw), &tm_u0, row, bar1);
+      }
+      if (ca.counter) atomicAdd(ca.counter, 1ull);
+    }
+  }
+  PipeItem<T, P> cur;
+  if (item < n_items)
+    pipe_fetch<T, P>(cur, item, nch, el, uin, stride, loc, halo, halo_cnt, chunk_tab, gscale,
+                     chunk_list, adv, c.gamma);
+  __syncthreads();  // the barriers exist before anyone polls them
+
+  // both barriers complete one phase per item: parity ph for this item;
+  // the u0 / result buffer of the k-th item of the block is buffer k & 1
+  for (uint32_t ph = 0; item < n_items; item += G, ph ^= 1u) {
+    T *so = reinterpret_cast<T *>(so_raw + (ph ? CB : 0));
+    const long long a0 = (long long)cur.chunk * kBlock;
+    const int cnt = cur.ci.x;
+    const bool live = el < cnt;
+    bool ok = mbar_wait(bar0, ph, ca.limit);
+    T u[NP], R[NP];
+    if (live && ok) St::read(su, el, u);
+    const long long next = item + G;
+    const bool more = next < n_items;
+    // order these reads of su before the tensor copy that refills it
+    fence_proxy_async_smem();
+    if (__syncthreads_or(!ok)) {  // leave as a block, after bounded waits for copies in flight
+      if constexpr (HAS_U0) mbar_wait(bar1, ph, ca.limit);
+      if (el == 0) {
+        asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+        atomicExch(ca.err, 1);
+      }
+      return;
+    }
+    // this item's u is in registers: the next item's u chunk and tables come
+    // in behind the work
+    if (el == 0 && more) {
+      mbar_expect_tx(bar0, bytes);
+      tma_load_rows(smem_u32(su), &tm_u, item_row(next), bar0);
+      if (ca.counter) atomicAdd(ca.counter, 1ull);
+    }
+    PipeItem<T, P> nxt;
+    if (more)
+      pipe_fetch<T, P>(nxt, next, nch, el, uin, stride, loc, halo, halo_cnt, chunk_tab, gscale,
+                       chunk_list, adv, c.gamma);
+    if (el == 0) {
+      T z[n];
+#pragma unroll
+      for (int t = 0; t < n; ++t) z[t] = (T)0;
+      rec.put(zero_rec, z, z);
+    }
+    if (live) element_records_volume<T, P>(u, tb, rec, el, R);
+    if (cur.hk.x >= 0) halo_face_record<T, P>(cur.hv, cur.hk.y, tb, rec, 4 * kBlock + el);
+    const T *U = uin + (size_t)cur.sd * (size_t)stride * NP;
+    for (int h = el + kBlock; h < cur.hcnt; h += kBlock) {  // chunks with > kBlock halo entries
+      const int2 q = __ldg(halo + (size_t)cur.chunk * kHaloCap + h);
+      T v[NP];
+      load_elem<T, NP>(U + (size_t)q.x * NP, v);
+      halo_face_record<T, P>(v, q.y, tb, rec, 4 * kBlock + h);
+    }
+    __syncthreads();
+    if (live) {
+      const int lq[4] = {cur.l4.x, cur.l4.y, cur.l4.z, cur.l4.w};
+      element_flux<T, P, FULL>(u, R, lq, el, zero_rec, rec, tb, c);
+    }
+    if constexpr (HAS_U0) ok = mbar_wait(bar1, ph, ca.limit);
+    if (live && ok) {
+      T o[NP];
+      if constexpr (HAS_U0) St::read(so, el, o);
+      const uint32_t h = SROUND ? element_key<T>(a0 + el - __ldg(grange + cur.ci.y).x, NP,
+                                                 cur.sd, u)
+                                : 0u;
+      element_update<T, P, HAS_U0, SROUND>(u, R, o, cur.gam, h, c);
+      St::write(so, el, o);
+    }
+    const bool store_tma = ca.store_tma && cnt == kBlock;  // a full chunk: one tiled store
+    if (store_tma) fence_proxy_async_smem();
+    if (__syncthreads_or(!ok)) {  // the u0 wait gave up; the next u copy may be in flight
+      if (more) mbar_wait(bar0, ph ^ 1u, ca.limit);
+      if (el == 0) {
+        asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+        atomicExch(ca.err, 1);
+      }
+      return;
+    }
+    if (store_tma) {
+      if (el == 0) {
+        asm volatile(
+            "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(
+                reinterpret_cast<uint64_t>(&tm_out)),
+            "r"(0), "r"((int)((long long)cur.sd * stride + a0)), "r"(smem_u32(so))
+            : "memory");
+        asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+      }
+    } else {  // coalesced 16-byte stores of a partial chunk
+      char *go = reinterpret_cast<char *>(out + (size_t)cur.sd * (size_t)stride * NP +
+                                          (size_t)a0 * NP);
+      const int np16 = St::pieces(cnt);
+      for (int j = el; j < np16; j += kBlock)
+        *reinterpret_cast<float4 *>(go + 16 * (size_t)j) =
+            *reinterpret_cast<const float4 *>(reinterpret_cast<unsigned char *>(so) +
+                                              16 * St::piece_dst(j));
+    }
+    if constexpr (HAS_U0) {
+      // the next u0 goes into the other buffer, whose last reader was the
+      // previous item's result store: wait until every store but this item's
+      // own has been read (all of them after a partial chunk, which committed
+      // none); a partial chunk's threads read their buffer one item earlier,
+      // ordered by this item's fences and barriers
+      if (el == 0 && more) {
+        if (store_tma) asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
+        else asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+        mbar_expect_tx(bar1, bytes);
+        tma_load_rows(smem_u32(so_raw + (ph ? 0 : CB)), &tm_u0, item_row(next), bar1);
+      }
+    }
+    if (more) cur = nxt;
+  }
+  // shared memory must outlive the reads of the last result stores
+  if (el == 0) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
 }
 
 template <typename T, int P>
@@ -865,6 +1206,49 @@ cudaError_t launch_stage_p(const T *u, const T *u0, T *out, const Geometry &geo,
   const CUtensorMap &mu = ca.use_tma ? *cp.map_u : zero_map;
   const CUtensorMap &mu0 = ca.use_tma && u0 ? *cp.map_u0 : zero_map;
   const CUtensorMap &mo = ca.store_tma ? *cp.map_out : zero_map;
+  if constexpr (kHasPipe<T, P>) {
+    if (cp.pipe_blocks > 0 && ca.store_tma) {
+      const int psmem = pipe_smem_bytes<T, P>(geo.halo_max);
+      static int pipe_attr = 0;
+      if (psmem > pipe_attr) {
+        cudaError_t e = cudaSuccess;
+        auto set = [&](auto kern) {
+          if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem);
+        };
+        set(k_stage_pipe<T, P, true, false, false>);
+        set(k_stage_pipe<T, P, false, false, false>);
+        set(k_stage_pipe<T, P, true, false, true>);
+        set(k_stage_pipe<T, P, false, false, true>);
+        set(k_stage_pipe<T, P, true, true, false>);
+        set(k_stage_pipe<T, P, false, true, false>);
+        set(k_stage_pipe<T, P, true, true, true>);
+        set(k_stage_pipe<T, P, false, true, true>);
+        if (e != cudaSuccess) return e;
+        pipe_attr = psmem;
+      }
+      int dev = 0, nsm = 0;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess) return e;
+      const long long items = nch * (long long)m;
+      const long long G = std::min<long long>(items, (long long)nsm * cp.pipe_blocks);
+      auto gop = [&](auto kern) {
+        kern<<<(unsigned)G, kBlock, psmem, s>>>(u, u0, out, geo.d_loc, geo.d_halo, geo.d_halo_cnt,
+                                                geo.d_chunk, geo.d_grange, gscale, stride, nrec,
+                                                sel.list, sel.adv, tb, c, mu, mu0, mo, ca, items,
+                                                (int)nch);
+      };
+      if (c.sround) {
+        if (u0) full ? gop(k_stage_pipe<T, P, true, true, true>) : gop(k_stage_pipe<T, P, true, true, false>);
+        else full ? gop(k_stage_pipe<T, P, false, true, true>) : gop(k_stage_pipe<T, P, false, true, false>);
+      } else {
+        if (u0) full ? gop(k_stage_pipe<T, P, true, false, true>) : gop(k_stage_pipe<T, P, true, false, false>);
+        else full ? gop(k_stage_pipe<T, P, false, false, true>) : gop(k_stage_pipe<T, P, false, false, false>);
+      }
+      return cudaGetLastError();
+    }
+  }
   auto go = [&](auto kern) {
     kern<<<grid, kBlock, smem, s>>>(u, u0, out, geo.d_loc, geo.d_halo, geo.d_halo_cnt,
                                     geo.d_chunk, geo.d_grange, gscale, stride, nrec, sel.list,
@@ -878,6 +1262,34 @@ cudaError_t launch_stage_p(const T *u, const T *u0, T *out, const Geometry &geo,
     else full ? go(k_stage<T, P, false, false, true>) : go(k_stage<T, P, false, false, false>);
   }
   return cudaGetLastError();
+}
+
+// Blocks of the persistent kernel that fit on one SM (shared memory and
+// registers), 0 where the variant does not exist.
+template <typename T, int P>
+int stage_pipe_max_blocks_p(const Geometry &geo) {
+  if constexpr (!kHasPipe<T, P>) {
+    return 0;
+  } else {
+    const int psmem = pipe_smem_bytes<T, P>(geo.halo_max);
+    if (cudaFuncSetAttribute(k_stage_pipe<T, P, true, true, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, psmem) != cudaSuccess)
+      return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage_pipe<T, P, true, true, false>,
+                                                      kBlock, psmem) != cudaSuccess)
+      return 0;
+    return nb;
+  }
+}
+
+template <typename T>
+int stage_pipe_max_blocks_any(int p, const Geometry &geo) {
+  switch (p) {
+    case 1: return stage_pipe_max_blocks_p<T, 1>(geo);
+    case 3: return stage_pipe_max_blocks_p<T, 3>(geo);
+    default: return 0;
+  }
 }
 
 template <typename T>
