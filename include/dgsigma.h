@@ -277,23 +277,25 @@ int dg_debug_copies(dg_ctx *ctx, int mode, unsigned long long *tensor_copies);
 
 /* Launch shape of the FP32 stage kernel (no counterpart in the paper: how the
  * element updates of Sec. 3.3, one independent update per element, are
- * mapped onto the GPU).  blocks_per_sm = 0: one block of 256 threads per
- * chunk of 256 elements and density (all chunks in one launch per RK
- * stage); k >= 1: a persistent launch of k blocks per SM that walk the
- * (density, chunk) work items of every geometry of the context and copy the
- * next item's chunks into shared memory behind the current item's work
- * (clamped to the blocks that fit; FP32 at p = 1 and 3 with tensor copies,
- * every other variant keeps the one-block-per-chunk launch); -1 (the
- * default): tuned -- before the first steps after a change of the densities
- * or geometry, each shape runs stage 1 with dt = 0 (which leaves the
- * state's values unchanged) four times on the context's stream and the
- * fastest is kept (under stream capture, where nothing can be timed, the
- * one-block-per-chunk launch).  Every shape gives the same bits.  Errors: DG_EINVAL
- * (blocks_per_sm < -1 or > 64). */
+ * mapped onto the GPU).  DG_LAUNCH_CHUNK (0): one block of 256 threads per
+ * chunk of 256 elements and density, one thread per element (all chunks in
+ * one launch per RK stage); k >= 1: a persistent launch of k blocks per SM
+ * that walk the (density, chunk) work items of every geometry of the
+ * context and copy the next item's chunks into shared memory behind the
+ * current item's work (clamped to the blocks that fit; FP32 at p = 1 and 3
+ * with tensor copies; every other variant keeps DG_LAUNCH_CHUNK);
+ * DG_LAUNCH_TUNED (-1, the default): before the first steps after a change
+ * of the densities or geometry, each shape runs stage 1 with dt = 0 (which
+ * leaves the state's values unchanged) four times on the context's stream
+ * and the fastest is kept (under stream capture, where nothing can be
+ * timed, DG_LAUNCH_CHUNK).  Every shape gives the same bits.  Errors:
+ * DG_EINVAL (blocks_per_sm < -1 or > 64). */
+#define DG_LAUNCH_TUNED (-1)
+#define DG_LAUNCH_CHUNK 0
 int dg_set_launch(dg_ctx *ctx, int blocks_per_sm);
 
-/* The launch shape the last steps used (0 or blocks per SM, see
- * dg_set_launch). */
+/* The launch shape the last steps used (DG_LAUNCH_CHUNK or blocks per SM,
+ * see dg_set_launch). */
 int dg_get_launch(dg_ctx *ctx, int *blocks_per_sm);
 
 /* Where the element contractions of the FP32 stage at p = 5 run.  Sec. 3.1

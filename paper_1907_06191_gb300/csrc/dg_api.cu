@@ -214,10 +214,15 @@ int resolve_launch(dg_ctx *ctx) {
   const bool fp32 = c.cfg.precision == DG_FP32 && !c.triangles() && c.tmap_ok && c.copy_mode != 1;
   const int maxb = fp32 ? stage_pipe_max_blocks(c.cfg.precision, c.cfg.p, c.geo) : 0;
   const bool tc_ok = fp32 && c.cfg.p == 5 && stage_tc_max_blocks(c.geo) >= 1;
+  std::vector<int> shapes{0};  // the launch shapes this context has
+  for (int k = 1; k <= maxb; ++k) shapes.push_back(k);
   int want = 0, want_tc = 0;
-  const bool fixed = c.launch_req >= 0 || maxb < 1;
+  const bool fixed = c.launch_req != -1 || shapes.size() == 1;
   const bool fixed_tc = c.contraction_req >= 0 || !tc_ok;
-  if (fixed) want = maxb < 1 ? 0 : std::min(c.launch_req, maxb);
+  if (fixed) {
+    if (c.launch_req >= 1) want = std::min(c.launch_req, maxb);  // 0 without a persistent kernel
+    else want = 0;
+  }
   if (fixed_tc) want_tc = tc_ok && c.contraction_req == 1 ? 1 : 0;
   if (!(fixed && fixed_tc)) {
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -226,15 +231,17 @@ int resolve_launch(dg_ctx *ctx) {
       // a test hook is active or nothing can be timed: the plain launch
       if (!fixed) want = 0;
       if (!fixed_tc) want_tc = 0;
-    } else if (c.tuned_key[0] == c.m && c.tuned_key[1] == c.geo.n_pad && c.tuned_blocks >= 0) {
-      if (!fixed) want = std::min(c.tuned_blocks, maxb);
+    } else if (c.tuned_key[0] == c.m && c.tuned_key[1] == c.geo.n_pad && c.tuned_blocks != -1) {
+      if (!fixed) want = c.tuned_blocks;
       if (!fixed_tc) want_tc = c.tuned_tc;
     } else {
       TraceRange trace("launch tuning");
-      std::vector<std::pair<int, int>> cand;  // (blocks per SM, tensor cores)
-      for (int k = fixed ? want : 0; k <= (fixed ? want : maxb); ++k)
+      std::vector<std::pair<int, int>> cand;  // (launch shape, tensor cores)
+      for (const int k : shapes) {
+        if (fixed && k != want) continue;
         for (int t = fixed_tc ? want_tc : 0; t <= (fixed_tc ? want_tc : 1); ++t)
-          if (t == 0 || k == 0) cand.push_back({k, t});  // no persistent tensor-core kernel
+          if (t == 0 || k == 0) cand.push_back({k, t});  // tensor cores: one block per chunk
+      }
       cudaEvent_t e0 = nullptr, e1 = nullptr;
       CK(cudaEventCreate(&e0), "tuning event");
       cudaError_t e = cudaEventCreate(&e1);

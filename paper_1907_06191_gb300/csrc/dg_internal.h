@@ -291,8 +291,9 @@ struct StageCopies {
   int use_tma = 0, extra_tx = 0, limit = 1 << 22;
   int *err = nullptr;
   unsigned long long *counter = nullptr;
-  // persistent launch (k_stage_pipe) with this many blocks per SM where the
-  // variant has one (FP32 p = 1, 3 with tensor copies); 0: one block per chunk
+  // launch shape: 0 one block per chunk, one thread per element (k_stage);
+  // k >= 1 persistent (k_stage_pipe, FP32 p = 1, 3 with tensor copies) with
+  // k blocks per SM
   int pipe_blocks = 0;
   // FP32 p = 5: element contractions on the tensor cores (k_stage_tc)
   int tensor_core = 0;

@@ -127,3 +127,4 @@ def test_bad_launch_shape():
             with pytest.raises(dg.DgError) as ei:
                 s.set_launch(bad)
             assert ei.value.code == dg.DG_EINVAL
+
