@@ -281,29 +281,38 @@ def sigma_solve(dg, w, s, dev, args, rnd, r_factor=10.0):
                     "path vs the plain FP64 GPU path on the same densities"}
 
 
+def _batch_member(args_tuple):
+    seed, delta = args_tuple
+    return dginputs.workload_batch_member(seed, delta=delta)
+
+
 def run_batch(args):
     """Uneven-geometry batch: seeded geometries with 64..256 elements per cell
     side (h = 0.156 um), p in {2, 3, 4}, packing 0.40-0.75, Gamma shape
-    1.5-3.0, 16 densities each, windows sized for Delta = 20 ms.  Geometries
-    of equal p share one context (one launch per RK stage for all of them);
-    geometries are added in seed order while the FP32 state stays under
-    --batch-gb.  The same geometries are then run one context at a time."""
+    1.5-3.0, 16 densities each, windows sized for Delta = --batch-delta ms
+    (1 ms: 512 geometries, ~130 GB of FP32 state; the 20 ms windows of the
+    full batch would need ~700 GB).  Geometries of equal p share one context
+    (one launch per RK stage for all of them); geometries are added in seed
+    order while the FP32 state stays under --batch-gb.  The same geometries
+    are then run one context each (one launch per stage and geometry)."""
+    import multiprocessing as mp
+    # the geometries are drawn on the host cores before CUDA starts
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        cands = pool.map(_batch_member, [(sd, args.batch_delta) for sd in range(args.batch_geometries)])
     import torch
     import paper_1907_06191_gb300 as dg
     from paper_1907_06191_gb300 import _build
     _build.build()
     torch.cuda.set_device(0)
     budget = args.batch_gb * 2 ** 30
-    members, used, seed = [], 0.0, 0
-    while seed < args.batch_geometries:
-        w = dginputs.workload_batch_member(seed)
+    members, used = [], 0.0
+    for w in cands:
         npe = (w.p + 1) ** 2
         est = w.n_window ** 2 * (1 - w.disks.packing) * npe * 16 * 4 * 3
         if used + est > budget:
             break
         members.append(w)
         used += est
-        seed += 1
     groups = {}
     for w in members:
         groups.setdefault(w.p, []).append(w)
@@ -312,6 +321,7 @@ def run_batch(args):
     for p, ws in sorted(groups.items()):
         s = dg.DGSolver(p=p, precision=dg.DG_FP32, D=2.0, sigma0=0.2, device=0)
         s.set_stream(stream.cuda_stream)
+        s.set_launch(args.launch)
         s.set_geometry_batch([(w.disks.cx, w.disks.cy, w.disks.r) for w in ws],
                              [w.L for w in ws], [w.n_cell for w in ws], [w.tiles for w in ws])
         s.set_sources(np.stack([w.sources for w in ws]))
@@ -329,6 +339,7 @@ def run_batch(args):
     for _ in range(args.warmup):
         step_all()
     torch.cuda.synchronize()
+    launches = {str(inf.p): s.get_launch() for s, _, inf in ctxs}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clk:
         e0.record(stream)
@@ -338,6 +349,7 @@ def run_batch(args):
         e1.synchronize()
     ms = e0.elapsed_time(e1)
     batched = dof * R * args.steps / (ms * 1e-3)
+    dt_of = dict((inf.p, dt) for s, dt, inf in ctxs)
     for s, _, _ in ctxs:
         s.close()
     # the same geometries one context each
@@ -345,12 +357,14 @@ def run_batch(args):
     for w in members:
         s = dg.DGSolver(p=w.p, precision=dg.DG_FP32, D=2.0, sigma0=0.2, device=0)
         s.set_stream(stream.cuda_stream)
+        s.set_launch(args.launch)
         s.set_geometry_disks(w.disks.cx, w.disks.cy, w.disks.r, w.L, w.n_cell, w.tiles)
         s.set_sources(w.sources)
-        singles.append((s, dict((p, dt) for (c, dt, inf), p in zip(ctxs, sorted(groups)))[w.p]))
-    for s, dt in singles:
-        s.step(R, dt)
-        s.covariance()
+        singles.append((s, dt_of[w.p]))
+    for _ in range(max(1, args.warmup)):
+        for s, dt in singles:
+            s.step(R, dt)
+            s.covariance()
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(args.steps):
@@ -363,17 +377,23 @@ def run_batch(args):
     ms1 = e0.elapsed_time(e1)
     for s, _ in singles:
         s.close()
+    unbatched = dof * R * args.steps / (ms1 * 1e-3)
     line = {"metric": METRIC, "value": batched, "unit": "DoF-steps/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": "batch_uneven_p234", "geometries": len(members),
                        "geometries_requested": args.batch_geometries,
+                       "delta_ms": args.batch_delta,
                        "per_p": {str(p): len(ws) for p, ws in groups.items()},
                        "densities_per_geometry": 16, "rk_steps_per_bench_step": R,
-                       "state_gb": used / 2 ** 30,
+                       "dof": dof, "state_gb": used / 2 ** 30,
+                       "window_elements_min_max": [min(w.n_window for w in members) ** 2,
+                                                   max(w.n_window for w in members) ** 2],
+                       "launch_blocks_per_sm": launches,
                        "l2": "state larger than L2, no flush"},
-            "unbatched_value": dof * R * args.steps / (ms1 * 1e-3),
+            "unbatched_value": unbatched, "batched_over_unbatched": batched / unbatched,
+            "unbatched_ms_per_step": ms1 / args.steps,
             "gpu_launches": args.steps * len(ctxs) * (3 * R + 3),
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
@@ -521,7 +541,9 @@ def main():
     ap.add_argument("--sg-epochs", type=int, default=100)
     ap.add_argument("--sg-sources", type=int, default=64)
     ap.add_argument("--batch-geometries", type=int, default=512)
-    ap.add_argument("--batch-gb", type=float, default=60.0)
+    ap.add_argument("--batch-gb", type=float, default=200.0)
+    ap.add_argument("--batch-delta", type=float, default=1.0,
+                    help="diffusion time (ms) the batch windows are sized for")
     args = ap.parse_args()
     world, rank, local = _dist()
     if args.workload == "batch" and args.impl == "ours":

@@ -256,10 +256,11 @@ def workload_cell40(seed: int = 0, m: int = 64, r_factor: float = 6.0) -> Worklo
                      min_gap=0.0, r_factor=r_factor)
 
 
-def workload_batch_member(seed: int, m: int = 16) -> Workload:
+def workload_batch_member(seed: int, m: int = 16, delta: float = 20.0) -> Workload:
     """One geometry of the uneven batch: h=0.15625 um, 64..256 elements per
     cell side, p in {2,3,4}, packing 0.40-0.75, Gamma shape 1.5-3.0 with
-    scale 0.5 um, 16 start points, Delta=20 ms."""
+    scale 0.5 um, 16 start points, Delta = 20 ms (the window is sized for
+    ``delta``; the geometry itself does not depend on it)."""
     rng = np.random.default_rng(seed + 15485863)
     n_cell = int(rng.integers(64, 257))
     p = int(rng.choice([2, 3, 4]))
@@ -267,7 +268,7 @@ def workload_batch_member(seed: int, m: int = 16) -> Workload:
     shape = float(rng.uniform(1.5, 3.0))
     h = 40.0 / 256
     return _workload(f"batch{seed}", seed, p, n_cell * h, n_cell, 2.0, 0.2,
-                     [20.0], shape, 0.5, m, packing=packing)
+                     [float(delta)], shape, 0.5, m, packing=packing)
 
 
 def workload_surrogate_member(seed: int, m: int = 16) -> Workload:

@@ -270,9 +270,11 @@ int dg_set_growing_window(dg_ctx *ctx, double r_factor);
  * dg_propagate_to return DG_ETIMEOUT (the state is then undefined and the
  * context usable again after dg_set_sources).  mode 0: that default; 1:
  * per-thread cp.async copies only; 2: the barriers also wait for 16 bytes no
- * copy delivers, so every wait runs out (after ~4k polls).  Returns in
+ * copy delivers, so every wait runs out (after ~4k polls); 3: every grid
+ * barrier of the DG_LAUNCH_STEP launch waits for one more block than the
+ * launch has, so its wait runs out (after ~4k polls).  Returns in
  * *tensor_copies (may be NULL) the chunk copies made by the tensor path since
- * the last call.  Errors: DG_EINVAL (mode outside 0..2). */
+ * the last call.  Errors: DG_EINVAL (mode outside 0..3). */
 int dg_debug_copies(dg_ctx *ctx, int mode, unsigned long long *tensor_copies);
 
 /* Launch shape of the FP32 stage kernel (no counterpart in the paper: how the
@@ -284,14 +286,21 @@ int dg_debug_copies(dg_ctx *ctx, int mode, unsigned long long *tensor_copies);
  * context and copy the next item's chunks into shared memory behind the
  * current item's work (clamped to the blocks that fit; FP32 at p = 1 and 3
  * with tensor copies; every other variant keeps DG_LAUNCH_CHUNK);
+ * DG_LAUNCH_STEP (-2): all three stages of an SSP-RK3 step in one
+ * cooperative launch, the blocks meeting at a grid-wide barrier between
+ * stages (FP32 at p = 1, 3, 5 with tensor copies; pays where launches are
+ * short); every barrier wait is bounded and one that runs out ends the
+ * launch with DG_ETIMEOUT at the next synchronising call;
  * DG_LAUNCH_TUNED (-1, the default): before the first steps after a change
- * of the densities or geometry, each shape runs stage 1 with dt = 0 (which
- * leaves the state's values unchanged) four times on the context's stream
- * and the fastest is kept (under stream capture, where nothing can be
- * timed, DG_LAUNCH_CHUNK).  Every shape gives the same bits.  Errors:
- * DG_EINVAL (blocks_per_sm < -1 or > 64). */
+ * of the densities or geometry, each shape runs stage 1 (DG_LAUNCH_STEP: a
+ * whole step) with dt = 0, which leaves the state's values unchanged, four
+ * times on the context's stream and the fastest per stage is kept (under
+ * stream capture, where nothing can be timed, DG_LAUNCH_CHUNK).  Every
+ * shape gives the same bits.  Errors: DG_EINVAL (blocks_per_sm < -2 or
+ * > 64). */
 #define DG_LAUNCH_TUNED (-1)
 #define DG_LAUNCH_CHUNK 0
+#define DG_LAUNCH_STEP (-2)
 int dg_set_launch(dg_ctx *ctx, int blocks_per_sm);
 
 /* The launch shape the last steps used (DG_LAUNCH_CHUNK or blocks per SM,

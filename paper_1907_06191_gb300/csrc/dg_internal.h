@@ -218,7 +218,8 @@ struct Ctx {
   CUtensorMap tmap[3];
   bool tmap_ok = false;
   int copy_mode = 0;              // 0 tensor copies where possible, 1 cp.async only,
-                                  // 2 test hook: barriers that never complete
+                                  // 2 test hook: barriers that never complete,
+                                  // 3 test hook: grid barriers that never complete
   // Launch shape of the FP32 stage kernel: launch_req -1 = tuned (the
   // candidates are timed before the first steps of a set of densities),
   // 0 = one block per chunk, k >= 1 = persistent with k blocks per SM.
@@ -235,6 +236,7 @@ struct Ctx {
   int tuned_tc = 0;
   long long tuned_key[2] = {-1, -1};
   int *d_err = nullptr;           // a bounded device wait gave up (and the copy counter)
+  unsigned *d_grid = nullptr;     // arrival counter of the one-launch-per-step grid barriers
   unsigned long long *d_tma = nullptr;
   size_t part_elems = 0;
 
@@ -309,6 +311,17 @@ cudaError_t launch_stage_tc_f32(const float *u, const float *u0, float *out, con
                                 const StageCopies &cp);
 int stage_tc_max_blocks(const Geometry &geo);
 cudaError_t stage_tc_prepare(const Gll &g, cudaStream_t s);
+// One SSP-RK3 step in one cooperative launch with bounded grid barriers
+// between the stages (FP32, p = 1, 3, 5, tensor copies); c[k] the stage
+// coefficients; grid_extra > 0 (test hook) makes every barrier wait for
+// arrivals no block makes.  cudaErrorNotSupported where it does not apply.
+cudaError_t launch_rk3_grid_f32(int p, float *U0, float *U1, float *U2, const Geometry &geo,
+                                long long stride, int m, const Gll &g,
+                                const StageCoef<float> (&c)[3], cudaStream_t s,
+                                const ChunkSel &sel, const CUtensorMap *maps, int *err,
+                                unsigned long long *counter, unsigned *grid_count,
+                                int extra_tx, int limit, int grid_extra, int grid_limit);
+constexpr int kLaunchStep = -2;  // one cooperative launch per RK step (DG_LAUNCH_STEP)
 // One stage over all m densities: out = u0 + beta (u - u0) + gamma R(u).
 cudaError_t launch_stage_f64(int p, const double *u, const double *u0, double *out,
                              const Geometry &geo, long long stride, int m,

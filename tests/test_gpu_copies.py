@@ -92,4 +92,4 @@ def test_wait_that_runs_out_reports_etimeout():
 def test_bad_copy_mode():
     with dg.DGSolver(p=3, device=0) as s:
         with pytest.raises(dg.DgError):
-            s.debug_copies(3)
+            s.debug_copies(4)

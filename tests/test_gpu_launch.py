@@ -123,8 +123,70 @@ def test_persistent_wait_that_runs_out_reports_etimeout():
 
 def test_bad_launch_shape():
     with dg.DGSolver(p=3, device=0) as s:
-        for bad in (-2, 65):
+        for bad in (-3, 65):
             with pytest.raises(dg.DgError) as ei:
                 s.set_launch(bad)
             assert ei.value.code == dg.DG_EINVAL
 
+
+
+STEP = -2  # DG_LAUNCH_STEP: the three stages of a step in one cooperative launch
+
+
+@pytest.mark.parametrize("p", [1, 3, 5])
+@pytest.mark.parametrize("rnd,eta", [(dg.DG_ROUND_STOCHASTIC, 0.0), (dg.DG_ROUND_NEAREST, 1.0)])
+def test_one_launch_per_step_gives_the_same_bits(p, rnd, eta):
+    ref, sref, _ = _run(p, 0, rnd, eta)
+    got, sig, used = _run(p, STEP, rnd, eta)
+    assert used == STEP
+    assert np.array_equal(got, ref) and np.array_equal(sig, sref)
+
+
+def test_one_launch_per_step_with_the_growing_window_and_a_batch():
+    ref, _, _ = _run(3, 0, grow=3.0)
+    got, _, used = _run(3, STEP, grow=3.0)
+    assert used == STEP and np.array_equal(got, ref)
+    ws = [dginputs.gamma_disks(s, 4.0, 2.0, 0.15, n=6 + s, min_gap=0.05) for s in range(3)]
+    src = np.stack([dginputs.sample_sources(10 + s, d, 4, 0.0, 4.0, margin=0.25)
+                    for s, d in enumerate(ws)])
+    out = []
+    for k in (0, STEP):
+        with dg.DGSolver(p=3, precision=dg.DG_FP32, D=1.0, sigma0=0.3, device=0) as s:
+            s.set_geometry_batch([(d.cx, d.cy, d.r) for d in ws], [4.0, 4.0, 4.0], [16, 20, 12],
+                                 [3, 3, 3])
+            s.set_launch(k)
+            s.set_sources(src)
+            dt, _ = s.query_dt()
+            s.step(40, dt)
+            out.append(s.covariance_batch()[0])
+    assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("mode", [2, 3])
+def test_grid_barrier_or_copy_wait_that_runs_out_reports_etimeout(mode):
+    """mode 3: every grid barrier waits for one block more than the launch
+    has (a count nothing reaches); mode 2: the chunk copies' barriers wait
+    for bytes no copy delivers.  Both bounded waits end in DG_ETIMEOUT and
+    the context then reproduces a fresh run bit for bit."""
+    d, src = _case()
+    with dg.DGSolver(p=3, precision=dg.DG_FP32, D=1.0, sigma0=0.3, device=0) as s:
+        s.set_geometry_disks(d.cx, d.cy, d.r, 4.0, 16, 1)
+        s.set_launch(STEP)
+        s.set_sources(src)
+        dt, _ = s.query_dt()
+        s.debug_copies(mode)
+        s.step(2, dt)
+        assert s.get_launch() == STEP
+        with pytest.raises(dg.DgError) as ei:
+            s.covariance()
+        assert ei.value.code == dg.DG_ETIMEOUT
+        s.debug_copies(0)
+        s.set_sources(src)
+        s.step(10, dt)
+        got = s.get_nodes()
+    with dg.DGSolver(p=3, precision=dg.DG_FP32, D=1.0, sigma0=0.3, device=0) as f:
+        f.set_geometry_disks(d.cx, d.cy, d.r, 4.0, 16, 1)
+        f.set_launch(0)
+        f.set_sources(src)
+        f.step(10, dt)
+        assert np.array_equal(f.get_nodes(), got)
