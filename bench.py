@@ -444,15 +444,7 @@ def run_surrogate(args):
     pred = pe.cpu().numpy()
     rel = np.linalg.norm(pred - tgt_e, axis=1) / np.linalg.norm(tgt_e, axis=1)
     # reference point: least squares on the packing fraction and log(D Delta)
-    def feats(ws):
-        rows = []
-        for w in ws:
-            for d in w.deltas:
-                ph, lt = w.disks.packing, np.log(w.D * d)
-                rows.append([1.0, ph, ph * ph, lt, ph * lt, lt * lt])
-        return np.array(rows)
-    coef, *_ = np.linalg.lstsq(feats(ws_tr), tgt.astype(np.float64), rcond=None)
-    base = feats(ws_te) @ coef
+    base = sgm.packing_fit(ws_tr, tgt, ws_te)
     rel_base = np.linalg.norm(base - tgt_e, axis=1) / np.linalg.norm(tgt_e, axis=1)
     # batch-4096 inference throughput (inputs resident)
     B = 4096
@@ -536,10 +528,11 @@ def main():
                     help="after the timed steps, solve every density to each of the workload's "
                          "diffusion times up to this Delta (ms) and report Sigma and the time")
     ap.add_argument("--workload", default="cell40", choices=["cell40", "batch", "p5", "surrogate"])
-    ap.add_argument("--sg-train", type=int, default=512)
-    ap.add_argument("--sg-test", type=int, default=128)
-    ap.add_argument("--sg-epochs", type=int, default=100)
-    ap.add_argument("--sg-sources", type=int, default=64)
+    ap.add_argument("--sg-train", type=int, default=4000,
+                    help="training cells (x 5 diffusion times = DG samples)")
+    ap.add_argument("--sg-test", type=int, default=1000, help="held-out cells")
+    ap.add_argument("--sg-epochs", type=int, default=30)
+    ap.add_argument("--sg-sources", type=int, default=16)
     ap.add_argument("--batch-geometries", type=int, default=512)
     ap.add_argument("--batch-gb", type=float, default=200.0)
     ap.add_argument("--batch-delta", type=float, default=1.0,

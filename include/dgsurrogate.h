@@ -8,21 +8,28 @@
  * the network is trained on Sigma values that the DG solver of dgsigma.h
  * produces, and the DG solve stays its fallback and the reference for its error.
  *
- * Network (NCHW): input 1 x 128 x 128; four blocks of 3x3 convolution (zero
- * padding) + ReLU + 2x2 average pooling with 16, 32, 64, 64 channels; global
- * average -> 64 features, concatenated with c = (log(D Delta / um^2), D);
- * dense 66 -> 128 + ReLU; dense 128 -> 3.  Weights and activations in BF16,
- * all sums accumulated in FP32; FP32 master weights, gradients and Adam.
+ * Network: input 1 x 128 x 128; four blocks of 3x3 convolution (zero
+ * padding) + ReLU + 2x2 average pooling with 48, 96, 192, 384 channels;
+ * global average -> 384 features, concatenated with c = (log(D Delta /
+ * um^2), D); dense 386 -> 256 + ReLU; dense 256 -> 3 (971,907 parameters).
+ * Weights and activations in BF16 (channels-last on the device), all sums
+ * accumulated in FP32; FP32 master weights, gradients and Adam.  The
+ * convolutions and their input and weight gradients run as implicit GEMMs
+ * on the tensor cores (tcgen05.mma, BF16 operands, FP32 accumulators in
+ * tensor memory); the gradient of a convolution's output enters them
+ * rounded to BF16.
  *
  * Parameter vector (FP32, sg_param_count values), in this order: for each
  * convolution l = 1..4 its weights [Cout][Cin][3][3] then biases [Cout];
- * dense 1 weights [128][66], biases [128]; dense 2 weights [3][128],
+ * dense 1 weights [256][386], biases [256]; dense 2 weights [3][256],
  * biases [3].
  *
  * Batches are device pointers: occ [B][128][128] bytes, cond [B][2] FP32,
  * target/out [B][3] FP32, 1 <= B <= max_batch.  Calls synchronise the
  * network's own stream before returning.  Status codes are those of
- * dgsigma.h.
+ * dgsigma.h; DG_ETIMEOUT if a tensor-core kernel's bounded wait for its MMAs
+ * ran out (the network's outputs are then undefined; the network stays
+ * usable).
  */
 #ifndef DGSURROGATE_H
 #define DGSURROGATE_H

@@ -10,15 +10,18 @@ weights and activations in BF16 and accumulates in FP32; this reference
 rounds weights and activations to BF16 at the same points (round to nearest
 even) and accumulates in FP64, so the two agree to FP32 accumulation error
 except where a BF16 rounding of an intermediate value falls the other way.
+The gradient of each convolution's output is rounded to BF16 before it
+enters the weight, bias and input gradients (the library's tensor cores take
+BF16 operands).
 """
 from __future__ import annotations
 
 import numpy as np
 
-CH = (1, 16, 32, 64, 64)
+CH = (1, 48, 96, 192, 384)
 RES = 128
-COND, HIDDEN, OUT = 2, 128, 3
-FEAT = 64 + COND
+COND, HIDDEN, OUT = 2, 256, 3
+FEAT = CH[-1] + COND
 
 
 ROUND_BF16 = True  # False turns the BF16 emulation off (smooth loss for finite differences)
@@ -131,10 +134,10 @@ def loss_and_grad(params, occ, cond, target):
     df = dh @ bf16(p["f1_w"])
     x4 = c["x"][4]
     HW = x4.shape[2] * x4.shape[3]
-    dx = np.broadcast_to(df[:, :64, None, None] / HW, x4.shape).copy()
+    dx = np.broadcast_to(df[:, :CH[-1], None, None] / HW, x4.shape).copy()
     for l in range(3, -1, -1):
         a = c["a"][l]
-        dz = 0.25 * np.repeat(np.repeat(dx, 2, axis=2), 2, axis=3) * (a > 0)
+        dz = bf16(0.25 * np.repeat(np.repeat(dx, 2, axis=2), 2, axis=3) * (a > 0))
         g[f"conv{l}_w"] = _conv_w(dz, c["x"][l])
         g[f"conv{l}_b"] = dz.sum(axis=(0, 2, 3))
         if l > 0:

@@ -26,10 +26,11 @@ def conditioning(D: float, delta: float) -> np.ndarray:
     return np.array([math.log(D * delta), D], dtype=np.float32)
 
 
-def dg_sigma(workloads, device: int = 0, chunk: int = 64):
+def dg_sigma(workloads, device: int = 0, chunk: int = 256, r_factor: float = 8.0):
     """Sigma of every workload at each of its diffusion times, from batched
-    FP32 DG solves (all workloads share the element order p, cell and
-    window).  Returns (sigma [n, n_delta, 3], seconds)."""
+    FP32 DG solves on the growing window of radius factor r_factor (all
+    workloads share the element order p, cell and window).  Returns
+    (sigma [n, n_delta, 3], seconds)."""
     out = np.zeros((len(workloads), len(workloads[0].deltas), 3))
     t0 = time.perf_counter()
     for c0 in range(0, len(workloads), chunk):
@@ -38,6 +39,7 @@ def dg_sigma(workloads, device: int = 0, chunk: int = 64):
         with DGSolver(p=w0.p, precision=DG_FP32, D=w0.D, sigma0=w0.sigma0, device=device) as s:
             s.set_geometry_batch([(w.disks.cx, w.disks.cy, w.disks.r) for w in ws],
                                  [w.L for w in ws], [w.n_cell for w in ws], [w.tiles for w in ws])
+            s.set_growing_window(r_factor)
             s.set_sources(np.stack([w.sources for w in ws]))
             for k, d in enumerate(w0.deltas):
                 s.propagate_to(d)
@@ -103,6 +105,25 @@ def train(net: Surrogate, occ, cond, tgt, epochs: int = 100, batch: int = 128,
             cnt += 1
         hist.append(tot / max(cnt, 1))
     return hist
+
+
+def packing_features(workloads):
+    """(1, phi, phi^2, tau, phi tau, tau^2) per (workload, Delta): phi the
+    packing fraction, tau = log(D Delta)."""
+    rows = []
+    for w in workloads:
+        for d in w.deltas:
+            ph, lt = w.disks.packing, math.log(w.D * d)
+            rows.append([1.0, ph, ph * ph, lt, ph * lt, lt * lt])
+    return np.array(rows)
+
+
+def packing_fit(ws_train, tgt_train, ws_eval):
+    """What a user has without the network: least squares of the targets on
+    the packing fraction and log(D Delta), evaluated on ws_eval."""
+    coef, *_ = np.linalg.lstsq(packing_features(ws_train), np.asarray(tgt_train, np.float64),
+                               rcond=None)
+    return packing_features(ws_eval) @ coef
 
 
 class SigmaService:

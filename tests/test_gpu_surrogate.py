@@ -34,6 +34,12 @@ def test_raster_is_complement_of_oracle_mask():
 
 
 def test_gradients_and_prediction_match_reference():
+    """Every gradient entry against the FP64 reference with the same BF16
+    rounding points.  Both sides round the same intermediate values to BF16;
+    where an FP32 and an FP64 sum straddle a rounding boundary one BF16 unit
+    (2^-8 relative) moves, and a gradient entry sums many such terms, so the
+    per-entry bound is a few BF16 units of the entry plus a few units of the
+    block's typical entry (for entries that cancel to near zero)."""
     net = dg.Surrogate(max_batch=8, seed=3, device=0)
     occ, cond = _batch(4, 100)
     rng = np.random.default_rng(1)
@@ -47,11 +53,17 @@ def test_gradients_and_prediction_match_reference():
     rloss, rgrad, ry = S.loss_and_grad(params.astype(np.float64), occ, cond, tgt)
     assert np.abs(out.cpu().numpy() - ry).max() <= 1e-2 * np.abs(ry).max()
     assert abs(loss / rloss - 1) < 1e-2
+    ulp = 2.0 ** -8
     off = 0
     for name, shp in S.layout():
         size = int(np.prod(shp))
-        g, r = grad[off:off + size], rgrad[off:off + size]
-        assert np.linalg.norm(g - r) <= 3e-2 * np.linalg.norm(r) + 1e-9, name
+        g, r = grad[off:off + size].astype(np.float64), rgrad[off:off + size]
+        typ = np.sqrt(np.mean(r * r)) + 1e-30
+        err = np.abs(g - r)
+        bound = 4 * ulp * np.abs(r) + 4 * ulp * typ
+        worst = float((err / bound).max())
+        print(f"{name}: max |g - r| / bound = {worst:.3f}, max rel {float((err / (np.abs(r) + typ)).max()):.2e}")
+        assert np.all(err <= bound), name
         off += size
     net.close()
 
@@ -100,3 +112,31 @@ def test_augmentation_is_an_exact_symmetry_of_the_dg_sigma():
     o, tt = sgm.augment(occ0, tg, 4, 0, 0)
     assert torch.equal(o, occ1)
     assert np.allclose(tt.cpu().numpy(), s1[:, 0], rtol=1e-5, atol=1e-7)
+
+
+def test_trained_network_beats_the_packing_fit_on_held_out_cells():
+    """The gain over the method without the network: trained on DG Sigma of
+    seeded cells, the network's error on held-out cells (against their DG
+    Sigma) is below that of a least-squares fit on the packing fraction and
+    log(D Delta), the summary a user would have without it."""
+    from paper_1907_06191_gb300 import surrogate as sgm
+    ws_tr = [dginputs.workload_surrogate_member(s, m=16) for s in range(256)]
+    ws_te = [dginputs.workload_surrogate_member(50000 + s, m=16) for s in range(48)]
+    sig_tr, _ = sgm.dg_sigma(ws_tr)
+    sig_te, _ = sgm.dg_sigma(ws_te)
+    occ, cond, tgt = sgm.build_samples(ws_tr, sig_tr)
+    occ_e, cond_e, tgt_e = sgm.build_samples(ws_te, sig_te)
+    to = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0", dt)
+    net = dg.Surrogate(max_batch=256, seed=1, device=0)
+    sgm.train(net, to(occ, torch.uint8), to(cond, torch.float32), to(tgt, torch.float32),
+              epochs=40, batch=64, lr=1e-3)
+    pred = torch.zeros((occ_e.shape[0], 3), device="cuda:0")
+    oe, ce = to(occ_e, torch.uint8), to(cond_e, torch.float32)
+    for b0 in range(0, oe.shape[0], 256):
+        net.predict(oe[b0:b0 + 256], ce[b0:b0 + 256], pred[b0:b0 + 256])
+    rel = np.linalg.norm(pred.cpu().numpy() - tgt_e, axis=1) / np.linalg.norm(tgt_e, axis=1)
+    base = sgm.packing_fit(ws_tr, tgt, ws_te)
+    rel_b = np.linalg.norm(base - tgt_e, axis=1) / np.linalg.norm(tgt_e, axis=1)
+    print(f"held-out error: network {rel.mean():.3f}, packing fit {rel_b.mean():.3f}")
+    assert rel.mean() < rel_b.mean()
+    net.close()

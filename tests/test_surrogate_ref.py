@@ -11,7 +11,9 @@ def test_reference_gradient_matches_finite_differences(monkeypatch):
     rng = np.random.default_rng(4)
     n = sum(int(np.prod(shp)) for _, shp in S.layout())
     params = rng.normal(size=n) * 0.15
-    occ = (rng.random((2, 128, 128)) > 0.6).astype(np.float64)
+    # the network is fully convolutional up to the global average: a 32 x 32
+    # raster exercises every layer at a fraction of the cost
+    occ = (rng.random((2, 32, 32)) > 0.6).astype(np.float64)
     cond = rng.normal(size=(2, 2))
     tgt = rng.normal(size=(2, 3)) * 0.3
     loss, grad, _ = S.loss_and_grad(params, occ, cond, tgt)
@@ -19,7 +21,7 @@ def test_reference_gradient_matches_finite_differences(monkeypatch):
     off = 0
     for name, shp in S.layout():
         size = int(np.prod(shp))
-        for k in rng.choice(size, size=min(3, size), replace=False):
+        for k in rng.choice(size, size=min(2, size), replace=False):
             i = off + int(k)
             eps = 1e-5
             pp, pm = params.copy(), params.copy()
