@@ -400,6 +400,11 @@ def run_batch(args):
     return 0
 
 
+def _surrogate_member(args_tuple):
+    seed, m = args_tuple
+    return dginputs.workload_surrogate_member(seed, m=m)
+
+
 def run_surrogate(args):
     """Learned covariance surrogate: DG Sigma of seeded 10 um cells (batched
     FP32 solves, Delta = 1..5 ms) trains the CNN; held-out cells test it.
@@ -412,10 +417,22 @@ def run_surrogate(args):
     _build.build()
     torch.cuda.set_device(0)
     ntr, nte, ms = args.sg_train, args.sg_test, args.sg_sources
-    ws_tr = [dginputs.workload_surrogate_member(s, m=ms) for s in range(ntr)]
-    ws_te = [dginputs.workload_surrogate_member(100000 + s, m=ms) for s in range(nte)]
+    t_start = time.perf_counter()
+    phases = {}
+
+    def mark(name):
+        phases[name] = round(time.perf_counter() - t_start, 2)
+        print(f"[surrogate] {name}: {phases[name]} s", file=sys.stderr, flush=True)
+
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        ws_tr = pool.map(_surrogate_member, [(s, ms) for s in range(ntr)], chunksize=16)
+        ws_te = pool.map(_surrogate_member, [(100000 + s, ms) for s in range(nte)], chunksize=16)
+    mark("cells drawn")
     sig_tr, t_tr = sgm.dg_sigma(ws_tr)
+    mark("DG training set")
     sig_te, t_te = sgm.dg_sigma(ws_te)
+    mark("DG held-out set")
     # the reference's own noise: the same held-out cells with an independent set
     # of start points (the network sees the substrate, not the start points)
     ws_te2 = []
@@ -425,6 +442,7 @@ def run_surrogate(args):
         ws_te2.append(dginputs.Workload(w.name, w.p, w.L, w.n_cell, w.tiles, w.D, w.sigma0,
                                         w.deltas, w.disks, src, w.meta))
     sig_te2, _ = sgm.dg_sigma(ws_te2)
+    mark("DG held-out set, second start points")
     occ, cond, tgt = sgm.build_samples(ws_tr, sig_tr)
     occ_e, cond_e, tgt_e = sgm.build_samples(ws_te, 0.5 * (sig_te + sig_te2))
     _, _, tgt_a = sgm.build_samples(ws_te, sig_te)
@@ -433,9 +451,11 @@ def run_surrogate(args):
     to = lambda a, dt: torch.from_numpy(a).to("cuda:0", dt)
     net = dg.Surrogate(max_batch=4096, seed=1, device=0)
     t0 = time.perf_counter()
+    mark("samples built")
     hist = sgm.train(net, to(occ, torch.uint8), to(cond, torch.float32), to(tgt, torch.float32),
                      epochs=args.sg_epochs)
     t_train = time.perf_counter() - t0
+    mark("trained")
     # held-out error against the DG solve (the reference)
     pe = torch.zeros((occ_e.shape[0], 3), device="cuda:0")
     oe, ce = to(occ_e, torch.uint8), to(cond_e, torch.float32)
@@ -482,6 +502,7 @@ def run_surrogate(args):
                                "what": "relative difference of the two DG solves"},
             "sources_per_geometry": ms,
             "train_loss_first_last": [hist[0], hist[-1]], "train_seconds": t_train,
+            "phase_seconds": phases,
             "dg_seconds_train_set": t_tr}
     net.close()
     print(json.dumps(line), flush=True)

@@ -143,19 +143,30 @@ def gamma_disks(seed: int, L: float, shape: float, scale: float, *,
                  float(np.sum(math.pi * rr_out ** 2) / (L * L)))
 
 
+class NoRoomForSources(RuntimeError):
+    """No admissible start point found in the box (the disks, grown by the
+    margin, cover it)."""
+
+
 def sample_sources(seed: int, disks: Disks, m: int, box_lo: float,
-                   box_hi: float, margin: float) -> np.ndarray:
+                   box_hi: float, margin: float, max_batches: int = 2000) -> np.ndarray:
     """``m`` start points uniform in the box [box_lo, box_hi)^2 (Sec. 4.1).
 
     A candidate is rejected when it lies within ``r + margin`` of any disk
     (periodic minimum image).  With ``margin`` at least one element side the
     element that contains the point has its centre outside every disk, so the
-    point lies in the meshed extracellular region.  Returns an (m, 2) array.
+    point lies in the meshed extracellular region.  Returns an (m, 2) array;
+    raises NoRoomForSources after ``max_batches`` batches of 4096 candidates
+    without the m points.
     """
     rng = np.random.default_rng(seed)
     out = np.empty((m, 2))
     k = 0
+    tries = 0
     while k < m:
+        tries += 1
+        if tries > max_batches:
+            raise NoRoomForSources(f"{k} of {m} start points after {max_batches * 4096} candidates")
         cand = rng.uniform(box_lo, box_hi, size=(4096, 2))
         if disks.n:
             dx = _min_image(cand[:, 0:1] - disks.cx[None, :], disks.L)
@@ -275,13 +286,25 @@ def workload_surrogate_member(seed: int, m: int = 16) -> Workload:
     """One geometry of the surrogate's training set: 10 um periodic cell of
     32 x 32 elements (h = 0.3125 um), p = 2, Gamma(shape, 0.4 um) disks with
     shape uniform in [1.5, 3.0] at a packing uniform in [0.40, 0.75], 16
-    start points, Delta in {1, 2, 3, 4, 5} ms, D = 2 um^2/ms."""
-    rng = np.random.default_rng(seed + 32452843)
-    packing = float(rng.uniform(0.40, 0.75))
-    shape = float(rng.uniform(1.5, 3.0))
-    return _workload(f"surrogate{seed}", seed, 2, 10.0, 32, 2.0, 0.2,
-                     [1.0, 2.0, 3.0, 4.0, 5.0], shape, 0.4, m, packing=packing,
-                     min_gap=0.05)
+    start points, Delta in {1, 2, 3, 4, 5} ms, D = 2 um^2/ms.  A draw whose
+    disks leave no room for start points (the last disk can overshoot the
+    packing target) is replaced by the draw of seed + 10^7 k, k = 1, 2, ...,
+    keeping the name and seed of the slot."""
+    for k in range(64):
+        sd = seed + 10_000_000 * k
+        rng = np.random.default_rng(sd + 32452843)
+        packing = float(rng.uniform(0.40, 0.75))
+        shape = float(rng.uniform(1.5, 3.0))
+        try:
+            w = _workload(f"surrogate{seed}", sd, 2, 10.0, 32, 2.0, 0.2,
+                          [1.0, 2.0, 3.0, 4.0, 5.0], shape, 0.4, m, packing=packing,
+                          min_gap=0.05)
+        except NoRoomForSources:
+            continue
+        w.meta["seed"] = seed
+        w.meta["draw_seed"] = sd
+        return w
+    raise NoRoomForSources(f"no admissible draw for surrogate cell {seed}")
 
 
 def workload_p5(seed: int = 0, m: int = 32) -> Workload:

@@ -133,3 +133,19 @@ def test_named_workloads_carry_their_sizes():
     assert np.all((w.sources >= 0) & (w.sources < w.L))
     fd = dginputs.free_diffusion_paper()
     assert 2 * fd["T"] * fd["D"] == pytest.approx(32.4)
+
+
+def test_start_points_without_room_raise_instead_of_looping():
+    """A box covered by disks (grown by the margin) has no admissible start
+    point: the rejection sampler gives up after a bounded number of
+    candidates.  The surrogate's cell 2268 is such a draw (its last disk
+    overshoots the packing target); its slot is filled by a redraw."""
+    import time
+    full = dginputs.Disks(np.array([0.5]), np.array([0.5]), np.array([2.0]), 1.0, 0.9, 0.9)
+    t0 = time.perf_counter()
+    with pytest.raises(dginputs.NoRoomForSources):
+        dginputs.sample_sources(1, full, 4, 0.0, 1.0, margin=0.1, max_batches=50)
+    assert time.perf_counter() - t0 < 30
+    w = dginputs.workload_surrogate_member(2268)
+    assert w.meta["seed"] == 2268 and w.meta["draw_seed"] != 2268
+    assert w.sources.shape == (16, 2)
