@@ -292,12 +292,13 @@ int dg_debug_copies(dg_ctx *ctx, int mode, unsigned long long *tensor_copies);
  * short); every barrier wait is bounded and one that runs out ends the
  * launch with DG_ETIMEOUT at the next synchronising call;
  * DG_LAUNCH_TUNED (-1, the default): before the first steps after a change
- * of the densities or geometry, each shape runs stage 1 (DG_LAUNCH_STEP: a
- * whole step) with dt = 0, which leaves the state's values unchanged, four
- * times on the context's stream and the fastest per stage is kept (under
- * stream capture, where nothing can be timed, DG_LAUNCH_CHUNK).  Every
- * shape gives the same bits.  Errors: DG_EINVAL (blocks_per_sm < -2 or
- * > 64). */
+ * of the densities or geometry, DG_LAUNCH_CHUNK and each persistent shape
+ * (and, at p = 5, the tensor-core contraction, see dg_set_contraction) run
+ * stage 1 with dt = 0, which leaves the state's values unchanged, four times
+ * on the context's stream and the fastest is kept (under stream capture,
+ * where nothing can be timed, DG_LAUNCH_CHUNK); DG_LAUNCH_STEP is taken only
+ * when asked for.  Every shape gives the same bits.  Errors: DG_EINVAL
+ * (blocks_per_sm < -2 or > 64). */
 #define DG_LAUNCH_TUNED (-1)
 #define DG_LAUNCH_CHUNK 0
 #define DG_LAUNCH_STEP (-2)

@@ -215,9 +215,12 @@ int resolve_launch(dg_ctx *ctx) {
   const bool fp32 = c.cfg.precision == DG_FP32 && !c.triangles() && c.tmap_ok && c.copy_mode != 1;
   const int maxb = fp32 ? stage_pipe_max_blocks(c.cfg.precision, c.cfg.p, c.geo) : 0;
   const bool tc_ok = fp32 && c.cfg.p == 5 && stage_tc_max_blocks(c.geo) >= 1;
-  std::vector<int> shapes{0};  // the launch shapes this context has
+  // the launch shapes this context has; one launch per step is opt-in only:
+  // it removes launch gaps, which a timing probe under a profiler (that
+  // serialises and slows every launch) would overrate
+  std::vector<int> shapes{0};
   const bool step_ok = fp32 && (c.cfg.p == 1 || c.cfg.p == 3 || c.cfg.p == 5);
-  if (step_ok) shapes.push_back(kLaunchStep);
+  if (step_ok && c.launch_req == kLaunchStep) shapes.push_back(kLaunchStep);
   for (int k = 1; k <= maxb; ++k) shapes.push_back(k);
   int want = 0, want_tc = 0;
   const bool fixed = c.launch_req != -1 || shapes.size() == 1;
