@@ -527,9 +527,9 @@ def main():
     ap.add_argument("--launch", type=int, default=-1,
                     help="stage-kernel launch shape: -1 tuned (library default), 0 one block "
                          "per chunk, k persistent blocks per SM")
-    ap.add_argument("--contraction", type=int, default=-1,
-                    help="FP32 p = 5 element contractions: -1 tuned (library default), "
-                         "0 CUDA cores, 1 tensor cores")
+    ap.add_argument("--contraction", type=int, default=0,
+                    help="FP32 p = 5 element contractions: 0 CUDA cores (library default), "
+                         "1 tensor cores, -1 tuned")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="bench steps of the plain FP64 GPU path timed beside the FP32 path")

@@ -293,7 +293,8 @@ int dg_debug_copies(dg_ctx *ctx, int mode, unsigned long long *tensor_copies);
  * launch with DG_ETIMEOUT at the next synchronising call;
  * DG_LAUNCH_TUNED (-1, the default): before the first steps after a change
  * of the densities or geometry, DG_LAUNCH_CHUNK and each persistent shape
- * (and, at p = 5, the tensor-core contraction, see dg_set_contraction) run
+ * (and, at p = 5 when asked for, the tensor-core contraction, see
+ * dg_set_contraction) run
  * stage 1 with dt = 0, which leaves the state's values unchanged, four times
  * on the context's stream and the fastest is kept (under stream capture,
  * where nothing can be timed, DG_LAUNCH_CHUNK); DG_LAUNCH_STEP is taken only
@@ -316,9 +317,11 @@ int dg_get_launch(dg_ctx *ctx, int *blocks_per_sm);
  * the tensor cores (tcgen05.mma, FP16 operands, FP32 accumulation) with
  * both operands split into FP16 high and low parts after a per-element
  * power-of-two scaling (three products, ~2^-21 of each element's largest
- * term); -1 (default): tuned together with the launch shape (see
- * dg_set_launch).  Other orders and FP64 always use the CUDA cores.
- * Errors: DG_EINVAL (mode outside -1..1). */
+ * term; a reduced-precision path: the split operator's rows do not sum to
+ * exactly zero, which lets the mass drift by ~3e-9 per step); -1: tuned
+ * together with the launch shape (see dg_set_launch).  The default is 0.
+ * Other orders and FP64 always use the CUDA cores.  Errors: DG_EINVAL
+ * (mode outside -1..1). */
 int dg_set_contraction(dg_ctx *ctx, int mode);
 
 /* The contraction the last steps used (0 CUDA cores, 1 tensor cores). */

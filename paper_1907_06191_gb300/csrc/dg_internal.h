@@ -228,10 +228,10 @@ struct Ctx {
   int launch_req = -1;
   int launch_blocks = 0;
   int tuned_blocks = -1;
-  // Element contractions of the FP32 p = 5 stage: contraction_req -1 =
-  // tuned with the launch shape, 0 = CUDA cores, 1 = tensor cores;
+  // Element contractions of the FP32 p = 5 stage: contraction_req 0 = CUDA
+  // cores (the default), 1 = tensor cores, -1 = tuned with the launch shape;
   // contraction_tc is the choice in use.
-  int contraction_req = -1;
+  int contraction_req = 0;
   int contraction_tc = 0;
   int tuned_tc = 0;
   long long tuned_key[2] = {-1, -1};
