@@ -533,9 +533,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="bench steps of the plain FP64 GPU path timed beside the FP32 path")
-    ap.add_argument("--solve-delta", type=float, default=5.0,
+    ap.add_argument("--solve-delta", type=float, default=None,
                     help="measure Sigma solves/s: every density to this Delta (ms) on the "
-                         "growing window (0: skip)")
+                         "growing window (0: skip; default 5 on the 40 um cell workload, "
+                         "0 otherwise)")
     ap.add_argument("--solve-fp64-densities", type=int, default=2,
                     help="densities solved in FP64 for the comparator rate and the error")
     ap.add_argument("--no-check", action="store_true")
@@ -559,6 +560,8 @@ def main():
     ap.add_argument("--batch-delta", type=float, default=1.0,
                     help="diffusion time (ms) the batch windows are sized for")
     args = ap.parse_args()
+    if args.solve_delta is None:
+        args.solve_delta = 5.0 if args.workload == "cell40" else 0.0
     world, rank, local = _dist()
     if args.workload == "batch" and args.impl == "ours":
         return run_batch(args) if rank == 0 else 0
