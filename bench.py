@@ -146,38 +146,48 @@ def _traffic_record(kernel_src: str):
     return rec if rec.get("kernel_sha") == h else None
 
 
+def workload_config(w, tri, window_elements, active_elements, densities, rk):
+    """The workload's identity (the same for both arms of the benchmark)."""
+    return {"workload": w.name + ("_triangles" if tri else ""), "p": w.p,
+            "element": "triangle" if tri else "square", "window_elements": int(window_elements),
+            "active_elements": int(active_elements), "densities_per_gpu": int(densities),
+            "rk_steps_per_bench_step": int(rk),
+            "l2": "state (>=16 GB) larger than L2, no flush"}
+
+
 def run_reference(args, world, rank):
     """The oracle (plain FP64 C, OpenMP over elements) on host cores, each
-    step a bounded sample of the workload: one density, one RK step on the
-    full 1792^2-element window."""
+    step a bounded sample of the workload: one of its densities carried R RK
+    steps on the full 1792^2-element window (the sample cpu_baseline times)."""
     if rank != 0:
         return 0
     import oracle as O
     O.build()
-    w = dginputs.workload_cell40(args.seed, m=64)
+    w = dginputs.workload_cell40(args.seed, m=args.densities)
     cell = O.mask_disks(w.L, w.n_cell, w.disks.cx, w.disks.cy, w.disks.r)
     act = O.window_mask(cell, w.tiles)
     mesh = O.Mesh(p=w.p, active=act, h=w.h, x0=w.origin, y0=w.origin, k0=w.D)
     dof = int(act.sum()) * (w.p + 1) ** 2
     u = O.init_gaussian(mesh, *w.sources[0], w.sigma0)
     dt = 1e-4
+    R = args.rk
     for _ in range(args.warmup):
-        u = O.rk3(mesh, u, 1, dt)
+        u = O.rk3(mesh, u, R, dt)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        u = O.rk3(mesh, u, 1, dt)
+        u = O.rk3(mesh, u, R, dt)
     el = time.perf_counter() - t0
-    v = dof * args.steps / el
+    v = dof * R * args.steps / el
     cores = O.threads()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "DoF-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "window_elements": int(act.size),
-                       "active_elements": int(act.sum()), "p": w.p},
+            "config": workload_config(w, False, act.size, act.sum(), len(w.sources), R),
             "cpu_baseline": {"value": v, "unit": "DoF-steps/s", "cores": cores,
                              "kind": "oracle", "cpu": _host_cpu(),
-                             "sample": "1 density x 1 SSP-RK3 step per bench step on the full window"},
+                             "sample": f"1 of {len(w.sources)} densities x {R} SSP-RK3 steps per "
+                                       "bench step on the full window"},
             "e2e": {"value": v, "unit": "DoF-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -820,18 +830,13 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.precision, "data": "synthetic",
-        "config": {"workload": w.name + ("_triangles" if tri else ""), "p": w.p,
-                   "element": args.element,
-                   "rounding": args.rounding if args.precision == "f32" else "nearest",
-                   "window_elements": inf.nx * inf.ny,
-                   "active_elements": inf.n_active, "densities_per_gpu": m,
-                   "dof_per_density": inf.dof_per_source, "rk_steps_per_bench_step": R,
-                   "dt_ms": dt, "rho_per_ms": rho, "packing": w.disks.packing,
-                   "halo_max_per_block": inf.halo_max,
-                   "launch_blocks_per_sm": launch_used,
-                   "contraction": "tensor cores (FP16 hi/lo split, FP32 accumulation)"
-                   if contraction_used else "CUDA cores",
-                   "disks": w.disks.n, "l2": "state (>=16 GB) larger than L2, no flush"},
+        "config": workload_config(w, tri, inf.nx * inf.ny, inf.n_active, m, R),
+        "run": {"rounding": args.rounding if args.precision == "f32" else "nearest",
+                "dof_per_density": inf.dof_per_source, "dt_ms": dt, "rho_per_ms": rho,
+                "packing": w.disks.packing, "disks": w.disks.n,
+                "halo_max_per_block": inf.halo_max, "launch_blocks_per_sm": launch_used,
+                "contraction": "tensor cores (FP16 hi/lo split, FP32 accumulation)"
+                if contraction_used else "CUDA cores"},
         "sigma_solves_per_s": solve["sigma_solves_per_s"] if solve else None,
         "sigma_solve": solve,
         "fp64_value": fp64["value"] if fp64 else None,

@@ -18,7 +18,7 @@ def _bench(args, env_extra=None):
 
 
 def test_reference_arm_prints_one_complete_line():
-    r = _bench(["--impl", "reference", "--steps", "1", "--warmup", "0"])
+    r = _bench(["--impl", "reference", "--steps", "1", "--warmup", "0", "--rk", "2"])
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
     assert len(lines) == 1, r.stdout
@@ -32,9 +32,11 @@ def test_reference_arm_prints_one_complete_line():
     assert (line["n_gpus"], line["steps"], line["warmup"]) == (1, 1, 0)
     assert line["value"] > 0 and line["ms_per_step"] > 0
     assert line["config"]["workload"] == "cell40_p3_256x256" and line["config"]["p"] == 3
-    # value = DoF per density x steps / time: one density, one RK step per bench step
+    # value = DoF per density x RK steps / time: one density, R RK steps per bench step
     dof = line["config"]["active_elements"] * 16
-    assert abs(line["value"] * line["ms_per_step"] * 1e-3 / dof - 1) < 1e-9
+    R = line["config"]["rk_steps_per_bench_step"]
+    assert R == 2 and line["config"]["densities_per_gpu"] == 64
+    assert abs(line["value"] * line["ms_per_step"] * 1e-3 / (dof * R) - 1) < 1e-9
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1
     assert cb["cores"] <= (os.cpu_count() or 1) and "logical CPUs" in cb["cpu"]
