@@ -186,6 +186,35 @@ __global__ void __launch_bounds__(kMmaThreads)
       px = r % p.W;
     }
   }
+  // Gather state, computed once per thread.  FWD / DGRAD with C >= 8
+  // channels (a multiple of 8) in the gathered tensor: the pixel index of
+  // each of the 9 tap pixels (-1 outside the map), and per 8-wide K group its
+  // (tap, channel), advanced by 32 channels per chunk.  WGRAD: this
+  // thread's B column (tap, channel) and its 16 pixels per chunk, decoded
+  // once per chunk and stepped.
+  constexpr int kGroups = kChunk / 8;
+  const int C = MODE == kFwd ? p.Cin : p.Cout;  // channels of the gathered tensor (FWD / DGRAD)
+  int toff[9];
+  int gtap[kGroups], gch[kGroups];
+  if (MODE != kWgrad) {
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+      const int yy = MODE == kFwd ? py + dy : py - dy, xx = MODE == kFwd ? px + dx : px - dx;
+      toff[tap] = (row_ok && yy >= 0 && yy < p.H && xx >= 0 && xx < p.W)
+                      ? (pb * p.H + yy) * p.W + xx  // pixel index (< 2^31 for B <= 65535)
+                      : -1;
+    }
+#pragma unroll
+    for (int g = 0; g < kGroups; ++g) {
+      gtap[g] = C >= 8 ? (8 * g) / C : 0;
+      gch[g] = C >= 8 ? (8 * g) % C : 0;
+    }
+  }
+  const int wn = col0 + (t >> 1);            // WGRAD: this thread's B column
+  const int wtap = MODE == kWgrad ? wn / p.Cin : 0, wci = MODE == kWgrad ? wn % p.Cin : 0;
+  const int wdy = wtap / 3 - 1, wdx = wtap % 3 - 1;
+  const __nv_bfloat16 *src = MODE == kFwd ? p.x : p.dz;
   bool ok = true;
   for (int c = 0; c < nchunks; ++c) {
     const int buf = c & 1;
@@ -196,35 +225,28 @@ __global__ void __launch_bounds__(kMmaThreads)
     const long long kc = k_begin + (long long)c * kChunk;
     // ---- A chunk: row t, 32 K values as 4 pieces of 8 ----
 #pragma unroll
-    for (int g = 0; g < kChunk / 8; ++g) {
+    for (int g = 0; g < kGroups; ++g) {
       alignas(16) __nv_bfloat16 v[8];
-      const long long k0 = kc + g * 8;
-      if (MODE == kFwd) {
-        if (p.Cin >= 8) {
-          const int tap = (int)(k0 / p.Cin), ci = (int)(k0 % p.Cin);
-          const int yy = py + tap / 3 - 1, xx = px + tap % 3 - 1;
-          uint4 q = make_uint4(0, 0, 0, 0);
-          if (row_ok && tap < 9 && yy >= 0 && yy < p.H && xx >= 0 && xx < p.W)
-            q = *reinterpret_cast<const uint4 *>(p.x + (((size_t)pb * p.H + yy) * p.W + xx) * p.Cin + ci);
-          *reinterpret_cast<uint4 *>(v) = q;
-        } else {  // Cin = 1: K = the 9 taps
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int tap = (int)k0 + e;
-            const int yy = py + tap / 3 - 1, xx = px + tap % 3 - 1;
-            v[e] = (row_ok && tap < 9 && yy >= 0 && yy < p.H && xx >= 0 && xx < p.W)
-                       ? p.x[((size_t)pb * p.H + yy) * p.W + xx]
-                       : __float2bfloat16(0.0f);
-          }
-        }
-      } else if (MODE == kDgrad) {
-        const int tap = (int)(k0 / p.Cout), co = (int)(k0 % p.Cout);
-        const int yy = py - (tap / 3 - 1), xx = px - (tap % 3 - 1);
+      if (MODE != kWgrad && C >= 8) {  // 8 channels of one tap: one 16-byte load
         uint4 q = make_uint4(0, 0, 0, 0);
-        if (row_ok && tap < 9 && yy >= 0 && yy < p.H && xx >= 0 && xx < p.W)
-          q = *reinterpret_cast<const uint4 *>(p.dz + (((size_t)pb * p.H + yy) * p.W + xx) * p.Cout + co);
+        const int off = gtap[g] < 9 ? toff[gtap[g]] : -1;
+        if (off >= 0) q = *reinterpret_cast<const uint4 *>(src + (size_t)off * C + gch[g]);
         *reinterpret_cast<uint4 *>(v) = q;
+        gch[g] += kChunk;  // the same group of the next chunk
+        while (gch[g] >= C) {
+          gch[g] -= C;
+          ++gtap[g];
+        }
+      } else if (MODE == kFwd) {  // Cin = 1: K = the 9 taps
+        const int k0 = (int)kc + g * 8;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int tap = k0 + e;
+          const int off = tap < 9 ? toff[tap] : -1;
+          v[e] = off >= 0 ? p.x[off] : __float2bfloat16(0.0f);
+        }
       } else {  // WGRAD: dz[pixel][co] for 8 consecutive pixels
+        const long long k0 = kc + g * 8;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
           const long long m = k0 + e;
@@ -234,38 +256,50 @@ __global__ void __launch_bounds__(kMmaThreads)
       *reinterpret_cast<uint4 *>(sa + core_off(t, g * 8)) = *reinterpret_cast<const uint4 *>(v);
     }
     // ---- B chunk: 64 rows x 32 K, two pieces of 8 per thread ----
+    if (MODE == kFwd || MODE == kDgrad) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int piece = t * 2 + h;          // 0..255
-      const int r = piece >> 2, g = piece & 3;
-      const int n = col0 + r;
-      alignas(16) __nv_bfloat16 v[8];
-      const long long k0 = kc + g * 8;
-      if (MODE == kFwd || MODE == kDgrad) {
+      for (int h = 0; h < 2; ++h) {
+        const int piece = t * 2 + h;  // 0..255
+        const int r = piece >> 2, g = piece & 3;
+        const int n = col0 + r;
         const int nrows = MODE == kFwd ? p.Cout : p.Cin;
         uint4 q = make_uint4(0, 0, 0, 0);
-        if (n < nrows) q = *reinterpret_cast<const uint4 *>(p.w + (size_t)n * p.kpad + k0);
-        *reinterpret_cast<uint4 *>(v) = q;
-      } else {  // WGRAD: column n of im2col(x) (or ones for the bias), 8 pixels
-        const int tap = n / p.Cin, ci = n % p.Cin;
+        if (n < nrows) q = *reinterpret_cast<const uint4 *>(p.w + (size_t)n * p.kpad + kc + g * 8);
+        *reinterpret_cast<uint4 *>(sbm + core_off(r, g * 8)) = q;
+      }
+    } else {  // WGRAD: column wn of im2col(x) (or ones for the bias), 16 pixels
+      const long long m0 = kc + 16 * (t & 1);
+      int b = (int)(m0 / HW);
+      int rr = (int)(m0 % HW);
+      int yy = rr / p.W, xx = rr % p.W;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        alignas(16) __nv_bfloat16 v[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          const long long m = k0 + e;
+          const long long m = m0 + 8 * h + e;
           float val = 0.0f;
-          if (m < k_end && n < p.ncol) {
-            if (n == p.ncol - 1) {
+          if (m < k_end && wn < p.ncol) {
+            if (wn == p.ncol - 1) {
               val = 1.0f;
             } else {
-              const int b = (int)(m / HW), rr = (int)(m % HW);
-              const int yy = rr / p.W + tap / 3 - 1, xx = rr % p.W + tap % 3 - 1;
-              if (yy >= 0 && yy < p.H && xx >= 0 && xx < p.W)
-                val = bf(p.x[(((size_t)b * p.H + yy) * p.W + xx) * p.Cin + ci]);
+              const int y2 = yy + wdy, x2 = xx + wdx;
+              if (y2 >= 0 && y2 < p.H && x2 >= 0 && x2 < p.W)
+                val = bf(p.x[(((size_t)b * p.H + y2) * p.W + x2) * p.Cin + wci]);
             }
           }
           v[e] = __float2bfloat16(val);
+          if (++xx == p.W) {  // the next pixel
+            xx = 0;
+            if (++yy == p.H) {
+              yy = 0;
+              ++b;
+            }
+          }
         }
+        *reinterpret_cast<uint4 *>(sbm + core_off(t >> 1, (2 * (t & 1) + h) * 8)) =
+            *reinterpret_cast<const uint4 *>(v);
       }
-      *reinterpret_cast<uint4 *>(sbm + core_off(r, g * 8)) = *reinterpret_cast<const uint4 *>(v);
     }
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
