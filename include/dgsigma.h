@@ -123,10 +123,10 @@ typedef struct dg_info {
   long long steps;        /* RK steps taken since dg_set_sources */
   size_t state_bytes;     /* device bytes of the three RK state arrays */
   int halo_max;           /* largest number of out-of-block face neighbours of
-                             a block of 256 consecutive elements */
+                             a block of 128 consecutive elements */
   int n_geometries;       /* G: geometries held by the context */
   long long n_elements_padded; /* element slots of all geometries, each padded to
-                             a multiple of 256 (the state stride per density) */
+                             a multiple of 128 (the state stride per density) */
 } dg_info;
 
 /* Fill *cfg with defaults: p=3, FP64, D=2, sigma0=0.2, eta=0, cfl 0.9,
@@ -279,8 +279,8 @@ int dg_debug_copies(dg_ctx *ctx, int mode, unsigned long long *tensor_copies);
 
 /* Launch shape of the FP32 stage kernel (no counterpart in the paper: how the
  * element updates of Sec. 3.3, one independent update per element, are
- * mapped onto the GPU).  DG_LAUNCH_CHUNK (0): one block of 256 threads per
- * chunk of 256 elements and density, one thread per element (all chunks in
+ * mapped onto the GPU).  DG_LAUNCH_CHUNK (0): one block of 128 threads per
+ * chunk of 128 elements and density, one thread per element (all chunks in
  * one launch per RK stage); k >= 1: a persistent launch of k blocks per SM
  * that walk the (density, chunk) work items of every geometry of the
  * context and copy the next item's chunks into shared memory behind the
@@ -312,7 +312,7 @@ int dg_get_launch(dg_ctx *ctx, int *blocks_per_sm);
 /* Where the element contractions of the FP32 stage at p = 5 run.  Sec. 3.1
  * (Remark) notes that each element's update is a small dense local system;
  * the element's volume term and the normal derivatives at its faces are one
- * dense [60 x 36] operator applied to its 36 nodal values, for 256 elements
+ * dense [60 x 36] operator applied to its 36 nodal values, for 128 elements
  * at a time a GEMM.  mode 0: sum-factorised on the CUDA cores (FP32); 1: on
  * the tensor cores (tcgen05.mma, FP16 operands, FP32 accumulation) with
  * both operands split into FP16 high and low parts after a per-element

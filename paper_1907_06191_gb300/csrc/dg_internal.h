@@ -45,11 +45,15 @@ cudaError_t dev_alloc(X **p, size_t bytes) {
 
 constexpr int kMaxP = 5;
 constexpr int kMaxN = kMaxP + 1;
-constexpr int kBlock = 256;         // threads per block of the element kernels
+constexpr int kBlock = 128;         // threads per block of the element kernels = elements per chunk
 constexpr int kTile = 16;           // element ordering: 16 x 16 tiles, row-major inside
 constexpr int kMomBlocks = 608;     // fixed grid of the moment reduction (4 x 152 SMs)
 constexpr int kMomFields = 7;       // M0, Mx, My, Mxx, Mxy, Myy, |u| mass
-constexpr int kHaloCap = 4 * 256;   // halo entries a chunk can have (4 faces x kBlock)
+constexpr int kHaloCap = 4 * kBlock;  // halo entries a chunk can have (4 faces x kBlock)
+// Blocks of kBlock threads per SM that fit the SM's 64K registers at `regs`
+// registers per thread: the __launch_bounds__ minimum that holds a kernel to
+// that register budget.
+constexpr int blocks_for_regs(int regs) { return 65536 / (regs * kBlock); }
 constexpr int kCovOut = 8;          // per geometry: Sigma(t)-Sigma(0) [3], mu [2], Sigma_mix(t) [3]
 
 // Face codes in the neighbour table (>= 0: neighbour element index).

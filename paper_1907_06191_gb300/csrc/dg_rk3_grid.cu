@@ -74,7 +74,7 @@ struct GridArgs {
 };
 
 template <typename T, int P, bool SROUND, bool FULL>
-__global__ void __launch_bounds__(kBlock, 2)
+__global__ void __launch_bounds__(kBlock, blocks_for_regs(128))
     k_rk3_grid(T *U0, T *U1, T *U2, const int4 *__restrict__ loc,
                const int2 *__restrict__ halo, const int *__restrict__ halo_cnt,
                const int2 *__restrict__ chunk_tab, const int2 *__restrict__ grange,

@@ -175,8 +175,8 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // Tensor-memory-accelerator copies of a whole chunk.  The state array is a 2D
 // tensor [rows = densities x padded elements][NP values]; one elected thread
-// arms an mbarrier with the expected bytes and issues one tiled copy of 256
-// rows.  With 32, 64 or 128 bytes per element the copy uses the hardware
+// arms an mbarrier with the expected bytes and issues one tiled copy of
+// kBlock rows.  With 32, 64 or 128 bytes per element the copy uses the hardware
 // swizzle of that width, which XORs the 16-byte slot index with bits of the
 // row exactly as Stage::swz does, so the shared-memory layout is the same as
 // with the per-thread cp.async copies.
@@ -201,7 +201,7 @@ __device__ __forceinline__ void tma_load_rows(uint32_t dst, const CUtensorMap *m
       "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(row), "r"(bar)
       : "memory");
 }
-// Tiled store of 256 rows from shared memory; the issuing thread waits until
+// Tiled store of kBlock rows from shared memory; the issuing thread waits until
 // the shared-memory source has been read (the block's other threads may have
 // left: shared memory lives until the last thread of the block exits).
 __device__ __forceinline__ void tma_store_rows(const CUtensorMap *map, int row, uint32_t src) {
@@ -693,10 +693,10 @@ __device__ __forceinline__ uint32_t element_key(long long elem_in_geo, int np, i
 // of the result), face records.
 template <typename T, int P>
 constexpr int stage_min_blocks() {
-  // blocks of 256 threads per SM the register budget is sized for:
-  // 4 -> 64 registers, 2 -> 128, 1 -> 255
-  if constexpr (sizeof(T) == 4) return P <= 3 ? 4 : 2;
-  else return P <= 3 ? 2 : 1;
+  // registers per thread: 64 (FP32, p <= 3: eight blocks of 128 per SM),
+  // 128 (FP32 p >= 4, FP64 p <= 3), 255 (FP64 p >= 4)
+  if constexpr (sizeof(T) == 4) return blocks_for_regs(P <= 3 ? 64 : 128);
+  else return blocks_for_regs(P <= 3 ? 128 : 255);
 }
 
 // FULL = false drops the flux terms in u^- and u^+ that vanish without a
@@ -888,8 +888,8 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
 // ---- persistent variant: each block walks many chunks, one ahead ---------
 //
 // The kernel above spends a block's life in three phases -- wait for the
-// chunk copies and the tables, compute, store -- and with 4 blocks of 256 per
-// SM the SM often has every block in the same phase.  This variant launches a
+// chunk copies and the tables, compute, store -- and with the SM's few blocks
+// it often has every block in the same phase.  This variant launches a
 // few blocks per SM that stay resident and walk the work items (density,
 // chunk) item = blockIdx.x + k gridDim.x, density-major so that the items in
 // flight are neighbouring chunks of one density (their halos come from L2).
@@ -913,7 +913,7 @@ int pipe_smem_bytes(int halo_max) {
   return 3 * pipe_chunk_bytes<T, P>() + Records<T, P>::bytes(nrec) + 16;
 }
 
-constexpr int kPipeMinBlocks = 2;  // blocks of 256 per SM the registers are sized for
+constexpr int kPipeMinBlocks = blocks_for_regs(128);  // 128 registers per thread
 // the variants that have a persistent kernel: FP32 with whole-slot rows and
 // at least two such blocks per SM in shared memory (p = 1, 3)
 template <typename T, int P>

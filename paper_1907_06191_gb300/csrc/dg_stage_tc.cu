@@ -5,10 +5,10 @@
 // elements independent within a stage) needs, from the element's own 36
 // nodal values u, the volume term (DD)u along x and y and the outward
 // normal derivative at the nodes of its four faces: a dense [60 x 36]
-// operator Op applied to u.  For a chunk of 256 elements this is the GEMM
-//   [256 x 64] = U [256 x 48] . Op^T [48 x 64]     (K, N padded with zeros)
+// operator Op applied to u.  For a chunk of kBlock = 128 elements this is the GEMM
+//   [128 x 64] = U [128 x 48] . Op^T [48 x 64]     (K, N padded with zeros)
 // run as tcgen05.mma kind::f16 -- FP16 operands from shared memory, FP32
-// accumulators in tensor memory -- two M = 128 tiles, one per half chunk.
+// accumulators in tensor memory -- one M = 128 tile per 128 elements.
 // FP16 alone would lose the FP32 state's accuracy, so both operands are
 // split (defect correction): per element u is scaled by a power of two
 // 2^k so that max |u| lies in [1, 2) (exact), v = 2^k u = v_hi + v_lo with
@@ -31,11 +31,13 @@ namespace {
 constexpr int kTcP = 5, kTcN = kTcP + 1, kTcNP = kTcN * kTcN;
 constexpr int kTcK = 48;                         // 36 nodes padded to 3 MMA steps of 16
 constexpr int kTcOut = 64;                       // 36 volume + 24 face derivatives + 4 zero
-constexpr int kTcCols = 128;                     // tensor-memory columns: 2 tiles x 64
+constexpr int kTcTiles = kBlock / 128;           // M = 128 tiles per chunk
+static_assert(kBlock % 128 == 0, "whole M = 128 tiles");
+constexpr int kTcCols = kTcTiles * kTcOut;       // tensor-memory columns (a power of 2)
 constexpr int kTcLBO = 128;                      // bytes between K-adjacent core matrices
 constexpr int kTcSBO = (kTcK / 8) * kTcLBO;      // bytes between 8-row groups (768)
 constexpr int kTcATile = 16 * kTcSBO;            // one M = 128 tile of U (12 KB)
-constexpr int kTcABytes = 2 * kTcATile;          // 256 rows of U, hi or lo
+constexpr int kTcABytes = kTcTiles * kTcATile;   // kBlock rows of U, hi or lo
 constexpr int kTcBBytes = (kTcOut / 8) * kTcSBO; // 64 rows of Op, hi or lo (6 KB)
 
 // Byte offset of (row r, column k) in a K-major operand of 48 FP16 columns
@@ -152,7 +154,7 @@ int tc_smem_bytes(int halo_max) {
 // Launched only with tensor copies (rows of 144 bytes are whole 16-byte
 // slots) and a full-chunk tensor store.
 template <bool HAS_U0, bool SROUND, bool FULL>
-__global__ void __launch_bounds__(kBlock, 2)
+__global__ void __launch_bounds__(kBlock, blocks_for_regs(128))
     k_stage_tc(const float *__restrict__ uin, const float *u0, float *out,
                const int4 *__restrict__ loc, const int2 *__restrict__ halo,
                const int *__restrict__ halo_cnt, const int2 *__restrict__ chunk_tab,
@@ -282,7 +284,7 @@ __global__ void __launch_bounds__(kBlock, 2)
     tc_fence_after();
     const uint32_t a_base = smem_u32(smem_raw), b_base = smem_u32(sb);
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < kTcTiles; ++t) {
       const uint32_t d = tmem + (uint32_t)(t * kTcOut);
 #pragma unroll
       for (int ks = 0; ks < kTcK / 16; ++ks) {

@@ -139,9 +139,9 @@ __device__ __forceinline__ int tri_rec_index(int L, int f, int el, int zero_rec)
   return L >= kBlock ? 4 * kBlock + (L - kBlock) : (L >= 0 ? (f ^ 1) * kBlock + L : zero_rec);
 }
 
-// Blocks of 256 threads per SM the register budget is sized for.
+// Register budget per thread: 64 in FP32, 128 in FP64.
 template <typename T>
-constexpr int tri_min_blocks() { return sizeof(T) == 4 ? 4 : 2; }
+constexpr int tri_min_blocks() { return blocks_for_regs(sizeof(T) == 4 ? 64 : 128); }
 
 // ---- pass Q -------------------------------------------------------------------
 // One triangle at a time: only its N values, its q and the diagonal traces of

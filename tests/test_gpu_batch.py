@@ -52,7 +52,7 @@ def test_batch_equals_single_contexts_and_oracle(prec):
                              [g[1] for g in geos], [g[2] for g in geos], [g[3] for g in geos])
         inf = b.info()
         assert inf.n_geometries == 3
-        assert inf.n_elements_padded % 256 == 0
+        assert inf.n_elements_padded % 128 == 0  # each geometry padded to whole chunks
         b.set_sources(np.stack([g[4] for g in geos]))
         b.step(nsteps, dt)
         s3, mu, mass = b.covariance_batch()
