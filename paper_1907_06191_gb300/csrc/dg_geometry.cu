@@ -224,8 +224,9 @@ __global__ void k_halo(const int4 *__restrict__ nb, const int2 *__restrict__ chu
   }
   loc[a] = live ? make_int4(out[0], out[1], out[2], out[3]) : make_int4(kEdge, kEdge, kEdge, kEdge);
   if (el == 0) halo_cnt[c] = base_s;
-  // every slot after the last entry holds element -1: the stage kernels read
-  // their threads' slots without waiting for the count
+  // every slot after the last entry holds element -1 (and the neighbour codes
+  // of the slots past the chunk's count kEdge): the stage kernels read their
+  // threads' slots without waiting for the counts
   for (int h = base_s + el; h < kHaloCap; h += kBlock)
     halo[(size_t)c * kHaloCap + h] = make_int2(-1, 0);
 }

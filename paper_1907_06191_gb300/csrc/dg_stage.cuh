@@ -739,38 +739,50 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
 
   const int chunk = chunk_list ? __ldg(chunk_list + blockIdx.x) : (int)blockIdx.x;
   const long long a0 = (long long)chunk * kBlock;
-  const uint64_t pol_last = l2_policy_evict_last();
-  const int2 ci = ldg_hint(chunk_tab + chunk, pol_last);
-  const int cnt = ci.x;
   const int el = threadIdx.x;
+  const size_t sbase = (size_t)blockIdx.y * (size_t)stride * NP;
+  const T *U = uin + sbase;
+
+  // tensor copies where the element is a whole number of 16-byte slots and the
+  // buffers sit on their alignment (the same for every thread of the block);
+  // they go out first: nothing they need comes from a table, so no table
+  // load's latency delays them
+  const bool tma = St::SLOT && ca.use_tma && (smem_u32(smem_raw) & 1023u) == 0;
+  const uint32_t bar0 = smem_u32(smem_raw + bar_off), bar1 = bar0 + 8;
+  if (tma && el == 0) {
+    mbar_init(bar0, 1);
+    if constexpr (HAS_U0) mbar_init(bar1, 1);
+    mbar_fence_init();
+    const uint32_t bytes = (uint32_t)(kBlock * NP * sizeof(T)) + (uint32_t)ca.extra_tx;
+    const int row = (int)((long long)blockIdx.y * stride + a0);
+    mbar_expect_tx(bar0, bytes);
+    tma_load_rows(smem_u32(su), &tm_u, row, bar0);
+    if constexpr (HAS_U0) {
+      mbar_expect_tx(bar1, bytes);
+      tma_load_rows_hint(smem_u32(so), &tm_u0, row, bar1, l2_policy_evict_first());
+    }
+    if (ca.counter) atomicAdd(ca.counter, 1ull);
+  }
+  // The table entries, no load waiting for another: this thread's first
+  // halo entry (entries past the chunk's count hold element -1, so the count
+  // is not waited for), its neighbour codes (slots past the chunk's count
+  // hold kEdge), the chunk's element count and geometry, its halo count.
+  const uint64_t pol_last = l2_policy_evict_last();
+  const int2 hk = ldg_hint(halo + (size_t)chunk * kHaloCap + el, pol_last);
+  const int4 l4 = ldg_hint(loc + a0 + el, pol_last);
+  const int2 ci = ldg_hint(chunk_tab + chunk, pol_last);
+  const int hcnt = ldg_hint(halo_cnt + chunk, pol_last);
+  // the halo element's values into registers while the chunk copies are in
+  // flight
+  T hv[NP];
+  if (hk.x >= 0) load_elem<T, NP>(U + (size_t)hk.x * NP, hv);
+  const int cnt = ci.x;
   const bool live = el < cnt;
   // beta dt D / J^2 of this geometry; 0 for an element held by the growing
   // window (its value then passes through every stage unchanged)
   T gam = c.gamma * __ldg(gscale + ci.y);
   if (adv != nullptr && live && __ldg(adv + a0 + el) == 0) gam = (T)0;
-  const size_t sbase = (size_t)blockIdx.y * (size_t)stride * NP;
-  const T *U = uin + sbase;
-
-  // tensor copies where the element is a whole number of 16-byte slots and the
-  // buffers sit on their alignment (the same for every thread of the block)
-  const bool tma = St::SLOT && ca.use_tma && (smem_u32(smem_raw) & 1023u) == 0;
-  const uint32_t bar0 = smem_u32(smem_raw + bar_off), bar1 = bar0 + 8;
-  if (tma) {
-    if (el == 0) {
-      mbar_init(bar0, 1);
-      if constexpr (HAS_U0) mbar_init(bar1, 1);
-      mbar_fence_init();
-      const uint32_t bytes = (uint32_t)(kBlock * NP * sizeof(T)) + (uint32_t)ca.extra_tx;
-      const int row = (int)((long long)blockIdx.y * stride + a0);
-      mbar_expect_tx(bar0, bytes);
-      tma_load_rows(smem_u32(su), &tm_u, row, bar0);
-      if constexpr (HAS_U0) {
-        mbar_expect_tx(bar1, bytes);
-        tma_load_rows_hint(smem_u32(so), &tm_u0, row, bar1, l2_policy_evict_first());
-      }
-      if (ca.counter) atomicAdd(ca.counter, 1ull);
-    }
-  } else {  // async copies of the u chunk (group 0) and the u0 chunk (group 1)
+  if (!tma) {  // async copies of the u chunk (group 0) and the u0 chunk (group 1)
     const char *gu = reinterpret_cast<const char *>(U + (size_t)a0 * NP);
     const int np16 = St::pieces(cnt);
     for (int j = el; j < np16; j += kBlock)
@@ -783,14 +795,6 @@ __global__ void __launch_bounds__(kBlock, stage_min_blocks<T, P>())
       cp_async_commit();
     }
   }
-  const int4 l4 = live ? ldg_hint(loc + a0 + el, pol_last) : make_int4(kEdge, kEdge, kEdge, kEdge);
-  const int hcnt = ldg_hint(halo_cnt + chunk, pol_last);
-  // first halo entry of this thread (entries past the chunk's count hold
-  // element -1, so the count is not waited for): element values into
-  // registers while the chunk copies are in flight
-  const int2 hk = ldg_hint(halo + (size_t)chunk * kHaloCap + el, pol_last);
-  T hv[NP];
-  if (hk.x >= 0) load_elem<T, NP>(U + (size_t)hk.x * NP, hv);
   // Each thread waits (bounded) for the u chunk itself: completing the
   // barrier phase makes the copied bytes visible to the waiting thread.  A
   // time-out is combined over the block at the barrier that hands the u

@@ -186,15 +186,10 @@ __global__ void __launch_bounds__(kBlock, blocks_for_regs(128))
 
   const int chunk = chunk_list ? __ldg(chunk_list + blockIdx.x) : (int)blockIdx.x;
   const long long a0 = (long long)chunk * kBlock;
-  const uint64_t pol_last = l2_policy_evict_last();
-  const int2 ci = ldg_hint(chunk_tab + chunk, pol_last);
-  const int cnt = ci.x;
-  const bool live = el < cnt;
-  float gam = c.gamma * __ldg(gscale + ci.y);
-  if (adv != nullptr && live && __ldg(adv + a0 + el) == 0) gam = 0.0f;
   const size_t sbase = (size_t)blockIdx.y * (size_t)stride * NP;
   const float *U = uin + sbase;
 
+  // the copies go out first (nothing they need comes from a table)
   if (el == 0) {
     mbar_init(bar0, 1);
     if constexpr (HAS_U0) mbar_init(bar1, 1);
@@ -212,12 +207,19 @@ __global__ void __launch_bounds__(kBlock, blocks_for_regs(128))
     }
     if (ca.counter) atomicAdd(ca.counter, 1ull);
   }
-  if (warp == 0) tc_alloc(smem_u32((const void *)tslot));
-  const int4 l4 = live ? ldg_hint(loc + a0 + el, pol_last) : make_int4(kEdge, kEdge, kEdge, kEdge);
-  const int hcnt = ldg_hint(halo_cnt + chunk, pol_last);
+  // table entries, no load waiting for another (as in k_stage)
+  const uint64_t pol_last = l2_policy_evict_last();
   const int2 hk = ldg_hint(halo + (size_t)chunk * kHaloCap + el, pol_last);
+  const int4 l4 = ldg_hint(loc + a0 + el, pol_last);
+  const int2 ci = ldg_hint(chunk_tab + chunk, pol_last);
+  const int hcnt = ldg_hint(halo_cnt + chunk, pol_last);
+  if (warp == 0) tc_alloc(smem_u32((const void *)tslot));
   float hv[NP];
   if (hk.x >= 0) load_elem<float, NP>(U + (size_t)hk.x * NP, hv);
+  const int cnt = ci.x;
+  const bool live = el < cnt;
+  float gam = c.gamma * __ldg(gscale + ci.y);
+  if (adv != nullptr && live && __ldg(adv + a0 + el) == 0) gam = 0.0f;
   tc_fence_before();
   __syncthreads();  // barriers initialised, tensor-memory address published
   tc_fence_after();
