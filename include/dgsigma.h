@@ -327,6 +327,21 @@ int dg_set_contraction(dg_ctx *ctx, int mode);
 /* The contraction the last steps used (0 CUDA cores, 1 tensor cores). */
 int dg_get_contraction(dg_ctx *ctx, int *mode);
 
+/* How a stage on the pixel triangles (DG_ELEMENT_TRIANGLE, Sec. 3.3, Eq. 7)
+ * runs.  With a full mass matrix a triangle's lifted gradient q needs its
+ * neighbours' traces, and the divergence needs the neighbours' q.  fused 0:
+ * two launches per stage, the first writing q of every pixel to device
+ * memory, the second reading it; 1 (the default): one launch per stage that
+ * keeps a chunk's q in shared memory and computes the q of each neighbouring
+ * triangle across the chunk boundary again from the values around it, with
+ * the same arithmetic, so both give the same bits.  One launch per stage runs
+ * in FP32 at p = 2 and 3; other triangle contexts keep two launches.
+ * Errors: DG_EINVAL (fused outside 0..1). */
+int dg_set_triangle_fusion(dg_ctx *ctx, int fused);
+
+/* 1 when the context's triangle stages run as one launch, else 0. */
+int dg_get_triangle_fusion(dg_ctx *ctx, int *fused);
+
 /* Test hook (no counterpart in the paper): the n-th device allocation of the
  * library from now on (0 = the next one, in any context) fails as if the
  * device were out of memory; -1 disarms.  Calls that hit it return

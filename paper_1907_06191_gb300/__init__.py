@@ -99,6 +99,8 @@ EXPORTS = {
     "dg_get_launch": (_I, [_P, ctypes.POINTER(_I)]),
     "dg_set_contraction": (_I, [_P, _I]),
     "dg_get_contraction": (_I, [_P, ctypes.POINTER(_I)]),
+    "dg_set_triangle_fusion": (_I, [_P, _I]),
+    "dg_get_triangle_fusion": (_I, [_P, ctypes.POINTER(_I)]),
     "dg_debug_copies": (_I, [_P, _I, ctypes.POINTER(ctypes.c_ulonglong)]),
     "dg_triangle_tables": (_I, [_I, _DP, _DP, _DP, _DP, _DP]),
     # learned surrogate (include/dgsurrogate.h)
@@ -301,6 +303,15 @@ class DGSolver:
     def get_contraction(self) -> int:
         k = ctypes.c_int()
         self._ck(self._L.dg_get_contraction(self.ctx, ctypes.byref(k)), "dg_get_contraction")
+        return k.value
+
+    def set_triangle_fusion(self, fused: int):
+        """Pixel triangles: 1 one launch per stage (FP32, p = 2, 3), 0 two."""
+        self._ck(self._L.dg_set_triangle_fusion(self.ctx, int(fused)), "dg_set_triangle_fusion")
+
+    def get_triangle_fusion(self) -> int:
+        k = ctypes.c_int()
+        self._ck(self._L.dg_get_triangle_fusion(self.ctx, ctypes.byref(k)), "dg_get_triangle_fusion")
         return k.value
 
     def step(self, nsteps: int, dt: float):

@@ -362,7 +362,7 @@ cudaError_t rk3_step(Ctx &c, double dt, cudaStream_t s, const ChunkSel &sel = Ch
       if (c.triangles())
         e = launch_tri_stage_f32(c.cfg.p, (const float *)in[k], (const float *)base[k],
                                  (float *)outp[k], (float *)c.d_q, c.geo, st, c.m, c.tri, sc,
-                                 s, sel);
+                                 s, sel, c.tri_fused != 0);
       else
         e = launch_stage_f32(c.cfg.p, (const float *)in[k], (const float *)base[k],
                              (float *)outp[k], c.geo, st, c.m, c.gll, sc, s, sel,
@@ -598,7 +598,8 @@ int set_parts(dg_ctx *ctx, const std::vector<PartSpec> &parts) {
   c.have_geo = false;
   c.have_rho = false;
   std::string err;
-  const int code = build_geometry(c.geo, parts, c.cfg.boundary == DG_BC_PERIODIC, c.stream, err);
+  const int code = build_geometry(c.geo, parts, c.cfg.boundary == DG_BC_PERIODIC, c.triangles(),
+                                  c.stream, err);
   if (code != DG_OK) return fail(ctx, code, err);
   c.have_geo = true;
   return DG_OK;
@@ -1032,6 +1033,26 @@ int dg_set_contraction(dg_ctx *ctx, int mode) {
   return DG_OK;
 }
 
+int dg_set_triangle_fusion(dg_ctx *ctx, int fused) {
+  if (!ctx || fused < 0 || fused > 1) return DG_EINVAL;
+  Ctx &c = ctx->c;
+  if (fused != c.tri_fused) {
+    c.tri_fused = fused;
+    drop_graph(c);  // captured launches carry the old kernels
+  }
+  return DG_OK;
+}
+
+int dg_get_triangle_fusion(dg_ctx *ctx, int *fused) {
+  if (!ctx || !fused) return DG_EINVAL;
+  const Ctx &c = ctx->c;
+  *fused = (c.tri_fused && c.triangles() && c.cfg.precision == DG_FP32 &&
+            (c.cfg.p == 2 || c.cfg.p == 3))
+               ? 1
+               : 0;
+  return DG_OK;
+}
+
 int dg_get_contraction(dg_ctx *ctx, int *mode) {
   if (!ctx || !mode) return DG_EINVAL;
   *mode = ctx->c.contraction_tc;
@@ -1222,7 +1243,8 @@ int dg_apply_operator(dg_ctx *ctx) {
     } else {
       StageCoef<float> sc{0.0f, 0.0f, (float)kc, (float)pen, wallA};
       e = launch_tri_stage_f32(c.cfg.p, (const float *)U0, nullptr, (float *)U1, (float *)c.d_q,
-                               c.geo, c.geo.n_pad, c.m, c.tri, sc, c.stream);
+                               c.geo, c.geo.n_pad, c.m, c.tri, sc, c.stream, ChunkSel{},
+                               c.tri_fused != 0);
     }
   } else if (c.cfg.precision == DG_FP64) {
     StageCoef<double> sc{0.0, 0.0, kc, pen, wallA};

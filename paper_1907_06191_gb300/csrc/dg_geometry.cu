@@ -231,6 +231,30 @@ __global__ void k_halo(const int4 *__restrict__ nb, const int2 *__restrict__ chu
     halo[(size_t)c * kHaloCap + h] = make_int2(-1, 0);
 }
 
+// Triangle halo entries: one block per chunk, one thread per entry slot below
+// the stride.  The halo pixel k meets the chunk across its face fk; the
+// triangle of k on that face has one more pixel face, f3 (A: east and south,
+// B: west and north), whose neighbour the fused triangle stage needs too.
+__global__ void k_halo_tri(const int4 *__restrict__ nb, const int2 *__restrict__ halo,
+                           const int *__restrict__ halo_cnt, int stride,
+                           int4 *__restrict__ htri) {
+  const int c = blockIdx.x;
+  const long long a0 = (long long)c * kBlock;
+  const int cnt = halo_cnt[c];
+  for (int h = threadIdx.x; h < stride; h += blockDim.x) {
+    int4 out = make_int4(-1, 0, 0, kEdge);
+    if (h < cnt) {
+      const int2 q = halo[(size_t)c * kHaloCap + h];
+      const int4 n4 = nb[q.x];
+      const int fn[4] = {n4.x, n4.y, n4.z, n4.w};
+      const int fk = q.y;
+      const int f3 = fk == 0 ? 3 : (fk == 3 ? 0 : (fk == 1 ? 2 : 1));
+      out = make_int4(q.x, fk, (int)(fn[fk] - a0), fn[f3]);
+    }
+    htri[(size_t)c * stride + h] = out;
+  }
+}
+
 __global__ void k_max_int(const int *__restrict__ v, int n, int *__restrict__ out) {
   __shared__ int sm[256];
   int m = 0;
@@ -247,7 +271,7 @@ __global__ void k_max_int(const int *__restrict__ v, int n, int *__restrict__ ou
 void free_geometry(Geometry &geo) {
   void *ptrs[] = {geo.d_mask, geo.d_cidx, geo.d_nb, geo.d_exy, geo.d_chunk, geo.d_gpar,
                   geo.d_gscale_f, geo.d_gscale_d, geo.d_grange, geo.d_loc, geo.d_halo,
-                  geo.d_halo_cnt};
+                  geo.d_halo_cnt, geo.d_htri};
   for (void *p : ptrs) cudaFree(p);
   geo = Geometry();
 }
@@ -273,7 +297,7 @@ struct Tmp {
 }  // namespace
 
 int build_geometry(Geometry &geo, const std::vector<PartSpec> &specs, int periodic,
-                   cudaStream_t s, std::string &err) {
+                   bool tri_halo, cudaStream_t s, std::string &err) {
   free_geometry(geo);
   const int G = (int)specs.size();
   if (G < 1) {
@@ -442,6 +466,12 @@ int build_geometry(Geometry &geo, const std::vector<PartSpec> &specs, int period
     return DG_ECUDA;
   }
   geo.halo_max = hmax;
+  if (tri_halo) {
+    const int stride = hmax > 0 ? hmax : 1;
+    GK(dev_alloc(&geo.d_htri, sizeof(int4) * (size_t)nch * stride), "halo table allocation", DG_ENOMEM);
+    k_halo_tri<<<(unsigned)nch, kBlock, 0, s>>>(geo.d_nb, geo.d_halo, geo.d_halo_cnt, stride, geo.d_htri);
+    GK(cudaGetLastError(), "triangle halo table", DG_ECUDA);
+  }
   const GeoPart &p0 = geo.parts[0];
   geo.nx = p0.nx; geo.ny = p0.ny; geo.h = p0.h; geo.x0 = p0.x0; geo.y0 = p0.y0;
 #undef GK

@@ -180,6 +180,11 @@ struct Geometry {
   int2 *d_halo = nullptr;       // [n_chunks][kHaloCap]
   int *d_halo_cnt = nullptr;    // [n_chunks + 1]
   int halo_max = 0;             // largest halo of any chunk
+  // Pixel triangles, one launch per stage: per chunk and halo entry (stride
+  // halo_max) {pixel k, its face toward the chunk, the chunk element across
+  // that face, k's neighbour across the other face of the same triangle
+  // (index, kWall or kEdge)}; entries past the chunk's count hold pixel -1.
+  int4 *d_htri = nullptr;       // [n_chunks][halo_max], built for triangle contexts
   int G() const { return (int)parts.size(); }
   long long n_chunks() const { return n_pad / kBlock; }
 };
@@ -237,6 +242,9 @@ struct Ctx {
   // contraction_tc is the choice in use.
   int contraction_req = 0;
   int contraction_tc = 0;
+  // Pixel triangles in FP32 at p = 2, 3: one launch per stage (1, the
+  // default) or the q pass and the divergence pass (0).
+  int tri_fused = 1;
   int tuned_tc = 0;
   long long tuned_key[2] = {-1, -1};
   int *d_err = nullptr;           // a bounded device wait gave up (and the copy counter)
@@ -338,15 +346,17 @@ cudaError_t launch_stage_f32(int p, const float *u, const float *u0, float *out,
                              const ChunkSel &sel = ChunkSel{},
                              const StageCopies &cp = StageCopies{});
 
-// One stage on the pixel triangles (two passes through qbuf, [m][n_pad][4 N]).
+// One stage on the pixel triangles: two passes through qbuf ([m][n_pad][4 N]),
+// or with `fused` (FP32, p = 2, 3, a geometry built with its triangle halo
+// table) one launch that keeps q in shared memory.
 cudaError_t launch_tri_stage_f64(int p, const double *u, const double *u0, double *out,
                                  double *qbuf, const Geometry &geo, long long stride, int m,
                                  const TriRef &ref, const StageCoef<double> &c, cudaStream_t s,
-                                 const ChunkSel &sel = ChunkSel{});
+                                 const ChunkSel &sel = ChunkSel{}, bool fused = false);
 cudaError_t launch_tri_stage_f32(int p, const float *u, const float *u0, float *out,
                                  float *qbuf, const Geometry &geo, long long stride, int m,
                                  const TriRef &ref, const StageCoef<float> &c, cudaStream_t s,
-                                 const ChunkSel &sel = ChunkSel{});
+                                 const ChunkSel &sel = ChunkSel{}, bool fused = false);
 
 cudaError_t build_mask_disks(const double *d_cx, const double *d_cy, const double *d_r,
                              int nd, double L, int n_cell, int tiles, uint8_t *d_mask,
@@ -354,7 +364,7 @@ cudaError_t build_mask_disks(const double *d_cx, const double *d_cy, const doubl
 // Geometry construction: masks, compaction in tile order, neighbour and halo
 // tables for every part; fills geo (allocates).  Returns a DG_* code.
 int build_geometry(Geometry &geo, const std::vector<PartSpec> &parts, int periodic,
-                   cudaStream_t s, std::string &err);
+                   bool tri_halo, cudaStream_t s, std::string &err);
 void free_geometry(Geometry &geo);
 
 // Densities, moments, covariance.

@@ -143,6 +143,85 @@ __device__ __forceinline__ int tri_rec_index(int L, int f, int el, int zero_rec)
 template <typename T>
 constexpr int tri_min_blocks() { return blocks_for_regs(sizeof(T) == 4 ? 64 : 128); }
 
+// ---- per-triangle pieces shared by the kernels ----------------------------------
+// Each is inlined where it is used, so the q pass, the divergence pass and the
+// fused stage run the same expressions in the same order (the same bits).
+
+// Face f of a pixel: edge e of triangle o (inverse of ftri / fedge).
+__host__ __device__ constexpr int tri_face(int o, int e) {
+  return o == 0 ? (e == 1 ? 0 : 3) : (e == 2 ? 1 : 2);
+}
+__host__ __device__ constexpr bool tri_diag(int o, int e) { return (o == 0 && e == 2) || (o == 1 && e == 0); }
+
+// q = grad u of triangle o, volume part: q = G u.
+template <typename T, int P>
+__device__ __forceinline__ void tri_q_volume(const TriTab<T, P> &tb, int o,
+                                             const T (&uo)[TriShape<P>::N],
+                                             T (&qx)[TriShape<P>::N], T (&qy)[TriShape<P>::N]) {
+  constexpr int N = TriShape<P>::N;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    T ax = 0, ay = 0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      ax += tb.G[o][0][i * N + j] * uo[j];
+      ay += tb.G[o][1][i * N + j] * uo[j];
+    }
+    qx[i] = ax;
+    qy[i] = ay;
+  }
+}
+
+// u-flux of edge e at its nodes: the diagonal's mean of both triangles'
+// traces (dg[o], dg[1 - o], each in its own edge order), or across a pixel
+// face cm u^- + cp u^+ with the neighbour's trace nb in its own edge order.
+template <typename T, int P>
+__device__ __forceinline__ void tri_uh(int o, int e, const T (&uo)[TriShape<P>::N],
+                                       const T (&dg)[2][P + 1], T cm, T cp, const T (&nb)[P + 1],
+                                       T (&uh)[P + 1]) {
+  using S = TriShape<P>;
+  const T half = (T)0.5;
+  if (tri_diag(o, e)) {
+#pragma unroll
+    for (int t = 0; t < P + 1; ++t) uh[t] = half * (dg[o][t] + dg[1 - o][P - t]);
+  } else {
+#pragma unroll
+    for (int t = 0; t < P + 1; ++t) uh[t] = cm * uo[S::en(e, t)] + cp * nb[P - t];
+  }
+}
+
+// q += n_e (Lf_e uh): the lifting of edge e's u-flux.
+template <typename T, int P>
+__device__ __forceinline__ void tri_q_edge(const TriTab<T, P> &tb, int o, int e,
+                                           const T (&uh)[P + 1], T (&qx)[TriShape<P>::N],
+                                           T (&qy)[TriShape<P>::N]) {
+  constexpr int N = TriShape<P>::N, NE = P + 1;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    T a = 0;
+#pragma unroll
+    for (int t = 0; t < NE; ++t) a += tb.Lf[o][e][i * NE + t] * uh[t];
+    qx[i] += tb.nrm[o][e][0] * a;
+    qy[i] += tb.nrm[o][e][1] * a;
+  }
+}
+
+// Weights of u^- and u^+ across a pixel face with neighbour code L.
+template <typename T>
+__device__ __forceinline__ void tri_uflux_weights(int L, int wallA, T &cm, T &cp) {
+  const T half = (T)0.5;
+  cp = L >= 0 ? half : (T)0;                                         // weight of u+
+  cm = L >= 0 ? half : (L == kWall ? (wallA ? half : (T)1) : (T)0);  // of u-
+}
+
+// q . n (outward normal of triangle o, edge e) at the edge's node t.
+template <typename T, int P>
+__device__ __forceinline__ T tri_qn(const TriTab<T, P> &tb, const T (&qx)[TriShape<P>::N],
+                                    const T (&qy)[TriShape<P>::N], int o, int e, int t) {
+  const int k = TriShape<P>::en(e, t);
+  return qx[k] * tb.nrm[o][e][0] + qy[k] * tb.nrm[o][e][1];
+}
+
 // ---- pass Q -------------------------------------------------------------------
 // One triangle at a time: only its N values, its q and the diagonal traces of
 // both triangles are live, which keeps the FP32 kernel within 64 registers.
@@ -196,49 +275,27 @@ __global__ void __launch_bounds__(kBlock, tri_min_blocks<T>())
   float4 *sq = reinterpret_cast<float4 *>(smem_raw + tri_rec_bytes(nrec, NE, (int)sizeof(T)));
 
   const int lq[4] = {b.l4.x, b.l4.y, b.l4.z, b.l4.w};
-  const T half = (T)0.5;
   T *Q = qout + (sbase + (size_t)(b.a0 + b.el)) * (4 * N);
 #pragma unroll 1
   for (int o = 0; o < 2 && b.live; ++o) {
     T uo[N];
     load_elem<T, N>(Ue + o * N, uo);
     T qx[N], qy[N];
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      T ax = 0, ay = 0;
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        ax += tb.G[o][0][i * N + j] * uo[j];
-        ay += tb.G[o][1][i * N + j] * uo[j];
-      }
-      qx[i] = ax;
-      qy[i] = ay;
-    }
+    tri_q_volume<T, P>(tb, o, uo, qx, qy);
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
-      T uh[NE];
-      const bool diag = (o == 0 && e == 2) || (o == 1 && e == 0);
-      if (diag) {
-#pragma unroll
-        for (int t = 0; t < NE; ++t) uh[t] = half * (dg[o][t] + dg[1 - o][P - t]);
-      } else {
-        const int f = o == 0 ? (e == 1 ? 0 : 3) : (e == 2 ? 1 : 2);
+      T uh[NE], nb[NE];
+      T cm = 0, cp = 0;
+      if (!tri_diag(o, e)) {
+        const int f = tri_face(o, e);
         const int L = lq[f];
         const int rn = tri_rec_index(L, f, b.el, zero_rec);
-        const T cp = L >= 0 ? half : (T)0;                                         // weight of u+
-        const T cm = L >= 0 ? half : (L == kWall ? (wallA ? half : (T)1) : (T)0);  // of u-
+        tri_uflux_weights<T>(L, wallA, cm, cp);
 #pragma unroll
-        for (int t = 0; t < NE; ++t)
-          uh[t] = cm * uo[S::en(e, t)] + cp * rec[rn * NE + (P - t)];
+        for (int t = 0; t < NE; ++t) nb[t] = rec[rn * NE + t];
       }
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        T a = 0;
-#pragma unroll
-        for (int t = 0; t < NE; ++t) a += tb.Lf[o][e][i * NE + t] * uh[t];
-        qx[i] += tb.nrm[o][e][0] * a;
-        qy[i] += tb.nrm[o][e][1] * a;
-      }
+      tri_uh<T, P>(o, e, uo, dg, cm, cp, nb, uh);
+      tri_q_edge<T, P>(tb, o, e, uh, qx, qy);
     }
     if constexpr (QS::ON) {
       QS::put(sq, b.el, o, qx, qy);
@@ -255,80 +312,21 @@ __global__ void __launch_bounds__(kBlock, tri_min_blocks<T>())
   }
 }
 
-// ---- pass R + stage update ------------------------------------------------------
-template <typename T, int P, bool HAS_U0, bool SROUND>
-__global__ void __launch_bounds__(kBlock, tri_min_blocks<T>())
-    k_tri_r(const T *__restrict__ qin, const T *__restrict__ uin, const T *u0, T *out,
-            const int4 *__restrict__ loc, const int2 *__restrict__ halo,
-            const int *__restrict__ halo_cnt, const int2 *__restrict__ chunk_tab,
-            const int2 *__restrict__ grange, const T *__restrict__ gscale, long long stride,
-            int nrec, const int *__restrict__ chunk_list, const uint8_t *__restrict__ adv,
-            const TriTab<T, P> tb, const StageCoef<T> c) {
+// ---- divergence and stage update of one pixel ------------------------------------
+// From its q (load_q(o, qx, qy)), the q . n records of its faces and of its
+// neighbours (rec: records f kBlock + el, 4 kBlock + halo slot, the zero
+// record) and the diagonal q . n of both triangles (dg): R = div q with the
+// harmonic-mean flux of Sec. 3.2, then out = u0 + beta (u - u0) + gamma R.
+template <typename T, int P, bool HAS_U0, bool SROUND, typename LoadQ>
+__device__ __forceinline__ void tri_finish(const TriBlock &b, LoadQ load_q, const T *rec,
+                                           int zero_rec, const T (&dg)[2][P + 1],
+                                           const TriTab<T, P> &tb, const StageCoef<T> &c,
+                                           const T *__restrict__ uin, const T *u0, T *out,
+                                           size_t sbase, const int2 *__restrict__ grange,
+                                           const T *__restrict__ gscale,
+                                           const uint8_t *__restrict__ adv) {
   using S = TriShape<P>;
   constexpr int N = S::N, NE = S::NE, NPX = S::NPX;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *rec = reinterpret_cast<T *>(smem_raw);
-  const int zero_rec = nrec - 1;
-  const TriBlock b = tri_block(chunk_list, chunk_tab, loc, halo_cnt);
-  const size_t sbase = (size_t)blockIdx.y * (size_t)stride;
-  const T *Qb = qin + sbase * (4 * N);
-  const T *Qe = Qb + (size_t)(b.a0 + b.el) * (4 * N);
-  using QS = TriQStage<T, P>;
-  float4 *sq = reinterpret_cast<float4 *>(smem_raw + tri_rec_bytes(nrec, NE, (int)sizeof(T)));
-  if constexpr (QS::ON) {  // coalesced 16-byte copies of the chunk's q
-    const char *gq = reinterpret_cast<const char *>(Qb + (size_t)b.a0 * (4 * N));
-    for (int j = b.el; j < b.cnt * QS::S; j += kBlock)
-      cp_async16(sq + (j / QS::S) * QS::SP + j % QS::S, gq + 16 * (size_t)j);
-    cp_async_commit();
-    cp_async_wait<0>();
-    __syncthreads();
-  }
-  auto load_q = [&](int o, T (&qx)[N], T (&qy)[N]) {
-    if constexpr (QS::ON) {
-      QS::get(sq, b.el, o, qx, qy);
-    } else {
-      load_elem<T, N>(Qe + (2 * o) * N, qx);
-      load_elem<T, N>(Qe + (2 * o + 1) * N, qy);
-    }
-  };
-
-  // q . n (outward normal of triangle o, edge e) at the edge's node t
-  auto qn = [&](const T (&qx)[N], const T (&qy)[N], int o, int e, int t) -> T {
-    const int k = S::en(e, t);
-    return qx[k] * tb.nrm[o][e][0] + qy[k] * tb.nrm[o][e][1];
-  };
-  T dg[2][NE];  // q . n on the diagonal of A (e2) and of B (e0)
-  if (b.live) {
-#pragma unroll
-    for (int o = 0; o < 2; ++o) {
-      T qx[N], qy[N];
-      load_q(o, qx, qy);
-#pragma unroll
-      for (int f = 0; f < 4; ++f)
-        if (S::ftri(f) == o)
-#pragma unroll
-          for (int t = 0; t < NE; ++t) rec[(f * kBlock + b.el) * NE + t] = qn(qx, qy, o, S::fedge(f), t);
-#pragma unroll
-      for (int t = 0; t < NE; ++t) dg[o][t] = qn(qx, qy, o, o == 0 ? 2 : 0, t);
-    }
-  }
-  if (b.el == 0)
-    for (int t = 0; t < NE; ++t) rec[zero_rec * NE + t] = (T)0;
-  for (int h = b.el; h < b.hcnt; h += kBlock) {
-    const int2 hq = __ldg(halo + (size_t)b.chunk * kHaloCap + h);
-    const int o = (hq.y == 0 || hq.y == 3) ? 0 : 1;
-    T qx[N], qy[N];
-    load_elem<T, N>(Qb + (size_t)hq.x * (4 * N) + (2 * o) * N, qx);
-    load_elem<T, N>(Qb + (size_t)hq.x * (4 * N) + (2 * o + 1) * N, qy);
-#pragma unroll
-    for (int f = 0; f < 4; ++f)
-      if (hq.y == f)
-#pragma unroll
-        for (int t = 0; t < NE; ++t) rec[(4 * kBlock + h) * NE + t] = qn(qx, qy, o, S::fedge(f), t);
-  }
-  __syncthreads();
-  if (!b.live) return;
-
   const int lq[4] = {b.l4.x, b.l4.y, b.l4.z, b.l4.w};
   const T half = (T)0.5;
   // gamma is beta dt D / J^2 with J = h/2 of the square elements: 1/h^2 = gscale / 4
@@ -354,12 +352,11 @@ __global__ void __launch_bounds__(kBlock, tri_min_blocks<T>())
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
       T hn[NE];  // the normal flux h_q . n / k at the edge nodes
-      const bool diag = (o == 0 && e == 2) || (o == 1 && e == 0);
-      if (diag) {
+      if (tri_diag(o, e)) {
 #pragma unroll
         for (int t = 0; t < NE; ++t) hn[t] = half * (dg[o][t] - dg[1 - o][P - t]);
       } else {
-        const int f = o == 0 ? (e == 1 ? 0 : 3) : (e == 2 ? 1 : 2);
+        const int f = tri_face(o, e);
         const int L = lq[f];
         const int rn = tri_rec_index(L, f, b.el, zero_rec);
         // interior: (q- . n - q+ . n+) / 2; wall: 0; absorbing edge: q- . n
@@ -401,10 +398,318 @@ __global__ void __launch_bounds__(kBlock, tri_min_blocks<T>())
   }
 }
 
+// q . n records of the pixel's own faces (record f kBlock + el) and its
+// diagonal q . n (dg), from its q.
+template <typename T, int P, typename LoadQ>
+__device__ __forceinline__ void tri_qn_records(const TriBlock &b, LoadQ load_q, T *rec,
+                                               const TriTab<T, P> &tb, T (&dg)[2][P + 1]) {
+  using S = TriShape<P>;
+  constexpr int N = S::N, NE = S::NE;
+#pragma unroll
+  for (int o = 0; o < 2; ++o) {
+    T qx[N], qy[N];
+    load_q(o, qx, qy);
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+      if (S::ftri(f) == o)
+#pragma unroll
+        for (int t = 0; t < NE; ++t)
+          rec[(f * kBlock + b.el) * NE + t] = tri_qn<T, P>(tb, qx, qy, o, S::fedge(f), t);
+#pragma unroll
+    for (int t = 0; t < NE; ++t) dg[o][t] = tri_qn<T, P>(tb, qx, qy, o, o == 0 ? 2 : 0, t);
+  }
+}
+
+// ---- pass R + stage update ------------------------------------------------------
+template <typename T, int P, bool HAS_U0, bool SROUND>
+__global__ void __launch_bounds__(kBlock, tri_min_blocks<T>())
+    k_tri_r(const T *__restrict__ qin, const T *__restrict__ uin, const T *u0, T *out,
+            const int4 *__restrict__ loc, const int2 *__restrict__ halo,
+            const int *__restrict__ halo_cnt, const int2 *__restrict__ chunk_tab,
+            const int2 *__restrict__ grange, const T *__restrict__ gscale, long long stride,
+            int nrec, const int *__restrict__ chunk_list, const uint8_t *__restrict__ adv,
+            const TriTab<T, P> tb, const StageCoef<T> c) {
+  using S = TriShape<P>;
+  constexpr int N = S::N, NE = S::NE;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *rec = reinterpret_cast<T *>(smem_raw);
+  const int zero_rec = nrec - 1;
+  const TriBlock b = tri_block(chunk_list, chunk_tab, loc, halo_cnt);
+  const size_t sbase = (size_t)blockIdx.y * (size_t)stride;
+  const T *Qb = qin + sbase * (4 * N);
+  const T *Qe = Qb + (size_t)(b.a0 + b.el) * (4 * N);
+  using QS = TriQStage<T, P>;
+  float4 *sq = reinterpret_cast<float4 *>(smem_raw + tri_rec_bytes(nrec, NE, (int)sizeof(T)));
+  if constexpr (QS::ON) {  // coalesced 16-byte copies of the chunk's q
+    const char *gq = reinterpret_cast<const char *>(Qb + (size_t)b.a0 * (4 * N));
+    for (int j = b.el; j < b.cnt * QS::S; j += kBlock)
+      cp_async16(sq + (j / QS::S) * QS::SP + j % QS::S, gq + 16 * (size_t)j);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+  }
+  auto load_q = [&](int o, T (&qx)[N], T (&qy)[N]) {
+    if constexpr (QS::ON) {
+      QS::get(sq, b.el, o, qx, qy);
+    } else {
+      load_elem<T, N>(Qe + (2 * o) * N, qx);
+      load_elem<T, N>(Qe + (2 * o + 1) * N, qy);
+    }
+  };
+  T dg[2][NE];  // q . n on the diagonal of A (e2) and of B (e0)
+  if (b.live) tri_qn_records<T, P>(b, load_q, rec, tb, dg);
+  if (b.el == 0)
+    for (int t = 0; t < NE; ++t) rec[zero_rec * NE + t] = (T)0;
+  for (int h = b.el; h < b.hcnt; h += kBlock) {
+    const int2 hq = __ldg(halo + (size_t)b.chunk * kHaloCap + h);
+    const int o = (hq.y == 0 || hq.y == 3) ? 0 : 1;
+    T qx[N], qy[N];
+    load_elem<T, N>(Qb + (size_t)hq.x * (4 * N) + (2 * o) * N, qx);
+    load_elem<T, N>(Qb + (size_t)hq.x * (4 * N) + (2 * o + 1) * N, qy);
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+      if (hq.y == f)
+#pragma unroll
+        for (int t = 0; t < NE; ++t) rec[(4 * kBlock + h) * NE + t] = tri_qn<T, P>(tb, qx, qy, o, S::fedge(f), t);
+  }
+  __syncthreads();
+  if (!b.live) return;
+  tri_finish<T, P, HAS_U0, SROUND>(b, load_q, rec, zero_rec, dg, tb, c, uin, u0, out, sbase,
+                                   grange, gscale, adv);
+}
+
+// ---- one launch per stage (FP32, p = 2, 3) ------------------------------------------
+// Both passes in one block, q never written to global memory.  The chunk's q
+// stays in the shared-memory staging; the divergence also needs q . n of each
+// halo triangle (the neighbour triangle across a chunk face), so the block
+// computes that triangle's q again from its values, the diagonal trace of its
+// pixel's other triangle, the chunk pixel's trace and the trace of its third
+// neighbour (the per-chunk table d_htri names them) -- by the same inlined
+// arithmetic as the q pass, so the stage gives the bits of the two launches.
+// A thread computes the q . n of its halo entry first, from device memory
+// alone (the chunk pixel's trace included), so that only those P + 1 values
+// stay live through the chunk's own work.  Records hold u traces first, then
+// (after the barrier behind the last read of a u trace) q . n; a thread's first
+// halo q . n waits in registers, the entries past kBlock in a small area
+// behind the q staging.
+template <typename T, int P>
+struct TriHaloIn {
+  T uo[TriShape<P>::N];  // the halo triangle's values
+  T od[P + 1];           // the diagonal trace of its pixel's other triangle
+  T tc[P + 1];           // the chunk pixel's trace across the face toward the chunk
+  T t3[P + 1];           // the third neighbour's trace across the triangle's other face (or 0)
+};
+
+// Third pixel face of the triangle that owns face fk (A: east, south; B: west, north).
+__host__ __device__ constexpr int tri_third_face(int fk) {
+  return fk == 0 ? 3 : (fk == 3 ? 0 : (fk == 1 ? 2 : 1));
+}
+
+// The halo entry's inputs, face FK of the halo pixel toward the chunk (a
+// template argument, so that every register array is indexed by constants).
+template <typename T, int P, int FK>
+__device__ __forceinline__ void tri_halo_load(const T *U, long long a0, const int4 e,
+                                              TriHaloIn<T, P> &hi) {
+  using S = TriShape<P>;
+  constexpr int N = S::N, NE = S::NE, NPX = S::NPX;
+  constexpr int o = S::ftri(FK);
+  load_elem<T, N>(U + (size_t)e.x * NPX + o * N, hi.uo);
+  T ot[N];
+  load_elem<T, N>(U + (size_t)e.x * NPX + (1 - o) * N, ot);
+#pragma unroll
+  for (int t = 0; t < NE; ++t) hi.od[t] = ot[S::en(o == 0 ? 0 : 2, t)];
+  {
+    constexpr int fc = FK ^ 1;  // the chunk pixel's face toward the halo pixel
+    T vc[N];
+    load_elem<T, N>(U + (size_t)(a0 + e.z) * NPX + S::ftri(fc) * N, vc);
+#pragma unroll
+    for (int t = 0; t < NE; ++t) hi.tc[t] = vc[S::en(S::fedge(fc), t)];
+  }
+  if (e.w >= 0) {
+    constexpr int fb = tri_third_face(FK) ^ 1;  // the third neighbour's face toward the halo pixel
+    T v3[N];
+    load_elem<T, N>(U + (size_t)e.w * NPX + S::ftri(fb) * N, v3);
+#pragma unroll
+    for (int t = 0; t < NE; ++t) hi.t3[t] = v3[S::en(S::fedge(fb), t)];
+  } else {
+#pragma unroll
+    for (int t = 0; t < NE; ++t) hi.t3[t] = (T)0;
+  }
+}
+
+// q . n of the halo triangle at its face FK toward the chunk (in that face's
+// edge order), as the q pass computes it in the halo pixel's own block.
+template <typename T, int P, int FK>
+__device__ __forceinline__ void tri_halo_qn(const int4 e, const TriHaloIn<T, P> &hi,
+                                            const TriTab<T, P> &tb, int wallA, T (&qn)[P + 1]) {
+  using S = TriShape<P>;
+  constexpr int N = S::N, NE = S::NE;
+  constexpr int o = S::ftri(FK);
+  T dgk[2][NE];
+#pragma unroll
+  for (int t = 0; t < NE; ++t) {
+    dgk[o][t] = hi.uo[S::en(o == 0 ? 2 : 0, t)];
+    dgk[1 - o][t] = hi.od[t];
+  }
+  T qx[N], qy[N];
+  tri_q_volume<T, P>(tb, o, hi.uo, qx, qy);
+#pragma unroll
+  for (int ed = 0; ed < 3; ++ed) {
+    T uh[NE], nb[NE];
+    T cm = 0, cp = 0;
+    if (!tri_diag(o, ed)) {
+      // the chunk pixel across FK, else the third neighbour, a wall or the edge
+      const bool chunk_side = tri_face(o, ed) == FK;
+      const int L = chunk_side ? 0 : e.w;
+#pragma unroll
+      for (int t = 0; t < NE; ++t) nb[t] = chunk_side ? hi.tc[t] : hi.t3[t];
+      tri_uflux_weights<T>(L, wallA, cm, cp);
+    }
+    tri_uh<T, P>(o, ed, hi.uo, dgk, cm, cp, nb, uh);
+    tri_q_edge<T, P>(tb, o, ed, uh, qx, qy);
+  }
+#pragma unroll
+  for (int t = 0; t < NE; ++t) qn[t] = tri_qn<T, P>(tb, qx, qy, o, S::fedge(FK), t);
+}
+
+// One halo entry: the halo triangle's u trace at its face toward the chunk
+// (ut) and its q . n there (qn).
+template <typename T, int P, int FK>
+__device__ __forceinline__ void tri_halo_face(const T *U, long long a0, const int4 e,
+                                              const TriTab<T, P> &tb, int wallA,
+                                              T (&ut)[P + 1], T (&qn)[P + 1]) {
+  using S = TriShape<P>;
+  TriHaloIn<T, P> hi;
+  tri_halo_load<T, P, FK>(U, a0, e, hi);
+#pragma unroll
+  for (int t = 0; t < P + 1; ++t) ut[t] = hi.uo[S::en(S::fedge(FK), t)];
+  tri_halo_qn<T, P, FK>(e, hi, tb, wallA, qn);
+}
+
+template <typename T, int P>
+__device__ __forceinline__ void tri_halo_entry(const T *U, long long a0, const int4 e,
+                                               const TriTab<T, P> &tb, int wallA,
+                                               T (&ut)[P + 1], T (&qn)[P + 1]) {
+  switch (e.y) {
+    case 0: tri_halo_face<T, P, 0>(U, a0, e, tb, wallA, ut, qn); break;
+    case 1: tri_halo_face<T, P, 1>(U, a0, e, tb, wallA, ut, qn); break;
+    case 2: tri_halo_face<T, P, 2>(U, a0, e, tb, wallA, ut, qn); break;
+    default: tri_halo_face<T, P, 3>(U, a0, e, tb, wallA, ut, qn); break;
+  }
+}
+
+template <typename T, int P, bool HAS_U0, bool SROUND>
+__global__ void __launch_bounds__(kBlock, tri_min_blocks<T>())
+    k_tri_f(const T *__restrict__ uin, const T *u0, T *out, const int4 *__restrict__ loc,
+            const int4 *__restrict__ htri, int hstride, const int *__restrict__ halo_cnt,
+            const int2 *__restrict__ chunk_tab, const int2 *__restrict__ grange,
+            const T *__restrict__ gscale, long long stride, int nrec,
+            const int *__restrict__ chunk_list, const uint8_t *__restrict__ adv,
+            const TriTab<T, P> tb, const StageCoef<T> c) {
+  using S = TriShape<P>;
+  using QS = TriQStage<T, P>;
+  static_assert(QS::ON, "the chunk's q is staged in shared memory");
+  constexpr int N = S::N, NE = S::NE, NPX = S::NPX;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *rec = reinterpret_cast<T *>(smem_raw);
+  float4 *sq = reinterpret_cast<float4 *>(smem_raw + tri_rec_bytes(nrec, NE, (int)sizeof(T)));
+  T *rx = reinterpret_cast<T *>(smem_raw + tri_rec_bytes(nrec, NE, (int)sizeof(T)) + QS::BYTES);
+  const int zero_rec = nrec - 1;
+  const TriBlock b = tri_block(chunk_list, chunk_tab, loc, halo_cnt);
+  const size_t sbase = (size_t)blockIdx.y * (size_t)stride;
+  const T *U = uin + sbase * NPX;
+  const T *Ue = U + (size_t)(b.a0 + b.el) * NPX;
+  const int4 *H = htri + (size_t)b.chunk * hstride;
+
+  // this thread's first halo entry (entries past the chunk's count hold
+  // pixel -1, so the count is not waited for): its u-trace record and its
+  // q . n, kept in registers; entries past kBlock: q . n into the small area
+  const int4 e0 = b.el < hstride ? __ldg(H + b.el) : make_int4(-1, 0, 0, kEdge);
+  T qh[NE];
+  if (e0.x >= 0) {
+    T ut[NE];
+    tri_halo_entry<T, P>(U, b.a0, e0, tb, c.wallA, ut, qh);
+#pragma unroll
+    for (int t = 0; t < NE; ++t) rec[(4 * kBlock + b.el) * NE + t] = ut[t];
+  }
+  for (int h = b.el + kBlock; h < b.hcnt; h += kBlock) {  // chunks with > kBlock halo entries
+    const int4 e = __ldg(H + h);
+    T ut[NE], q2[NE];
+    tri_halo_entry<T, P>(U, b.a0, e, tb, c.wallA, ut, q2);
+#pragma unroll
+    for (int t = 0; t < NE; ++t) {
+      rec[(4 * kBlock + h) * NE + t] = ut[t];
+      rx[(h - kBlock) * NE + t] = q2[t];
+    }
+  }
+
+  // u traces of the pixel's faces and diagonals (as the q pass)
+  T dg[2][NE];
+  if (b.live) {
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+      T uo[N];
+      load_elem<T, N>(Ue + o * N, uo);
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+        if (S::ftri(f) == o)
+#pragma unroll
+          for (int t = 0; t < NE; ++t) rec[(f * kBlock + b.el) * NE + t] = uo[S::en(S::fedge(f), t)];
+#pragma unroll
+      for (int t = 0; t < NE; ++t) dg[o][t] = uo[S::en(o == 0 ? 2 : 0, t)];
+    }
+  }
+  if (b.el == 0)
+    for (int t = 0; t < NE; ++t) rec[zero_rec * NE + t] = (T)0;
+  __syncthreads();
+
+  // the chunk's q into the staging (as the q pass)
+  const int lq[4] = {b.l4.x, b.l4.y, b.l4.z, b.l4.w};
+#pragma unroll 1
+  for (int o = 0; o < 2 && b.live; ++o) {
+    T uo[N];
+    load_elem<T, N>(Ue + o * N, uo);
+    T qx[N], qy[N];
+    tri_q_volume<T, P>(tb, o, uo, qx, qy);
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      T uh[NE], nb[NE];
+      T cm = 0, cp = 0;
+      if (!tri_diag(o, e)) {
+        const int f = tri_face(o, e);
+        const int L = lq[f];
+        const int rn = tri_rec_index(L, f, b.el, zero_rec);
+        tri_uflux_weights<T>(L, c.wallA, cm, cp);
+#pragma unroll
+        for (int t = 0; t < NE; ++t) nb[t] = rec[rn * NE + t];
+      }
+      tri_uh<T, P>(o, e, uo, dg, cm, cp, nb, uh);
+      tri_q_edge<T, P>(tb, o, e, uh, qx, qy);
+    }
+    QS::put(sq, b.el, o, qx, qy);
+  }
+  __syncthreads();  // every u trace read, the staged q complete
+
+  auto load_q = [&](int o, T (&qx)[N], T (&qy)[N]) { QS::get(sq, b.el, o, qx, qy); };
+  if (b.live) tri_qn_records<T, P>(b, load_q, rec, tb, dg);
+  if (e0.x >= 0) {
+#pragma unroll
+    for (int t = 0; t < NE; ++t) rec[(4 * kBlock + b.el) * NE + t] = qh[t];
+  }
+  for (int h = b.el + kBlock; h < b.hcnt; h += kBlock) {
+#pragma unroll
+    for (int t = 0; t < NE; ++t) rec[(4 * kBlock + h) * NE + t] = rx[(h - kBlock) * NE + t];
+  }
+  __syncthreads();
+  if (!b.live) return;
+  tri_finish<T, P, HAS_U0, SROUND>(b, load_q, rec, zero_rec, dg, tb, c, uin, u0, out, sbase,
+                                   grange, gscale, adv);
+}
+
 template <typename T, int P>
 cudaError_t launch_tri_p(const T *u, const T *u0, T *out, T *qbuf, const Geometry &geo,
                          long long stride, int m, const TriRef &ref, const StageCoef<T> &c,
-                         cudaStream_t s, const ChunkSel &sel) {
+                         cudaStream_t s, const ChunkSel &sel, bool fused) {
   const long long nch = sel.list ? sel.count : geo.n_chunks();
   if (geo.n_pad <= 0 || m <= 0 || nch <= 0) return cudaSuccess;
   if (nch > geo.n_chunks()) return cudaErrorInvalidValue;
@@ -414,9 +719,44 @@ cudaError_t launch_tri_p(const T *u, const T *u0, T *out, T *qbuf, const Geometr
   else gscale = geo.d_gscale_f;
   const TriTab<T, P> tb = make_tri_tab<T, P>(ref);
   const int nrec = 4 * kBlock + geo.halo_max + 1;
+  constexpr bool kSR = sizeof(T) == 4;
+  if constexpr (TriQStage<T, P>::ON) {
+    if (fused && geo.d_htri != nullptr) {  // one launch: q stays in shared memory
+      const int hstride = geo.halo_max > 0 ? geo.halo_max : 1;
+      const int extra = geo.halo_max > kBlock ? (geo.halo_max - kBlock) * TriShape<P>::NE * (int)sizeof(T) : 0;
+      const int fsmem = tri_rec_bytes(nrec, TriShape<P>::NE, (int)sizeof(T)) + TriQStage<T, P>::BYTES +
+                        (extra + 15) / 16 * 16;
+      static int fattr_bytes = 0;
+      if (fsmem > fattr_bytes) {
+        cudaError_t e = cudaSuccess;
+        auto set = [&](auto kern) {
+          if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, fsmem);
+        };
+        set(k_tri_f<T, P, true, false>);
+        set(k_tri_f<T, P, false, false>);
+        set(k_tri_f<T, P, true, kSR>);
+        set(k_tri_f<T, P, false, kSR>);
+        if (e != cudaSuccess) return e;
+        fattr_bytes = fsmem;
+      }
+      auto gof = [&](auto kern) {
+        kern<<<grid, kBlock, fsmem, s>>>(u, u0, out, geo.d_loc, geo.d_htri, hstride, geo.d_halo_cnt,
+                                         geo.d_chunk, geo.d_grange, gscale, stride, nrec, sel.list,
+                                         sel.adv, tb, c);
+      };
+      if (kSR && c.sround) {
+        if (u0) gof(k_tri_f<T, P, true, kSR>);
+        else gof(k_tri_f<T, P, false, kSR>);
+      } else {
+        if (u0) gof(k_tri_f<T, P, true, false>);
+        else gof(k_tri_f<T, P, false, false>);
+      }
+      return cudaGetLastError();
+    }
+  }
   const int smem = tri_rec_bytes(nrec, TriShape<P>::NE, (int)sizeof(T)) + TriQStage<T, P>::BYTES;
   static int attr_bytes = 0;
-  constexpr bool kSR = sizeof(T) == 4;
   if (smem > attr_bytes) {
     cudaError_t e = cudaSuccess;
     auto set = [&](auto kern) {
@@ -453,11 +793,11 @@ cudaError_t launch_tri_p(const T *u, const T *u0, T *out, T *qbuf, const Geometr
 template <typename T>
 cudaError_t launch_tri_any(int p, const T *u, const T *u0, T *out, T *qbuf, const Geometry &geo,
                            long long stride, int m, const TriRef &ref, const StageCoef<T> &c,
-                           cudaStream_t s, const ChunkSel &sel) {
+                           cudaStream_t s, const ChunkSel &sel, bool fused) {
   switch (p) {
-    case 1: return launch_tri_p<T, 1>(u, u0, out, qbuf, geo, stride, m, ref, c, s, sel);
-    case 2: return launch_tri_p<T, 2>(u, u0, out, qbuf, geo, stride, m, ref, c, s, sel);
-    case 3: return launch_tri_p<T, 3>(u, u0, out, qbuf, geo, stride, m, ref, c, s, sel);
+    case 1: return launch_tri_p<T, 1>(u, u0, out, qbuf, geo, stride, m, ref, c, s, sel, fused);
+    case 2: return launch_tri_p<T, 2>(u, u0, out, qbuf, geo, stride, m, ref, c, s, sel, fused);
+    case 3: return launch_tri_p<T, 3>(u, u0, out, qbuf, geo, stride, m, ref, c, s, sel, fused);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -465,14 +805,14 @@ cudaError_t launch_tri_any(int p, const T *u, const T *u0, T *out, T *qbuf, cons
 cudaError_t launch_tri_stage_f64(int p, const double *u, const double *u0, double *out,
                                  double *qbuf, const Geometry &geo, long long stride, int m,
                                  const TriRef &ref, const StageCoef<double> &c, cudaStream_t s,
-                                 const ChunkSel &sel) {
-  return launch_tri_any<double>(p, u, u0, out, qbuf, geo, stride, m, ref, c, s, sel);
+                                 const ChunkSel &sel, bool fused) {
+  return launch_tri_any<double>(p, u, u0, out, qbuf, geo, stride, m, ref, c, s, sel, fused);
 }
 cudaError_t launch_tri_stage_f32(int p, const float *u, const float *u0, float *out,
                                  float *qbuf, const Geometry &geo, long long stride, int m,
                                  const TriRef &ref, const StageCoef<float> &c, cudaStream_t s,
-                                 const ChunkSel &sel) {
-  return launch_tri_any<float>(p, u, u0, out, qbuf, geo, stride, m, ref, c, s, sel);
+                                 const ChunkSel &sel, bool fused) {
+  return launch_tri_any<float>(p, u, u0, out, qbuf, geo, stride, m, ref, c, s, sel, fused);
 }
 
 }  // namespace dg
