@@ -79,9 +79,13 @@ __host__ __device__ constexpr int tri_rec_bytes(int nrec, int ne, int tsize) {
 template <typename T, int P>
 struct TriTab {
   static constexpr int N = TriShape<P>::N, NE = TriShape<P>::NE;
+  using T2 = typename Vec2<T>::type;
   T G[2][2][N * N];
   T Lf[2][3][N * NE];
   T nrm[2][3][2];
+  // rows 2ip and 2ip + 1 of G side by side, for the packed two-lane FP32
+  // instructions: Gp[o][c][ip N + j] = (G[o][c][2ip][j], G[o][c][2ip + 1][j])
+  T2 Gp[2][2][(N / 2) * N];
 };
 
 template <typename T, int P>
@@ -91,6 +95,12 @@ TriTab<T, P> make_tri_tab(const TriRef &r) {
   for (int o = 0; o < 2; ++o) {
     for (int c = 0; c < 2; ++c)
       for (int k = 0; k < N * N; ++k) t.G[o][c][k] = (T)r.G[o][c][k];
+    for (int c = 0; c < 2; ++c)
+      for (int ip = 0; ip < N / 2; ++ip)
+        for (int j = 0; j < N; ++j) {
+          t.Gp[o][c][ip * N + j].x = t.G[o][c][2 * ip * N + j];
+          t.Gp[o][c][ip * N + j].y = t.G[o][c][(2 * ip + 1) * N + j];
+        }
     for (int e = 0; e < 3; ++e) {
       for (int k = 0; k < N * NE; ++k) t.Lf[o][e][k] = (T)r.Lf[o][e][k];
       t.nrm[o][e][0] = (T)r.nrm[o][e][0];
@@ -153,12 +163,35 @@ __host__ __device__ constexpr int tri_face(int o, int e) {
 }
 __host__ __device__ constexpr bool tri_diag(int o, int e) { return (o == 0 && e == 2) || (o == 1 && e == 0); }
 
+// Packed two-lane FP32 for the element matrices where N is even (p = 2, 3):
+// two rows per instruction, each lane rounded like the scalar fused
+// multiply-add, in the same order.
+template <typename T, int P>
+constexpr bool kTriPacked = sizeof(T) == 4 && TriShape<P>::N % 2 == 0;
+
 // q = grad u of triangle o, volume part: q = G u.
 template <typename T, int P>
 __device__ __forceinline__ void tri_q_volume(const TriTab<T, P> &tb, int o,
                                              const T (&uo)[TriShape<P>::N],
                                              T (&qx)[TriShape<P>::N], T (&qy)[TriShape<P>::N]) {
   constexpr int N = TriShape<P>::N;
+  if constexpr (kTriPacked<T, P>) {
+#pragma unroll
+    for (int ip = 0; ip < N / 2; ++ip) {
+      float2 ax = make_float2(0.0f, 0.0f), ay = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const float2 uj = make_float2(uo[j], uo[j]);
+        ax = __ffma2_rn(tb.Gp[o][0][ip * N + j], uj, ax);
+        ay = __ffma2_rn(tb.Gp[o][1][ip * N + j], uj, ay);
+      }
+      qx[2 * ip] = ax.x;
+      qx[2 * ip + 1] = ax.y;
+      qy[2 * ip] = ay.x;
+      qy[2 * ip + 1] = ay.y;
+    }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     T ax = 0, ay = 0;
@@ -340,13 +373,26 @@ __device__ __forceinline__ void tri_finish(const TriBlock &b, LoadQ load_q, cons
     {
       T qx[N], qy[N];
       load_q(o, qx, qy);
+      if constexpr (kTriPacked<T, P>) {
 #pragma unroll
-      for (int i = 0; i < N; ++i) {
-        T a = 0;
+        for (int ip = 0; ip < N / 2; ++ip) {
+          float2 a = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int j = 0; j < N; ++j)
-          a = fmaT(tb.G[o][1][i * N + j], qy[j], fmaT(tb.G[o][0][i * N + j], qx[j], a));
-        R[i] = a;
+          for (int j = 0; j < N; ++j)
+            a = __ffma2_rn(tb.Gp[o][1][ip * N + j], make_float2(qy[j], qy[j]),
+                           __ffma2_rn(tb.Gp[o][0][ip * N + j], make_float2(qx[j], qx[j]), a));
+          R[2 * ip] = a.x;
+          R[2 * ip + 1] = a.y;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          T a = 0;
+#pragma unroll
+          for (int j = 0; j < N; ++j)
+            a = fmaT(tb.G[o][1][i * N + j], qy[j], fmaT(tb.G[o][0][i * N + j], qx[j], a));
+          R[i] = a;
+        }
       }
     }
 #pragma unroll
