@@ -86,6 +86,8 @@ struct TriTab {
   // rows 2ip and 2ip + 1 of G side by side, for the packed two-lane FP32
   // instructions: Gp[o][c][ip N + j] = (G[o][c][2ip][j], G[o][c][2ip + 1][j])
   T2 Gp[2][2][(N / 2) * N];
+  // the liftings likewise: Lfp[o][e][ip NE + t] = (Lf[o][e][2ip][t], Lf[o][e][2ip + 1][t])
+  T2 Lfp[2][3][(N / 2) * NE];
 };
 
 template <typename T, int P>
@@ -103,6 +105,11 @@ TriTab<T, P> make_tri_tab(const TriRef &r) {
         }
     for (int e = 0; e < 3; ++e) {
       for (int k = 0; k < N * NE; ++k) t.Lf[o][e][k] = (T)r.Lf[o][e][k];
+      for (int ip = 0; ip < N / 2; ++ip)
+        for (int q = 0; q < NE; ++q) {
+          t.Lfp[o][e][ip * NE + q].x = t.Lf[o][e][2 * ip * NE + q];
+          t.Lfp[o][e][ip * NE + q].y = t.Lf[o][e][(2 * ip + 1) * NE + q];
+        }
       t.nrm[o][e][0] = (T)r.nrm[o][e][0];
       t.nrm[o][e][1] = (T)r.nrm[o][e][1];
     }
@@ -229,6 +236,23 @@ __device__ __forceinline__ void tri_q_edge(const TriTab<T, P> &tb, int o, int e,
                                            const T (&uh)[P + 1], T (&qx)[TriShape<P>::N],
                                            T (&qy)[TriShape<P>::N]) {
   constexpr int N = TriShape<P>::N, NE = P + 1;
+  if constexpr (kTriPacked<T, P>) {
+    const float2 n0 = make_float2(tb.nrm[o][e][0], tb.nrm[o][e][0]);
+    const float2 n1 = make_float2(tb.nrm[o][e][1], tb.nrm[o][e][1]);
+#pragma unroll
+    for (int ip = 0; ip < N / 2; ++ip) {
+      float2 a = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int t = 0; t < NE; ++t) a = __ffma2_rn(tb.Lfp[o][e][ip * NE + t], make_float2(uh[t], uh[t]), a);
+      const float2 x = __ffma2_rn(n0, a, make_float2(qx[2 * ip], qx[2 * ip + 1]));
+      const float2 y = __ffma2_rn(n1, a, make_float2(qy[2 * ip], qy[2 * ip + 1]));
+      qx[2 * ip] = x.x;
+      qx[2 * ip + 1] = x.y;
+      qy[2 * ip] = y.x;
+      qy[2 * ip + 1] = y.y;
+    }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     T a = 0;
@@ -411,12 +435,24 @@ __device__ __forceinline__ void tri_finish(const TriBlock &b, LoadQ load_q, cons
 #pragma unroll
         for (int t = 0; t < NE; ++t) hn[t] = cm * rec[(f * kBlock + b.el) * NE + t] + cp * rec[rn * NE + (P - t)];
       }
+      if constexpr (kTriPacked<T, P>) {
 #pragma unroll
-      for (int i = 0; i < N; ++i) {
-        T a = 0;
+        for (int ip = 0; ip < N / 2; ++ip) {
+          float2 a = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int t = 0; t < NE; ++t) a += tb.Lf[o][e][i * NE + t] * hn[t];
-        R[i] += a;
+          for (int t = 0; t < NE; ++t) a = __ffma2_rn(tb.Lfp[o][e][ip * NE + t], make_float2(hn[t], hn[t]), a);
+          const float2 r2 = __fadd2_rn(make_float2(R[2 * ip], R[2 * ip + 1]), a);
+          R[2 * ip] = r2.x;
+          R[2 * ip + 1] = r2.y;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          T a = 0;
+#pragma unroll
+          for (int t = 0; t < NE; ++t) a += tb.Lf[o][e][i * NE + t] * hn[t];
+          R[i] += a;
+        }
       }
     }
     T u[N], w[N];
