@@ -55,6 +55,13 @@ def test_host_only_calls(L):
     assert L.dg_create(ctypes.byref(bad), ctypes.byref(h)) == dg.DG_EINVAL
     assert L.dg_create(None, ctypes.byref(h)) == dg.DG_EINVAL
     assert L.dg_step(None, 1, 1.0) == dg.DG_EINVAL
+    # the switches refuse a null context before touching anything
+    k = ctypes.c_int()
+    for call, args in ((L.dg_set_launch, (0,)), (L.dg_set_contraction, (0,)),
+                       (L.dg_set_triangle_fusion, (1,)), (L.dg_get_launch, (ctypes.byref(k),)),
+                       (L.dg_get_contraction, (ctypes.byref(k),)),
+                       (L.dg_get_triangle_fusion, (ctypes.byref(k),))):
+        assert call(None, *args) == dg.DG_EINVAL
     # raster arguments are checked before any device call: a cell side that is
     # not a positive finite number is refused
     out = (ctypes.c_uint8 * 16)()
